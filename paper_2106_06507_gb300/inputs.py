@@ -1,0 +1,75 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the smoke check.
+
+This module holds no part of the method's arithmetic: it only draws the
+random numbers that the method consumes as inputs (Rambo uniforms, sampled
+helicity labels, sampled colours).  Both the CUDA path and the CPU oracle are
+fed the arrays it returns, so that they see identical inputs.
+
+Generator: SplitMix64 (Steele, Lea, Flood 2014) used as a counter-based
+generator, value(seed, stream, i) = mix(mix(seed * GOLDEN + stream) + i *
+GOLDEN), with the 53 high bits mapped to the open interval (0, 1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+STREAM_UNIFORMS = 1
+STREAM_HELICITY = 2
+STREAM_COLOUR = 3
+STREAM_MULTIPLICITY = 4
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def raw64(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """`count` 64-bit words of one (seed, stream) sequence starting at `offset`."""
+    with np.errstate(over="ignore"):
+        key = _mix(np.array([seed], dtype=np.uint64) * _GOLDEN + np.uint64(stream))[0]
+        idx = np.arange(offset, offset + count, dtype=np.uint64)
+        return _mix(key + idx * _GOLDEN)
+
+
+def uniforms(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """Doubles in the open interval (0, 1)."""
+    r = raw64(seed, stream, count, offset) >> np.uint64(11)
+    return (r.astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def rambo_uniforms(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.ndarray:
+    """[batch, 4(n-2)] uniforms for Rambo: per final-state gluon (u1..u4)."""
+    d = 4 * (n - 2)
+    return uniforms(seed, STREAM_UNIFORMS + 16 * n, batch * d, first_event * d).reshape(batch, d)
+
+
+def helicities(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.ndarray:
+    """[batch, n] int8 labels, +1 or -1 with equal probability."""
+    r = raw64(seed, STREAM_HELICITY + 16 * n, batch * n, first_event * n) >> np.uint64(63)
+    return (1 - 2 * r.astype(np.int64)).astype(np.int8).reshape(batch, n)
+
+
+def adjoint_colours(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.ndarray:
+    """[batch, n] int8 adjoint indices, uniform in 1..8."""
+    r = raw64(seed, STREAM_COLOUR + 16 * n, batch * n, first_event * n) >> np.uint64(61)
+    return (1 + r.astype(np.int64)).astype(np.int8).reshape(batch, n)
+
+
+def flow_colours(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.ndarray:
+    """[batch, 2n] int8 colour-flow pairs (r_i, c_i), each uniform in 1..3."""
+    u = uniforms(seed, STREAM_COLOUR + 16 * n + 8, batch * 2 * n, first_event * 2 * n)
+    return (1 + np.minimum((u * 3.0).astype(np.int64), 2)).astype(np.int8).reshape(batch, 2 * n)
+
+
+def multiplicities(batch: int, n_min: int, n_max: int, seed: int = 0) -> np.ndarray:
+    """[batch] int32 multiplicities uniform in n_min..n_max."""
+    u = uniforms(seed, STREAM_MULTIPLICITY, batch)
+    span = n_max - n_min + 1
+    return (n_min + np.minimum((u * span).astype(np.int64), span - 1)).astype(np.int32)

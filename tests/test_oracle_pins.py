@@ -1,0 +1,357 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the
+mathematics, independent of the oracle's own formulas (CPU only).
+
+Each test is chosen so that a plausible slip in the oracle (a dropped
+vertex term, a wrong sign or sqrt(2), a transposed colour product, a wrong
+boost) fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2106_06507_gb300 import inputs
+
+SQRT_S = 1000.0
+Q = (1.0, 0.0, 0.0, 1.0)
+
+
+def event(O, n, seed=0, i=0):
+    u = inputs.rambo_uniforms(n, i + 1, seed=seed)[i]
+    p = O.rambo(n, SQRT_S, u)
+    return u, p, O.outgoing(p)
+
+
+def helicity_vector(O, k, t, q=Q):
+    """Definite-helicity vector (e1 + i e2)/sqrt2 or its conjugate, labelled by
+    the sign of i (p^ x eps_T).eps_T* for the positive-energy momentum p = +-k."""
+    e1, e2 = O.polarisations(k, q)
+    v = (e1 + 1j * e2) / math.sqrt(2.0)
+    p = k if k[0] > 0 else -k
+    eT = v[1:] - (v[0] / p[0]) * p[1:]
+    ph = p[1:] / np.linalg.norm(p[1:])
+    h = (1j * np.dot(np.cross(ph, eT), np.conj(eT)) / np.dot(eT, np.conj(eT))).real
+    assert abs(abs(h) - 1.0) < 1e-9
+    return v if np.sign(h) == t else np.conj(v)
+
+
+# --------------------------------------------------------------------------
+# Rambo (P7) and flatness
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5, 6, 8, 10, 12])
+def test_rambo_conservation_and_masslessness(oracle, n):
+    for i in range(20):
+        _, p, k = event(oracle, n, seed=1, i=i)
+        assert np.allclose(k.sum(axis=0), 0.0, atol=1e-12 * SQRT_S)
+        assert np.all(np.abs(oracle.mdot(k, k)) <= 1e-9 * SQRT_S**2)
+        assert abs(p[2:, 0].sum() - SQRT_S) <= 1e-12 * SQRT_S
+        assert np.all(p[:, 0] > 0)
+
+
+def test_rambo_flat_energy_spectrum(oracle):
+    # Flat massless n_out-body phase space: x = 2E/sqrt(s) has density
+    # (m-1)(m-2) x (1-x)^(m-3), m = n_out, so <x^2> = 6/(m(m+1)); directions
+    # are isotropic, <cos^2 theta> = 1/3.
+    n = 6
+    m = n - 2
+    B = 20000
+    u = inputs.rambo_uniforms(n, B, seed=7)
+    x2 = []
+    c2 = []
+    for e in range(B):
+        p = oracle.rambo(n, SQRT_S, u[e])
+        x = 2.0 * p[2:, 0] / SQRT_S
+        x2.extend(x * x)
+        c2.extend((p[2:, 3] / p[2:, 0]) ** 2)
+    assert abs(np.mean(x2) / (6.0 / (m * (m + 1))) - 1.0) < 0.01
+    assert abs(np.mean(c2) * 3.0 - 1.0) < 0.01
+
+
+# --------------------------------------------------------------------------
+# polarisations, Eq. (2.2)
+# --------------------------------------------------------------------------
+def test_polarisation_projector(oracle):
+    g = np.diag([1.0, -1.0, -1.0, -1.0])
+    for n in (4, 7):
+        _, _, k = event(oracle, n, seed=2)
+        for i in range(n):
+            e1, e2 = oracle.polarisations(k[i], Q)
+            for e in (e1, e2):
+                assert abs(oracle.mdot(e, e) + 1.0) < 1e-12
+                assert abs(oracle.mdot(e, k[i])) < 1e-12 * abs(k[i][0])
+            assert abs(oracle.mdot(e1, e2)) < 1e-12
+            q = np.array(Q) if abs(oracle.mdot(k[i], Q)) > 1e-9 * abs(k[i][0]) else np.array([1.0, 0, 0, -1.0])
+            assert abs(oracle.mdot(e1, q)) < 1e-12 and abs(oracle.mdot(e2, q)) < 1e-12
+            # sum_l e_l^mu e_l^nu = -g^{mu nu} + (k^mu q^nu + q^mu k^nu)/(k.q)
+            lhs = np.outer(e1, e1) + np.outer(e2, e2)
+            rhs = -np.linalg.inv(g) + (np.outer(k[i], q) + np.outer(q, k[i])) / oracle.mdot(k[i], q)
+            assert np.allclose(lhs, rhs, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# P1: the 4-gluon colour- and helicity-summed |M|^2
+# --------------------------------------------------------------------------
+def test_four_gluon_closed_form(oracle):
+    # sum over all 256 colour and helicity states of |M(gg->gg)|^2 =
+    # 256 * (9/2) g^4 (3 - tu/s^2 - su/t^2 - st/u^2)
+    g = 1.2
+    B = 50
+    u = inputs.rambo_uniforms(4, B, seed=3)
+    me2 = oracle.me2_co(4, u, sqrt_s=SQRT_S, g=g)
+    for e in range(B):
+        k = oracle.outgoing(oracle.rambo(4, SQRT_S, u[e]))
+        s = oracle.mdot(k[0] + k[1], k[0] + k[1])
+        t = oracle.mdot(k[0] + k[2], k[0] + k[2])
+        uu = oracle.mdot(k[0] + k[3], k[0] + k[3])
+        ref = 1152.0 * g**4 * (3.0 - t * uu / s**2 - s * uu / t**2 - s * t / uu**2)
+        assert abs(me2[e] / ref - 1.0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# P2: Parke-Taylor MHV magnitudes, vanishing all-plus / one-minus
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+def test_parke_taylor(oracle, n):
+    _, _, k = event(oracle, n, seed=4)
+    order = list(range(n))
+    rng = np.random.default_rng(n)
+    rng.shuffle(order)
+
+    def s(a, b):
+        return 2.0 * oracle.mdot(k[a], k[b])
+
+    den = abs(np.prod([s(order[i], order[(i + 1) % n]) for i in range(n)]))
+    pairs = list(itertools.combinations(range(n), 2))
+    mags = []
+    for (i, j) in pairs[:12]:
+        for t0 in (1, -1):
+            t = [t0] * n
+            t[i] = t[j] = -t0
+            eps = np.stack([helicity_vector(oracle, k[a], t[a]) for a in range(n)])
+            A = oracle.amp_co_complex(k, eps, order)
+            mags.append(abs(A))
+            assert abs(abs(A) ** 2 / (s(i, j) ** 4 / den) - 1.0) < 1e-8
+    scale = max(mags)
+    for t in ([1] * n, [-1] * n, [-1] + [1] * (n - 1), [1, -1] + [-1] * (n - 2)):
+        eps = np.stack([helicity_vector(oracle, k[a], t[a]) for a in range(n)])
+        assert abs(oracle.amp_co_complex(k, eps, order)) < 1e-10 * scale
+
+
+# --------------------------------------------------------------------------
+# P3: gauge invariance
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5, 6, 7])
+def test_ward_identity(oracle, n):
+    _, _, k = event(oracle, n, seed=5)
+    hel = inputs.helicities(n, 1, seed=5)[0]
+    eps = oracle.pols_for(k, hel)
+    order = list(range(n))
+    ref = abs(oracle.amp_co(k, eps, order))
+    for r in range(min(6, math.factorial(n - 2))):
+        o = [0] + list(oracle.ordering(n, r)) + [n - 1]
+        a0 = oracle.amp_co(k, eps, o)
+        ref = max(ref, abs(a0))
+        for i in range(n):
+            e2 = eps.copy()
+            e2[i] = k[i] * (np.linalg.norm(eps[i]) / abs(k[i][0]))
+            assert abs(oracle.amp_co(k, e2, o)) < 1e-10 * max(ref, abs(a0))
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_summed_me2_independent_of_reference_vector(oracle, n):
+    u = inputs.rambo_uniforms(n, 3, seed=6)
+    a = oracle.me2_co(n, u, sqrt_s=SQRT_S, q=(1.0, 0.0, 0.0, 1.0))
+    b = oracle.me2_co(n, u, sqrt_s=SQRT_S, q=(1.0, 0.6, 0.0, 0.8))
+    c = oracle.me2_co(n, u, sqrt_s=SQRT_S, q=(2.0, -1.2, 1.6, 0.0))
+    assert np.allclose(a, b, rtol=1e-11, atol=0)
+    assert np.allclose(a, c, rtol=1e-11, atol=0)
+
+
+# --------------------------------------------------------------------------
+# P4: cyclic, reflection, photon decoupling; linear == helicity sums
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5, 6, 7])
+def test_cyclic_reflection_decoupling(oracle, n):
+    _, _, k = event(oracle, n, seed=8)
+    hel = inputs.helicities(n, 1, seed=8)[0]
+    eps = oracle.pols_for(k, hel)
+    base = list(range(n))
+    a = oracle.amp_co(k, eps, base)
+    scale = abs(a)
+    for c in range(1, n):
+        cyc = base[c:] + base[:c]
+        scale = max(scale, abs(oracle.amp_co(k, eps, cyc)))
+    for c in range(1, n):
+        cyc = base[c:] + base[:c]
+        assert abs(oracle.amp_co(k, eps, cyc) - a) < 1e-10 * scale
+    assert abs(oracle.amp_co(k, eps, base[::-1]) - (-1) ** n * a) < 1e-10 * scale
+    # U(1) decoupling: gluon 1 inserted at every place of the cyclic order of 2..n
+    rest = base[1:]
+    terms = [oracle.amp_co(k, eps, rest[:j] + [0] + rest[j:]) for j in range(1, n)]
+    assert abs(sum(terms)) < 1e-10 * max(abs(t) for t in terms)
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_linear_sum_equals_helicity_sum(oracle, n):
+    _, _, k = event(oracle, n, seed=9)
+    order = list(range(n))
+    lin = 0.0
+    hel = 0.0
+    for conf in range(2**n):
+        h = [1 if (conf >> i) & 1 == 0 else -1 for i in range(n)]
+        lin += oracle.amp_co(k, oracle.pols_for(k, h), order) ** 2
+        eps = np.stack([helicity_vector(oracle, k[a], h[a]) for a in range(n)])
+        hel += abs(oracle.amp_co_complex(k, eps, order)) ** 2
+    assert abs(lin / hel - 1.0) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# P7: tensor form == V4 form; current conservation
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+def test_tensor_form_equals_v4_form(oracle, n):
+    _, _, k = event(oracle, n, seed=10)
+    hel = inputs.helicities(n, 1, seed=10)[0]
+    eps = oracle.pols_for(k, hel)
+    for r in range(min(5, math.factorial(n - 2))):
+        o = [0] + list(oracle.ordering(n, r)) + [n - 1]
+        Jv, _ = oracle.currents_co(k, eps, o, tensor_form=False)
+        Jt, _ = oracle.currents_co(k, eps, o, tensor_form=True)
+        assert np.allclose(Jv, Jt, rtol=1e-10, atol=1e-12 * np.abs(Jv).max())
+
+
+@pytest.mark.parametrize("n", [5, 6, 7, 8])
+def test_current_conservation(oracle, n):
+    _, _, k = event(oracle, n, seed=11)
+    hel = inputs.helicities(n, 1, seed=11)[0]
+    eps = oracle.pols_for(k, hel)
+    o = [0] + list(oracle.ordering(n, 3)) + [n - 1]
+    J, P = oracle.currents_co(k, eps, o)
+    m = n - 1
+    for i in range(m):
+        for j in range(i, m - (1 if i == 0 else 0)):
+            scale = np.abs(J[i, j]).max() * np.abs(P[i, j]).max()
+            assert abs(oracle.mdot(P[i, j], J[i, j])) <= 1e-10 * scale
+
+
+# --------------------------------------------------------------------------
+# P5: colour matrix, Eq. (2.17)
+# --------------------------------------------------------------------------
+def test_adjoint_generators(oracle):
+    F = oracle.adjoint_generators()
+    assert np.abs(F.real).max() < 1e-14  # F = i f with f real
+    f = F.imag
+    assert np.allclose(f, -np.swapaxes(f, 1, 2), atol=1e-14)
+    assert np.allclose(f, -np.swapaxes(f, 0, 1), atol=1e-14)
+    # sum_{bc} f^abc f^a'bc = 2 N delta^aa'  (C_A = N with Tr(T^a T^b) = delta)
+    assert np.allclose(np.einsum("abc,dbc->ad", f, f), 6.0 * np.eye(8), atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+def test_colour_matrix_closed_forms(oracle, n):
+    C = oracle.colour_matrix(n)
+    k = math.factorial(n - 2)
+    assert C.shape == (k, k)
+    # diagonal: sum_a |(F..F)_{a1 an}|^2 = Tr((sum_b F^b F^b)^(n-2)) = 8 (2N)^(n-2)
+    assert np.allclose(np.diag(C), 8.0 * 6.0 ** (n - 2), rtol=1e-12)
+    assert np.allclose(C, C.T, rtol=0, atol=1e-9 * C.max())
+    # entries are integers (each term of the U(N) expansion is +-N^loops)
+    assert np.abs(C - np.round(C)).max() < 1e-6
+    # symmetric positive definite
+    np.linalg.cholesky(C)
+
+
+def test_colour_matrix_depends_on_relative_permutation(oracle):
+    for n in (5, 6):
+        k = math.factorial(n - 2)
+        pairs = np.array([(s, t) for s in range(k) for t in range(k)], dtype=np.int64)
+        direct = oracle.colour_entries(n, pairs).reshape(k, k)
+        assert np.allclose(direct, oracle.colour_matrix(n), rtol=0, atol=1e-9)
+
+
+def test_colour_golden_rows_reproduce(oracle):
+    for n in (4, 5, 6):
+        assert np.allclose(oracle.colour_row_explicit(n), oracle.colour_row(n), rtol=0, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# P6: colour-dressed == colour-ordered x colour matrix (brute force)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5])
+def test_colour_dressed_bruteforce_adjoint(oracle, n):
+    u = inputs.rambo_uniforms(n, 1, seed=12)
+    hel = inputs.helicities(n, 1, seed=12)
+    cols = np.array(list(itertools.product(range(1, 9), repeat=n)), dtype=np.int8)
+    B = cols.shape[0]
+    est = oracle.me2_cd(n, np.repeat(u, B, axis=0), np.repeat(hel, B, axis=0), cols, mode=0, sqrt_s=SQRT_S)
+    co = oracle.me2_co(n, u, sqrt_s=SQRT_S, hel=hel)
+    assert abs(est.mean() / co[0] - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_colour_dressed_bruteforce_flow(oracle, n):
+    u = inputs.rambo_uniforms(n, 1, seed=13)
+    hel = inputs.helicities(n, 1, seed=13)
+    cols = np.array(list(itertools.product(range(1, 4), repeat=2 * n)), dtype=np.int8)
+    B = cols.shape[0]
+    est = oracle.me2_cd(n, np.repeat(u, B, axis=0), np.repeat(hel, B, axis=0), cols, mode=1, sqrt_s=SQRT_S)
+    co = oracle.me2_co(n, u, sqrt_s=SQRT_S, hel=hel)
+    assert abs(est.mean() / co[0] - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_colour_dressed_current_is_ordering_sum(oracle, n):
+    # Eq. (2.28): J(S) = sum over orderings of S of (E_s1 ... E_sL) J(s1..sL)
+    _, _, k = event(oracle, n, seed=14)
+    hel = inputs.helicities(n, 1, seed=14)[0]
+    eps = oracle.pols_for(k, hel)
+    E = oracle.externals_for(inputs.adjoint_colours(n, 1, seed=14)[0], 0)
+    m = n - 1
+    for S in range(1, 2**m):
+        labels = [i for i in range(m) if S >> i & 1]
+        L = len(labels)
+        ref = np.zeros((3, 3, 4))
+        mag = 0.0
+        for perm in itertools.permutations(labels):
+            rest = [i for i in range(n) if i not in perm]
+            o = list(perm) + rest
+            J, _ = oracle.currents_co(k, eps, o)
+            col = np.eye(3)
+            for i in perm:
+                col = col @ E[i]
+            ref += col[:, :, None] * J[0, L - 1][None, None, :]
+            mag = max(mag, np.abs(col).max() * np.abs(J[0, L - 1]).max())
+        got = oracle.current_cd(k, eps, E, S)
+        assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * mag)
+
+
+def test_colour_dressed_current_conservation(oracle):
+    n = 7
+    _, _, k = event(oracle, n, seed=15)
+    hel = inputs.helicities(n, 1, seed=15)[0]
+    eps = oracle.pols_for(k, hel)
+    E = oracle.externals_for(inputs.flow_colours(n, 1, seed=15)[0], 1)
+    for S in (0b11, 0b111, 0b10110, 0b111101):
+        J = oracle.current_cd(k, eps, E, S)
+        P = k[[i for i in range(n - 1) if S >> i & 1]].sum(axis=0)
+        scale = np.abs(J).max() * np.abs(P).max() + 1e-300
+        assert np.abs(oracle.mdot(P[None, None, :], J)).max() < 1e-10 * scale
+
+
+# --------------------------------------------------------------------------
+# P8: gradient with respect to the Rambo uniforms
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [4, 5])
+def test_gradient_dual_vs_central_differences(oracle, n):
+    u = inputs.rambo_uniforms(n, 1, seed=16)[0]
+    hel = inputs.helicities(n, 1, seed=16)[0]
+    v, grad = oracle.me2_co_grad(n, u, hel, sqrt_s=SQRT_S)
+    assert abs(v / oracle.me2_co(n, u[None], sqrt_s=SQRT_S, hel=hel[None])[0] - 1.0) < 1e-12
+    h = 1e-6
+    for j in range(u.size):
+        up = u.copy(); up[j] += h
+        um = u.copy(); um[j] -= h
+        fd = (oracle.me2_co(n, up[None], sqrt_s=SQRT_S, hel=hel[None])[0]
+              - oracle.me2_co(n, um[None], sqrt_s=SQRT_S, hel=hel[None])[0]) / (2 * h)
+        assert abs(fd - grad[j]) <= 1e-5 * np.abs(grad).max()
