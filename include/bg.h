@@ -1,0 +1,157 @@
+/* bg.h -- C ABI of the GB300 Berends-Giele library (libbg.so).
+ *
+ * Per-event colour- and helicity-summed (or sampled) squared tree amplitudes
+ * |M|^2 for n-gluon scattering, gg -> (n-2) g, computed with the
+ * Berends-Giele recursion of "Many-gluon tree amplitudes on modern GPUs"
+ * (Bothmann, Giele, Hoeche, Isaacson, Knobbe), in two forms:
+ *   - colour-ordered currents (Sec. 2.3, Eqs. 2.20-2.22) for all (n-2)!
+ *     orderings of the adjoint (DDM) basis, Eq. (2.15), followed by the
+ *     colour sum A^T C A of Eq. (2.16) with the colour matrix of Eq. (2.17);
+ *   - colour-dressed currents (Eqs. 2.28-2.32) for sampled colours.
+ * Inputs are Rambo phase-space points (Sec. 3) and helicity / colour labels;
+ * the output is |M|^2 per event, as in the paper's statement of the problem
+ * (Eqs. 2.1, 2.4).
+ *
+ * Conventions shared by every call
+ *   - n is the total number of gluons (gg -> gg is n = 4); 4 <= n <= 12.
+ *   - All array arguments are caller-owned DEVICE pointers unless stated
+ *     otherwise; the library never frees them.  Nothing here allocates
+ *     memory except bg_colormat_create and bg_plan_create.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are asynchronous on it: argument errors are returned synchronously,
+ *     launch errors as BG_ECUDA; data-dependent device errors (an invalid
+ *     helicity or colour label) are recorded in a device status word that
+ *     bg_device_status() reads after a synchronisation.
+ *   - Momenta are in GeV, metric (+,-,-,-).  Event-indexed arrays are
+ *     structure-of-arrays with the event index fastest, so that consecutive
+ *     GPU threads read consecutive addresses.
+ *   - Polarisations: real light-cone-gauge vectors e1, e2 of Eq. (2.7) with
+ *     reference vector q (Eq. 2.2); helicity label +1 selects e1, -1 selects
+ *     e2.  Sums over both labels equal the helicity sums (Eq. 2.3).  The
+ *     gauge frame: with n = q_vec/|q_vec|, a and b are x^ and y^ rotated by
+ *     the rotation taking z^ to n (for n_z < 0: a(-n) and -b(-n)); e1 =
+ *     A - (A.k/q.k) q, e2 = B - (B.k/q.k) q with A = (0,a), B = (0,b).  If a
+ *     gluon momentum k is parallel to q (|k.q| <= 1e-9 |k0| q0), q is
+ *     replaced by (q0, -q_vec) for that gluon.
+ *   - Couplings: |M|^2 includes g_s^(2n-4).  It is summed (not averaged)
+ *     over colours and helicities; no symmetry factor is applied.
+ *   - Errors never abort and never throw.
+ */
+#ifndef BG_H
+#define BG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BG_OK = 0,
+  BG_EINVAL = 1,        /* invalid argument (size, pointer, alignment, enum) */
+  BG_ENOMEM = 2,        /* device or host allocation failed (create calls only) */
+  BG_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  BG_EUNSUPPORTED = 4,  /* valid but not supported (e.g. n out of range for a mode) */
+  BG_ETIMEOUT = 5       /* a bounded device wait gave up */
+} bg_status;
+
+/* Arithmetic type of the recursion (currents and amplitudes). */
+typedef enum { BG_F64 = 0, BG_F32 = 1 } bg_prec;
+
+/* Colour-sum arithmetic: FP64 CUDA cores, FP32 CUDA cores. */
+typedef enum { BG_CS_F64 = 0, BG_CS_F32 = 1 } bg_cs_mode;
+
+/* Sampled-colour representation for the colour-dressed recursion. */
+typedef enum { BG_COL_ADJOINT = 0, BG_COL_FLOW = 1 } bg_color_mode;
+
+/* Last error message of the calling thread ("" if none). */
+const char* bg_last_error(void);
+
+/* Number of colour orderings (n-2)! of the adjoint basis, Eq. (2.15);
+ * 0 if n is outside 4..12. */
+int64_t bg_num_orderings(int n);
+
+/* ---------------------------------------------------------------------------
+ * Colour matrix C_{sigma sigma'} of Eq. (2.17), sigma, sigma' in S_{n-2}
+ * (orderings of gluons 2..n-1 in lexicographic order), normalised with
+ * Tr(T^a T^b) = delta^ab so that F^a_bc = Tr(T^a [T^b, T^c]).  Built on the
+ * host by expanding each chain of adjoint generators into fundamental
+ * traces and contracting with the U(N) completeness relation (each term is
+ * +-N^loops), then uploaded to the current device.  The object is
+ * library-owned: free it with bg_colormat_destroy.  Supported: 4 <= n <= 9.
+ * Errors: BG_EINVAL (n, out), BG_EUNSUPPORTED (n > 9), BG_ENOMEM, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+typedef struct bg_colormat bg_colormat;
+bg_status bg_colormat_create(int n, bg_colormat** out);
+void bg_colormat_destroy(bg_colormat* C);
+/* Copies the first row C_{id, tau} (length (n-2)!) to HOST memory `row`. */
+bg_status bg_colormat_row(const bg_colormat* C, double* row);
+/* Same first row computed on the host only (no device is touched), for
+ * 4 <= n <= 9; `row` is HOST memory of length (n-2)!. */
+bg_status bg_colormat_row_host(int n, double* row);
+
+/* ---------------------------------------------------------------------------
+ * bg_momenta_rambo -- Rambo flat massless phase space (Sec. 3; Kleiss,
+ * Stirling, Ellis), FP64.
+ *   u       [B][4(n-2)]  uniforms in (0,1): per final-state gluon i,
+ *                        u[e][4i+0..3] = (cos-theta, phi, energy, energy)
+ *                        variables of the Rambo construction.
+ *   p       [4][n][B]    output lab momenta (component, gluon, event);
+ *                        p1 = (E,0,0,E), p2 = (E,0,0,-E), E = sqrt_s/2.
+ *   accept  [B] or NULL  output 1 if every final-state gluon has
+ *                        pT > pt_min (Sec. 5 cut), else 0.
+ * Errors: BG_EINVAL (n outside 4..12, B < 0, NULL u/p, sqrt_s <= 0).
+ * B = 0 is a no-op.
+ * ------------------------------------------------------------------------- */
+bg_status bg_momenta_rambo(int n, int64_t B, double sqrt_s, const double* u, double* p, double pt_min,
+                           uint8_t* accept, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * bg_currents_co -- colour-ordered Berends-Giele currents, Eqs. (2.20)-(2.22),
+ * for every ordering sigma in S_{n-2}: A(1, sigma_2..sigma_{n-1}, n).
+ *   p       [4][n][B]    lab momenta (as written by bg_momenta_rambo).
+ *   hel     [n][B] int8  helicity labels +-1 (sampled helicities), or NULL
+ *                        to evaluate all H = 2^n polarisation configurations
+ *                        (configuration h: gluon i takes label -1 iff bit i
+ *                        of h is set).
+ *   q       [4] HOST     light-like reference vector with q0 > 0.
+ *   prec                 BG_F32: currents in FP32 (polarisations built in
+ *                        FP64); BG_F64: all FP64.
+ *   amps    [B][H][k]    output, float or double per prec, k = (n-2)!,
+ *                        orderings lexicographic.  Amplitudes carry unit
+ *                        coupling (g_s = 1) and are in units of sqrt_s:
+ *                        A[GeV^(4-n)] = amps * sqrt_s^(4-n).
+ * Momenta are divided by sqrt_s before the recursion (FP32 range).
+ * Supported: 4 <= n <= 9.  Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_currents_co(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                         bg_prec prec, void* amps, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * bg_color_sum -- |M|^2 = g_s^(2n-4) sqrt_s^(8-2n) w sum_h sum_{s,s'}
+ * C_{s s'} A_{h s} A_{h s'}, Eq. (2.16), with w = 2^n if hel_sampled (one
+ * sampled polarisation configuration per event, H = 1) else 1.
+ *   amps    [B][H][k]    as written by bg_currents_co (amp_prec its type).
+ *   accept  [B] or NULL  events with accept == 0 get |M|^2 = 0.
+ *   me2     [B] double   output in GeV^(8-2n).
+ * mode BG_CS_F64 accumulates in FP64; BG_CS_F32 forms C A in FP32 (C's
+ * integer entries are exact in FP32) and accumulates the quadratic form
+ * per event in FP64.
+ * Errors: BG_EINVAL (NULL C/amps/me2, B < 0, H < 1), BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps, bg_prec amp_prec,
+                       bg_cs_mode mode, double g_s, double sqrt_s, int hel_sampled, const uint8_t* accept,
+                       double* me2, void* stream);
+
+/* Device status word of the current device: 0 if no kernel has seen an
+ * invalid label since the last reset, else a BG_* code.  Synchronises the
+ * device.  bg_device_status_reset clears it. */
+bg_status bg_device_status(int* status);
+bg_status bg_device_status_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BG_H */

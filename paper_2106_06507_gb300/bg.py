@@ -1,0 +1,177 @@
+"""Thin ctypes binding of libbg.so (include/bg.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Tensors are torch CUDA tensors (device memory and
+streams come from PyTorch); the calls enqueue work on the current torch
+stream unless `stream` is given.  Raises if the library is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbg.so")
+
+BG_OK, BG_EINVAL, BG_ENOMEM, BG_ECUDA, BG_EUNSUPPORTED, BG_ETIMEOUT = range(6)
+BG_F64, BG_F32 = 0, 1
+BG_CS_F64, BG_CS_F32 = 0, 1
+BG_COL_ADJOINT, BG_COL_FLOW = 0, 1
+
+G_S_DEFAULT = math.sqrt(4.0 * math.pi * 0.118)  # alpha_s = 0.118
+DEFAULT_Q = (1.0, 0.0, 0.0, 1.0)
+
+_lib = None
+
+
+class BGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bg status {code}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbg.so (built by build_lib.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbg.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        c_int, c_dbl, c_i64, vp = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.bg_last_error.restype = ctypes.c_char_p
+        L.bg_num_orderings.argtypes = [c_int]
+        L.bg_num_orderings.restype = c_i64
+        L.bg_colormat_create.argtypes = [c_int, ctypes.POINTER(vp)]
+        L.bg_colormat_destroy.argtypes = [vp]
+        L.bg_colormat_destroy.restype = None
+        L.bg_colormat_row.argtypes = [vp, dp]
+        L.bg_colormat_row_host.argtypes = [c_int, dp]
+        L.bg_momenta_rambo.argtypes = [c_int, c_i64, c_dbl, vp, vp, c_dbl, vp, vp]
+        L.bg_currents_co.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, vp, vp]
+        L.bg_color_sum.argtypes = [vp, c_i64, c_int, vp, c_int, c_int, c_dbl, c_dbl, c_int, vp, vp, vp]
+        L.bg_device_status.argtypes = [ctypes.POINTER(c_int)]
+        L.bg_device_status_reset.argtypes = []
+        for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
+                     "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset"):
+            getattr(L, name).restype = c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int) -> None:
+    if code != BG_OK:
+        raise BGError(code, lib().bg_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _q(q) -> ctypes.Array:
+    return (ctypes.c_double * 4)(*[float(x) for x in q])
+
+
+def num_orderings(n: int) -> int:
+    return int(lib().bg_num_orderings(n))
+
+
+class ColourMatrix:
+    """Device colour matrix of Eq. (2.17) (library-owned; freed on close)."""
+
+    def __init__(self, n: int):
+        self.n = n
+        self.k = num_orderings(n)
+        h = ctypes.c_void_p()
+        _check(lib().bg_colormat_create(n, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def row(self):
+        import numpy as np
+        out = np.zeros(self.k)
+        _check(lib().bg_colormat_row(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().bg_colormat_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def colour_row_host(n: int):
+    import numpy as np
+    out = np.zeros(math.factorial(n - 2))
+    _check(lib().bg_colormat_row_host(n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def momenta_rambo(n: int, u: torch.Tensor, sqrt_s: float = 1000.0, pt_min: float = -1.0, p=None, accept=None,
+                  stream=None):
+    """u [B, 4(n-2)] float64 CUDA -> (p [4, n, B] float64, accept [B] uint8)."""
+    B = u.shape[0]
+    assert u.dtype == torch.float64 and u.is_cuda and u.is_contiguous()
+    if p is None:
+        p = torch.empty((4, n, B), dtype=torch.float64, device=u.device)
+    if accept is None:
+        accept = torch.empty((B,), dtype=torch.uint8, device=u.device)
+    _check(lib().bg_momenta_rambo(n, B, sqrt_s, _ptr(u), _ptr(p), pt_min, _ptr(accept), _stream(stream)))
+    return p, accept
+
+
+def currents_co(n: int, p: torch.Tensor, hel: torch.Tensor | None = None, q=DEFAULT_Q, prec: int = BG_F32,
+                sqrt_s: float = 1000.0, amps=None, stream=None) -> torch.Tensor:
+    """p [4, n, B] float64, hel [n, B] int8 or None (all 2^n configurations)
+    -> amps [B, H, (n-2)!] (float32 or float64)."""
+    B = p.shape[2]
+    H = 1 if hel is not None else 2**n
+    k = num_orderings(n)
+    dt = torch.float32 if prec == BG_F32 else torch.float64
+    if amps is None:
+        amps = torch.empty((B, H, k), dtype=dt, device=p.device)
+    if hel is not None:
+        assert hel.dtype == torch.int8 and hel.is_contiguous() and tuple(hel.shape) == (n, B)
+    _check(lib().bg_currents_co(n, B, sqrt_s, _ptr(p), _ptr(hel), _q(q), prec, _ptr(amps), _stream(stream)))
+    return amps
+
+
+def color_sum(C: ColourMatrix, amps: torch.Tensor, hel_sampled: bool, mode: int = BG_CS_F64,
+              g_s: float = G_S_DEFAULT, sqrt_s: float = 1000.0, accept: torch.Tensor | None = None, me2=None,
+              stream=None) -> torch.Tensor:
+    """amps [B, H, k] -> me2 [B] float64 (GeV^(8-2n))."""
+    B, H, k = amps.shape
+    assert k == C.k and amps.is_contiguous()
+    prec = BG_F32 if amps.dtype == torch.float32 else BG_F64
+    if me2 is None:
+        me2 = torch.empty((B,), dtype=torch.float64, device=amps.device)
+    _check(lib().bg_color_sum(C.handle, B, H, _ptr(amps), prec, mode, g_s, sqrt_s, int(bool(hel_sampled)),
+                              _ptr(accept), _ptr(me2), _stream(stream)))
+    return me2
+
+
+def device_status() -> int:
+    s = ctypes.c_int(0)
+    _check(lib().bg_device_status(ctypes.byref(s)))
+    return s.value
+
+
+def device_status_reset() -> None:
+    _check(lib().bg_device_status_reset())

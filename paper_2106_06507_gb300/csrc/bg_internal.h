@@ -1,0 +1,69 @@
+// bg_internal.h -- declarations shared by the translation units of libbg.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bg.h"
+
+namespace bg {
+
+// Thread-local last-error message (bg_last_error).
+void set_error(const std::string& msg);
+bg_status fail(bg_status code, const std::string& msg);
+bg_status cuda_check(cudaError_t e, const char* what);
+
+constexpr int kMaxN = 12;
+constexpr int kMaxNCO = 9;  // colour-ordered path: (n-2)! orderings
+
+int64_t factorial(int m);
+
+// Host colour-matrix generator (colormat.cpp).
+// First row C[id][tau] of Eq. (2.17), tau in lexicographic order.
+void colour_row(int n, std::vector<double>& row);
+// Lexicographic rank of a permutation of 0..m-1.
+int64_t perm_rank(const int* perm, int m);
+// Dense matrix from the row: C[s][t] = row[rank(sigma_s^-1 o sigma_t)].
+void colour_dense(int n, const std::vector<double>& row, std::vector<double>& dense);
+
+// Device status word (api.cu).
+int* device_status_ptr();
+
+// Kernel launchers (one per .cu file).
+cudaError_t launch_rambo(int n, int64_t B, double sqrt_s, const double* u, double* p, double pt_min,
+                         uint8_t* accept, cudaStream_t s);
+
+cudaError_t launch_co_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                          float* amps, int* status, cudaStream_t s);
+cudaError_t launch_co_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                          double* amps, int* status, cudaStream_t s);
+
+struct ColourSumArgs {
+  int n;
+  int64_t B;
+  int H;
+  int k;
+  const void* amps;
+  bool amps_f32;
+  const double* C64;  // [k][k]
+  const float* C32;   // [k][k]
+  double scale;       // g^(2n-4) sqrt_s^(8-2n) w
+  const uint8_t* accept;
+  double* me2;
+};
+cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
+cudaError_t launch_color_sum_f32(const ColourSumArgs& a, cudaStream_t s);
+
+}  // namespace bg
+
+struct bg_colormat {
+  int n;
+  int k;
+  int device;
+  std::vector<double> row;  // host copy of the first row
+  double* C64;              // device [k][k]
+  float* C32;               // device [k][k]
+};

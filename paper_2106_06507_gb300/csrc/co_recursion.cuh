@@ -1,0 +1,323 @@
+// co_recursion.cuh -- colour-ordered Berends-Giele currents on the GPU,
+// Eqs. (2.20)-(2.22) of the paper, for every ordering sigma in S_{n-2} of
+// the adjoint basis, Eq. (2.15).
+//
+// Work decomposition: one thread per (event, polarisation configuration,
+// ordering).  A block takes a tile of EB events chosen so that the
+// EB * H * (n-2)! tasks fill whole rounds of the 256 threads.  Per event the
+// block first builds, in FP64, the scaled momenta, the polarisation vectors
+// (Eq. 2.7) and a table of inverse propagators 1/P(S)^2 for every subset S of
+// the first n-1 gluons (from the pair invariants 2 k_a.k_b, so that nearly
+// collinear subsets keep full precision), and stores them in shared memory
+// in the recursion's arithmetic type T.  Each thread then runs the whole
+// recursion of its ordering in registers: the current table J(i..j) is fully
+// unrolled at compile time for the given n.
+//
+// Arithmetic per segment (i..j) of the ordering, with X_s = J(i..s),
+// Y_s = J(s+1..j), P = P(i..j) and unit vertex factors (the couplings
+// 1/sqrt2 per three-vertex and 1/2 per four-vertex combine to
+// (1/sqrt2)^(n-2) per amplitude, applied once at the end):
+//   V3 terms (Eq. 2.21): with current conservation P_s.X_s = 0 and
+//   Q_s.Y_s = 0 the vertex becomes
+//     (X_s.Y_s)(P_s - Q_s) + 2 (P.X_s) Y_s - 2 (P.Y_s) X_s,
+//   and sum_s (X_s.Y_s)(P_s - Q_s) = 2 sum_s (X_s.Y_s) S_{s+1}
+//                                   - (sum_s X_s.Y_s)(S_i + S_{j+1})
+//   with prefix sums S of the ordered momenta.
+//   V4 terms (Eq. 2.21): 2(X.Z)Y - (X.Y)Z - (Y.Z)X with X = J(i..s),
+//   Y = J(s+1..t), Z = J(t+1..j); the X and Z parts are collected as scalar
+//   coefficients of J(i..s) and J(t+1..j) and applied once per split.
+//   Propagator: J(i..j) = bracket / P(i..j)^2; the full segment is put on
+//   shell and contracted with the last gluon's polarisation (Eq. 2.22).
+#pragma once
+
+#include "bg_internal.h"
+#include "device_common.cuh"
+
+namespace bg {
+
+struct Q4 {
+  double v[4];
+};
+
+__host__ __device__ constexpr int ct_fact(int m) { return m <= 1 ? 1 : m * ct_fact(m - 1); }
+__host__ __device__ constexpr int ct_gcd(int a, int b) { return b == 0 ? a : ct_gcd(b, a % b); }
+
+template <int N, bool SUMHEL>
+struct CoShape {
+  static constexpr int NT = 256;                    // threads per block
+  static constexpr int M = N - 1;                   // legs of the off-shell current
+  static constexpr int K = ct_fact(N - 2);          // orderings
+  static constexpr int H = SUMHEL ? (1 << N) : 1;   // polarisation configurations
+  static constexpr int TPE = K * H;                 // tasks per event
+  static constexpr int EB0 = NT / ct_gcd(NT, TPE);  // events per block: EB*TPE % NT == 0
+  static constexpr int EB = EB0 > 128 ? 128 : EB0;
+  static constexpr int NPOL = SUMHEL ? 2 : 1;
+  static constexpr int NMASK = 1 << M;
+  static constexpr int NPAIR = M * (M - 1) / 2;
+};
+
+template <int N, typename T, bool SUMHEL>
+struct CoSmem {
+  using S = CoShape<N, SUMHEL>;
+  static constexpr size_t off_pair = 0;                                                   // double [EB][NPAIR]
+  static constexpr size_t off_inv = off_pair + sizeof(double) * S::EB * S::NPAIR;          // T [EB][NMASK]
+  static constexpr size_t off_k = off_inv + sizeof(T) * S::EB * S::NMASK;                  // T [EB][N][4]
+  static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                       // T [EB][NPOL][N][4]
+  static constexpr size_t off_ord = off_e + sizeof(T) * S::EB * S::NPOL * N * 4;           // int [K]
+  static constexpr size_t bytes = off_ord + sizeof(int) * S::K;
+};
+
+// Recursion for one ordering; J[i][i] hold the external currents in colour
+// order, Sp[p] the prefix sums of the ordered momenta, msk[p] the prefix
+// subset masks, inv the event's inverse-propagator table, en the last
+// gluon's polarisation.  Returns the amplitude with unit vertex factors.
+template <int N, typename T>
+__device__ __forceinline__ T co_recursion(T (&J)[N - 1][N - 1][4], const T (&Sp)[N][4], const int (&msk)[N],
+                                          const T* __restrict__ inv, const T (&en)[4]) {
+  constexpr int M = N - 1;
+  T amp = T(0);
+#pragma unroll
+  for (int len = 2; len <= M; ++len) {
+#pragma unroll
+    for (int i = 0; i + len - 1 < M; ++i) {
+      const int j = i + len - 1;
+      T P2[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) P2[m] = T(2) * (Sp[j + 1][m] - Sp[i][m]);
+      T br[4], by[4], W[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) { br[m] = T(0); by[m] = T(0); W[m] = T(0); }
+      T sxy = T(0);
+      T cX[M], cR[M];
+#pragma unroll
+      for (int s = i; s < j; ++s) {
+        const T xy = mdot(J[i][s], J[s + 1][j]);
+        const T px = mdot(P2, J[i][s]);
+        const T py = mdot(P2, J[s + 1][j]);
+        sxy += xy;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) W[m] = fma(xy, Sp[s + 1][m], W[m]);
+        cX[s] = -py;
+        cR[s] = px;
+      }
+#pragma unroll
+      for (int s = i; s < j; ++s) {
+#pragma unroll
+        for (int t = s + 1; t < j; ++t) {
+          const T xz = mdot(J[i][s], J[t + 1][j]);
+          const T xy = mdot(J[i][s], J[s + 1][t]);
+          const T yz = mdot(J[s + 1][t], J[t + 1][j]);
+          cX[s] -= yz;
+          cR[t] -= xy;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) by[m] = fma(xz, J[s + 1][t][m], by[m]);
+        }
+      }
+#pragma unroll
+      for (int s = i; s < j; ++s) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) br[m] = fma(cX[s], J[i][s][m], fma(cR[s], J[s + 1][j][m], br[m]));
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) br[m] += T(2) * (W[m] + by[m]) - sxy * (Sp[i][m] + Sp[j + 1][m]);
+      if (len < M) {
+        const T ip = inv[msk[j + 1] ^ msk[i]];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) J[i][j][m] = br[m] * ip;
+      } else {
+        amp = mdot(en, br);
+      }
+    }
+  }
+  return amp;
+}
+
+template <int N, typename T, bool SUMHEL>
+__global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, const double* __restrict__ p,
+                                                 const int8_t* __restrict__ hel, Q4 q, T* __restrict__ amps,
+                                                 int* __restrict__ status) {
+  using S = CoShape<N, SUMHEL>;
+  using L = CoSmem<N, T, SUMHEL>;
+  constexpr int M = S::M, K = S::K, H = S::H, EB = S::EB, NPOL = S::NPOL;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* s_pair = reinterpret_cast<double*>(smem + L::off_pair);
+  T* s_inv = reinterpret_cast<T*>(smem + L::off_inv);
+  T* s_k = reinterpret_cast<T*>(smem + L::off_k);
+  T* s_e = reinterpret_cast<T*>(smem + L::off_e);
+  int* s_ord = reinterpret_cast<int*>(smem + L::off_ord);
+
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int tid = threadIdx.x;
+
+  // ---- phase 1a: ordering table (packed 4-bit labels), momenta, polarisations
+  for (int r = tid; r < K; r += S::NT) {
+    int avail = (1 << (N - 2)) - 1;
+    int rr = r, packed = 0;
+#pragma unroll
+    for (int pos = 0; pos < N - 2; ++pos) {
+      const int f = ct_fact(N - 3 - pos);
+      const int d = rr / f;
+      rr -= d * f;
+      int lab = 0, cnt = -1;
+#pragma unroll
+      for (int b = 0; b < N - 2; ++b) {
+        const bool on = (avail >> b) & 1;
+        cnt += on ? 1 : 0;
+        if (on && cnt == d) lab = b;
+      }
+      avail &= ~(1 << lab);
+      packed |= (lab + 1) << (4 * pos);  // gluon index 1..N-2
+    }
+    s_ord[r] = packed;
+  }
+  for (int it = tid; it < EB * N; it += S::NT) {
+    const int el = it / N, g = it % N;
+    const int64_t e = e0 + el;
+    if (e >= B) continue;
+    double k[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * B + e] * inv_sqrt_s;
+    if (g < 2) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) k[m] = -k[m];
+    }
+    double e1[4], e2[4];
+    lc_polarisations(k, q.v, e1, e2);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) s_k[(el * N + g) * 4 + m] = T(k[m]);
+    if (SUMHEL) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        s_e[((el * 2 + 0) * N + g) * 4 + m] = T(e1[m]);
+        s_e[((el * 2 + 1) * N + g) * 4 + m] = T(e2[m]);
+      }
+    } else {
+      const int h = hel[(int64_t)g * B + e];
+      if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
+      const double* ev = (h < 0) ? e2 : e1;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) s_e[(el * N + g) * 4 + m] = T(ev[m]);
+    }
+  }
+  // pair invariants 2 k_a.k_b (FP64) among the first M gluons
+  for (int it = tid; it < EB * S::NPAIR; it += S::NT) {
+    const int el = it / S::NPAIR;
+    int pr = it % S::NPAIR;
+    const int64_t e = e0 + el;
+    if (e >= B) continue;
+    int a = 0;
+    while (pr >= M - 1 - a) { pr -= M - 1 - a; ++a; }
+    const int b = a + 1 + pr;
+    double ka[4], kb[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      ka[m] = p[((int64_t)m * N + a) * B + e];
+      kb[m] = p[((int64_t)m * N + b) * B + e];
+    }
+    // both beams or neither flipped -> +, one flipped -> - (k = -p for gluons 1, 2)
+    const double sgn = ((a < 2) != (b < 2)) ? -1.0 : 1.0;
+    s_pair[el * S::NPAIR + it % S::NPAIR] =
+        sgn * 2.0 * (ka[0] * kb[0] - ka[1] * kb[1] - ka[2] * kb[2] - ka[3] * kb[3]) * inv_sqrt_s * inv_sqrt_s;
+  }
+  __syncthreads();
+  // ---- phase 1b: inverse propagators for every subset of the first M gluons
+  for (int it = tid; it < EB * S::NMASK; it += S::NT) {
+    const int el = it / S::NMASK, mask = it % S::NMASK;
+    if (e0 + el >= B) continue;
+    double p2 = 0.0;
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+#pragma unroll
+      for (int b = a + 1; b < M; ++b) {
+        if (((mask >> a) & 1) && ((mask >> b) & 1)) p2 += s_pair[el * S::NPAIR + idx];
+        ++idx;
+      }
+    }
+    s_inv[el * S::NMASK + mask] = (__popc(mask) >= 2 && mask != S::NMASK - 1) ? T(1) / T(p2) : T(0);
+  }
+  __syncthreads();
+
+  // ---- phase 2: one ordering (and polarisation configuration) per thread
+  constexpr int TOTAL = EB * S::TPE;
+  const T vfac = T(1.0 / double(1 << ((N - 2) / 2)) * (((N - 2) & 1) ? 0.70710678118654752440 : 1.0));
+  for (int t = tid; t < TOTAL; t += S::NT) {
+    const int el = t / S::TPE;
+    const int rem = t - el * S::TPE;
+    const int h = rem / K;
+    const int r = rem - h * K;
+    const int64_t e = e0 + el;
+    if (e >= B) continue;
+    const int packed = s_ord[r];
+    int gl[N];
+    gl[0] = 0;
+#pragma unroll
+    for (int pos = 1; pos < N - 1; ++pos) gl[pos] = (packed >> (4 * (pos - 1))) & 15;
+    gl[N - 1] = N - 1;
+    const T* ke = s_k + el * N * 4;
+    T J[M][M][4];
+    T Sp[N][4];
+    int msk[N];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Sp[0][m] = T(0);
+    msk[0] = 0;
+#pragma unroll
+    for (int pos = 0; pos < M; ++pos) {
+      const int g = gl[pos];
+      const int pol = SUMHEL ? ((h >> g) & 1) : 0;
+      const T* ev = s_e + ((el * NPOL + pol) * N + g) * 4;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        J[pos][pos][m] = ev[m];
+        Sp[pos + 1][m] = Sp[pos][m] + ke[g * 4 + m];
+      }
+      msk[pos + 1] = msk[pos] | (1 << g);
+    }
+    T en[4];
+    {
+      const int pol = SUMHEL ? ((h >> (N - 1)) & 1) : 0;
+      const T* ev = s_e + ((el * NPOL + pol) * N + (N - 1)) * 4;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) en[m] = ev[m];
+    }
+    const T a = co_recursion<N, T>(J, Sp, msk, s_inv + el * S::NMASK, en);
+    amps[(e * H + h) * (int64_t)K + r] = a * vfac;
+  }
+}
+
+template <int N, typename T, bool SUMHEL>
+cudaError_t launch_co_n(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
+                        int* status, cudaStream_t s) {
+  using S = CoShape<N, SUMHEL>;
+  using L = CoSmem<N, T, SUMHEL>;
+  auto kern = co_kernel<N, T, SUMHEL>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  if (err != cudaSuccess) return err;
+  Q4 qq;
+  for (int m = 0; m < 4; ++m) qq.v[m] = q[m];
+  const int64_t blocks = (B + S::EB - 1) / S::EB;
+  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, 1.0 / sqrt_s, p, hel, qq, amps, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                        T* amps, int* status, cudaStream_t s) {
+  const bool sum = (hel == nullptr);
+#define BG_CO_CASE(NN)                                                            \
+  case NN:                                                                        \
+    return sum ? launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s) \
+               : launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s);
+  switch (n) {
+    BG_CO_CASE(4)
+    BG_CO_CASE(5)
+    BG_CO_CASE(6)
+    BG_CO_CASE(7)
+    BG_CO_CASE(8)
+    BG_CO_CASE(9)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BG_CO_CASE
+}
+
+}  // namespace bg

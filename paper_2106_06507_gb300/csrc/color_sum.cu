@@ -1,0 +1,123 @@
+// color_sum.cu -- the colour sum of Eq. (2.16) on CUDA cores:
+//   |M|^2_e = scale * sum_h sum_{a,b} C_ab A_{e h a} A_{e h b}
+// evaluated as a tiled product Y = C A_e (C symmetric, so column b of C is
+// row b) followed by the per-event contraction sum_a A_{e h a} Y_{a e},
+// all inside one kernel.  A block owns a tile of 64 events and walks all
+// row tiles of C, so each event's quadratic form is finished in registers
+// and written once (no atomics, no scratch memory, deterministic order).
+// TC is the arithmetic type of C A; the per-event sum is accumulated in FP64.
+#include "bg_internal.h"
+#include "device_common.cuh"
+
+namespace bg {
+namespace {
+
+constexpr int TA = 64;   // rows of C per tile
+constexpr int TE = 64;   // events per block
+constexpr int KT = 16;   // reduction step
+constexpr int NT = 256;  // threads: 16 x 16, each 4 rows x 4 events
+
+template <typename TIn, typename TC>
+__global__ void __launch_bounds__(NT) color_sum_kernel(int64_t B, int H, int k, const TIn* __restrict__ A,
+                                                       const TC* __restrict__ C, double scale,
+                                                       const uint8_t* __restrict__ accept,
+                                                       double* __restrict__ me2) {
+  __shared__ __align__(16) TC Cs[KT][TA];
+  __shared__ __align__(16) TC As[KT][TE];
+  __shared__ double red[16][TE];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;   // event group (4 events)
+  const int ty = tid >> 4;   // row group (4 rows)
+  const int64_t e0 = (int64_t)blockIdx.x * TE;
+  const int64_t strideE = (int64_t)H * k;
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+
+  for (int h = 0; h < H; ++h) {
+    for (int a0 = 0; a0 < k; a0 += TA) {
+      TC acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = TC(0);
+      for (int b0 = 0; b0 < k; b0 += KT) {
+        // C tile: Cs[kk][r] = C[b0+kk][a0+r]   (1024 elements, 4 per thread)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const int idx = tid + l * NT;
+          const int kk = idx / TA, r = idx % TA;
+          const int b = b0 + kk, a = a0 + r;
+          Cs[kk][r] = (b < k && a < k) ? C[(int64_t)b * k + a] : TC(0);
+        }
+        // A tile: As[kk][c] = A[e0+c][h][b0+kk]
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const int idx = tid + l * NT;
+          const int c = idx / KT, kk = idx % KT;
+          const int b = b0 + kk;
+          const int64_t e = e0 + c;
+          As[kk][c] = (b < k && e < B) ? TC(A[e * strideE + (int64_t)h * k + b]) : TC(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+          TC cv[4], av[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) cv[i] = Cs[kk][ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) av[j] = As[kk][tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(cv[i], av[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+      // contract with A at the tile's rows: part_e += sum_a A_{e a} Y_{a e}
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t e = e0 + tx * 4 + j;
+        if (e >= B) continue;
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int a = a0 + ty * 4 + i;
+          if (a < k) s += (double)A[e * strideE + (int64_t)h * k + a] * (double)acc[i][j];
+        }
+        part[j] += s;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) red[ty][tx * 4 + j] = part[j];
+  __syncthreads();
+  if (tid < TE) {
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) s += red[r][tid];
+    const int64_t e = e0 + tid;
+    if (e < B) {
+      const bool ok = (accept == nullptr) || (accept[e] != 0);
+      me2[e] = ok ? scale * s : 0.0;
+    }
+  }
+}
+
+template <typename TIn, typename TC>
+cudaError_t launch_cs(const ColourSumArgs& a, const TC* C, cudaStream_t s) {
+  const int64_t blocks = (a.B + TE - 1) / TE;
+  color_sum_kernel<TIn, TC><<<(unsigned)blocks, NT, 0, s>>>(a.B, a.H, a.k, static_cast<const TIn*>(a.amps), C,
+                                                           a.scale, a.accept, a.me2);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s) {
+  return a.amps_f32 ? launch_cs<float, double>(a, a.C64, s) : launch_cs<double, double>(a, a.C64, s);
+}
+
+cudaError_t launch_color_sum_f32(const ColourSumArgs& a, cudaStream_t s) {
+  return a.amps_f32 ? launch_cs<float, float>(a, a.C32, s) : launch_cs<double, float>(a, a.C32, s);
+}
+
+}  // namespace bg

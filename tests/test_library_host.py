@@ -1,0 +1,85 @@
+"""Host-side checks of libbg.so that need no GPU: the library builds for
+sm_103a, loads, exports every symbol declared in include/bg.h, and its host
+colour-matrix generator (U(N) loop counting) agrees with the oracle's
+explicit SU(3) contraction."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libbg():
+    from paper_2106_06507_gb300 import build_lib
+    path = build_lib.build()
+    return ctypes.CDLL(path)
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(bg_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("bg_momenta_rambo", "bg_currents_co", "bg_color_sum", "bg_colormat_create"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libbg):
+    missing = [n for n in declared_symbols() if not hasattr(libbg, n)]
+    assert not missing, missing
+
+
+def test_num_orderings(libbg):
+    libbg.bg_num_orderings.restype = ctypes.c_int64
+    assert [libbg.bg_num_orderings(n) for n in range(3, 14)] == [0, 2, 6, 24, 120, 720, 5040, 40320, 362880,
+                                                                  3628800, 0]
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+def test_library_colour_row_matches_oracle(libbg, oracle, n):
+    import math
+    row = np.zeros(math.factorial(n - 2))
+    rc = libbg.bg_colormat_row_host(n, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert rc == 0
+    assert np.array_equal(row, np.round(row))
+    assert np.allclose(row, oracle.colour_row(n), rtol=0, atol=1e-6)
+
+
+def test_library_colour_row_n9_closed_forms(libbg):
+    # n = 9 has no explicit-contraction golden row (8^9 terms per entry); check
+    # the closed-form diagonal 8 (2N)^(n-2), integrality and the BF16-exactness
+    # of the entries scaled by their gcd.
+    row = np.zeros(5040)
+    assert libbg.bg_colormat_row_host(9, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+    assert row[0] == 8 * 6**7
+    assert np.array_equal(row, np.round(row))
+    g = np.gcd.reduce(np.abs(row).astype(np.int64))
+    assert g == 432
+    assert row.sum() != 0
+
+
+def test_argument_errors_without_gpu(libbg):
+    libbg.bg_last_error.restype = ctypes.c_char_p
+    vp = ctypes.c_void_p
+    libbg.bg_momenta_rambo.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, vp, vp, ctypes.c_double, vp,
+                                       vp]
+    assert libbg.bg_momenta_rambo(3, 10, 1000.0, None, None, 0.0, None, None) == 1
+    assert b"n must be" in libbg.bg_last_error()
+    assert libbg.bg_momenta_rambo(5, -1, 1000.0, None, None, 0.0, None, None) == 1
+    assert libbg.bg_momenta_rambo(5, 0, 1000.0, None, None, 0.0, None, None) == 0  # empty batch is a no-op
+    assert libbg.bg_momenta_rambo(5, 10, 1000.0, None, None, 0.0, None, None) == 1
+    row = np.zeros(10)
+    assert libbg.bg_colormat_row_host(10, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
