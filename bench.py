@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Throughput of the colour-ordered Berends-Giele hot path on GB300.
+
+Workload (one "step"): for each multiplicity n = 5, 6, 7, 8 gluons, one batch
+of 2^20 Rambo phase-space points at sqrt(s) = 1 TeV with a final-state
+pT > 20 GeV cut, one sampled helicity configuration per event, FP32
+colour-ordered currents for all (n-2)! orderings, and the full colour sum
+A^T C A with the exact SU(3) colour matrix; FP64 Rambo and FP64 per-event
+accumulation.  Metric: events/s (all generated events of all four
+multiplicities; per-n figures are in "per_n").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  N > 1 runs under torch.distributed.run, one
+process per GPU, each with its own events (weak scaling, no collective on the
+data path; a barrier and a max-reduction of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NS = (5, 6, 7, 8)
+BATCH = 1 << 20
+SQRT_S = 1000.0
+PT_MIN = 20.0
+SEED = 0
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+MAX_SM_MHZ = 2070.0
+L2_BYTES = 129 * 1024 * 1024
+
+WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqrt(s)=1 TeV, pT>20 GeV, "
+            "sampled helicities, FP32 currents for all (n-2)! orderings, exact colour sum A^T C A")
+
+# DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
+# n = 8, 2^20 events), valid only for the kernel sources it was taken from.
+NCU_TRAFFIC = {"sources_sha1": None, "bytes_per_launch": None}
+DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
+                    "paper_2106_06507_gb300/csrc/device_common.cuh")
+
+
+def canonical_recursion_flops(n: int) -> int:
+    """Canonical FLOPs per event of the colour-ordered recursion (all (n-2)!
+    orderings, one polarisation configuration): V3 = 65, V4 = 46,
+    propagator = 12, final contraction = 7 per ordering."""
+    per_order = 65 * math.comb(n, 3) + 46 * math.comb(n, 4) + 12 * math.comb(n - 1, 2) + 7
+    return math.factorial(n - 2) * per_order
+
+
+def colour_sum_flops(n: int) -> int:
+    k = math.factorial(n - 2)
+    return 2 * k * k + 2 * k
+
+
+def sources_sha1() -> str:
+    h = hashlib.sha1()
+    for rel in DOMINANT_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (host logic; covered by a gloo test on CPU)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+CPU_SAMPLE = {5: 1 << 20, 6: 1 << 19, 7: 1 << 17, 8: 1 << 15}
+REF_STEP_SAMPLE = {5: 1 << 16, 6: 1 << 14, 7: 1 << 12, 8: 1 << 10}
+
+
+def oracle_rates(sample: dict) -> tuple[dict, int, float]:
+    """events/s of the oracle per n on `sample[n]` events (all host cores)."""
+    from oracle import oracle as O
+    from paper_2106_06507_gb300 import inputs
+    rates = {}
+    total = 0.0
+    for n in NS:
+        B = sample[n]
+        u = inputs.rambo_uniforms(n, B, seed=SEED + 1)
+        hel = inputs.helicities(n, B, seed=SEED + 1)
+        O.colour_matrix(n)
+        t0 = time.perf_counter()
+        O.me2_co(n, u, sqrt_s=SQRT_S, hel=hel, pt_min=PT_MIN)
+        dt = time.perf_counter() - t0
+        rates[n] = B / dt
+        total += dt
+    return rates, O.n_cores(), total
+
+
+def aggregate_rate(rates: dict, batch: int = BATCH) -> float:
+    """events/s of a step (batch events of every n) from per-n rates."""
+    t = sum(batch / rates[n] for n in NS)
+    return len(NS) * batch / t
+
+
+def cpu_baseline() -> dict:
+    rates, cores, secs = oracle_rates(CPU_SAMPLE)
+    return {"value": aggregate_rate(rates), "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": ("FP64 C++ oracle, all host threads, per n: "
+                       + ", ".join(f"n={n}: {CPU_SAMPLE[n]} events" for n in NS)
+                       + f" of the same workload ({secs:.1f} s); value = events/s of the full step "
+                       "extrapolated from the per-n rates"),
+            "per_n": {str(n): rates[n] for n in NS}}
+
+
+def run_reference(args) -> None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_rates(REF_STEP_SAMPLE)
+    step_rates = []
+    t_total = 0.0
+    for _ in range(args.steps):
+        rates, cores, secs = oracle_rates(REF_STEP_SAMPLE)
+        step_rates.append(rates)
+        t_total += secs
+    per_n = {n: statistics.median(r[n] for r in step_rates) for n in NS}
+    value = aggregate_rate(per_n)
+    sample = ("FP64 C++ oracle on all host threads, each step per n: "
+              + ", ".join(f"n={n}: {REF_STEP_SAMPLE[n]} events" for n in NS)
+              + "; value = events/s of the full step extrapolated from the per-n rates")
+    print(json.dumps({
+        "impl": "reference", "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(NS) * BATCH / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S,
+                   "pt_min_gev": PT_MIN},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "per_n": {str(n): per_n[n] for n in NS},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2106_06507_gb300 import bg, build_lib, inputs
+    build_lib.build()
+    bg.lib()
+
+    stream = torch.cuda.current_stream(dev)
+    # inputs: resident in HBM before the timed region; each rank its own events
+    first = rank * BATCH
+    U, HEL, P, ACC, AMPS, ME2, CM = {}, {}, {}, {}, {}, {}, {}
+    h2d = 0
+    for n in NS:
+        u = inputs.rambo_uniforms(n, BATCH, seed=SEED, first_event=first)
+        h = np.ascontiguousarray(inputs.helicities(n, BATCH, seed=SEED, first_event=first).T)
+        U[n] = torch.from_numpy(u).to(dev)
+        HEL[n] = torch.from_numpy(h).to(dev)
+        P[n] = torch.empty((4, n, BATCH), dtype=torch.float64, device=dev)
+        ACC[n] = torch.empty((BATCH,), dtype=torch.uint8, device=dev)
+        AMPS[n] = torch.empty((BATCH, 1, math.factorial(n - 2)), dtype=torch.float32, device=dev)
+        ME2[n] = torch.empty((BATCH,), dtype=torch.float64, device=dev)
+        CM[n] = bg.ColourMatrix(n)
+        h2d += u.nbytes + h.nbytes
+    input_bytes = sum(U[n].numel() * 8 for n in NS)
+
+    ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(4)] for n in NS}
+    launches_per_step = 3 * len(NS)
+
+    def step(record: bool):
+        for n in NS:
+            if record:
+                ev[n][0].record(stream)
+            bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            if record:
+                ev[n][1].record(stream)
+            bg.currents_co(n, P[n], HEL[n], prec=bg.BG_F32, sqrt_s=SQRT_S, amps=AMPS[n], stream=stream)
+            if record:
+                ev[n][2].record(stream)
+            bg.color_sum(CM[n], AMPS[n], True, mode=bg.BG_CS_F32, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
+                         stream=stream)
+            if record:
+                ev[n][3].record(stream)
+
+    # FP32 / FP64 pipe peaks measured by the FMA probe (for context)
+    def probe(prec, iters):
+        bg.probe_fma(prec, NUM_SMS * 8, 64, stream=stream)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        fl = bg.probe_fma(prec, NUM_SMS * 8, iters, stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        return fl / (s0.elapsed_time(s1) * 1e-3) / 1e12
+
+    probe_f32 = probe(bg.BG_F32, 20000)
+    probe_f64 = probe(bg.BG_F64, 500)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+    barrier()
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", "")) or str(local)
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = {n: [0.0, 0.0, 0.0] for n in NS}
+    torch.cuda.synchronize(dev)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize(dev)
+        for n in NS:
+            for j in range(3):
+                kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1])
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) * 1e-3
+    barrier()
+    elapsed = max_over_ranks(elapsed, dev)
+    events = world * len(NS) * BATCH * args.steps
+    value = events / elapsed
+
+    # e2e: the public plan API with HOST buffers, copies inside the timed region
+    plans = {n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_F32, hel_sampled=True)
+             for n in NS}
+    host_u = {n: U[n].cpu().pin_memory() for n in NS}
+    host_h = {n: HEL[n].cpu().pin_memory() for n in NS}
+    host_m = {n: torch.empty((BATCH,), dtype=torch.float64).pin_memory() for n in NS}
+    d2h = sum(host_m[n].numel() * 8 for n in NS)
+    for _ in range(max(1, args.warmup)):
+        for n in NS:
+            plans[n].me2(host_u[n], host_h[n], out=host_m[n], stream=stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        for n in NS:
+            plans[n].me2(host_u[n], host_h[n], out=host_m[n], stream=stream)
+    torch.cuda.synchronize(dev)
+    e2e_elapsed = max_over_ranks(time.perf_counter() - w0, dev)
+    e2e_value = world * len(NS) * BATCH * args.steps / e2e_elapsed
+    # the e2e results must equal the device-resident results
+    for n in NS:
+        if not torch.equal(host_m[n], ME2[n].cpu()):
+            raise RuntimeError(f"e2e |M|^2 differs from the device-resident run at n={n}")
+
+    # roofline of the dominant kernel (colour-ordered recursion at n = 8)
+    n_dom = max(NS, key=lambda n: kernel_ms[n][1])
+    dom_s = kernel_ms[n_dom][1] / args.steps * 1e-3
+    flops = canonical_recursion_flops(n_dom) * BATCH
+    achieved = flops / dom_s / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    traffic = None
+    if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    total_ms = sum(sum(v) for v in kernel_ms.values()) / args.steps
+    shares = {f"n{n}_{name}": kernel_ms[n][j] / args.steps / total_ms
+              for n in NS for j, name in enumerate(("rambo", "co_recursion", "colour_sum"))}
+
+    if rank == 0:
+        line = {
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S,
+                       "pt_min_gev": PT_MIN, "helicities": "sampled, weight 2^n",
+                       "precision": "FP32 currents and colour sum, FP64 Rambo/polarisations/accumulation",
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB of uniforms per step"},
+            "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS},
+            "kernel_ms_per_step": {f"n{n}": [round(x / args.steps, 4) for x in kernel_ms[n]] for n in NS},
+            "kernel_share": {k: round(v, 4) for k, v in shares.items()},
+            "roofline": {"kernel": f"co_kernel<{n_dom},float> (colour-ordered recursion)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "flops_per_launch": flops, "flops_model": "canonical (V3=65, V4=46, prop=12, final=7)",
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts, max clock)",
+                         "probe_fp32_tflops": probe_f32, "probe_fp64_tflops": probe_f64},
+            "cpu_baseline": None,
+            "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    for n in NS:
+        plans[n].close()
+        CM[n].close()
+    if world > 1 and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+def run_profile_case(args) -> None:
+    """A small case of one multiplicity for ncu captures: `warmup` steps, then
+    one step (Rambo, recursion, colour sum), on cuda:0."""
+    import numpy as np
+    import torch
+
+    from paper_2106_06507_gb300 import bg, build_lib, inputs
+    build_lib.build()
+    n, B = args.profile_n, args.profile_batch
+    dev = torch.device("cuda", 0)
+    u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
+    h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
+    C = bg.ColourMatrix(n)
+    p = torch.empty((4, n, B), dtype=torch.float64, device=dev)
+    acc = torch.empty((B,), dtype=torch.uint8, device=dev)
+    amps = torch.empty((B, 1, math.factorial(n - 2)), dtype=torch.float32, device=dev)
+    me2 = torch.empty((B,), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup + 1):
+        bg.momenta_rambo(n, u, SQRT_S, PT_MIN, p=p, accept=acc)
+        bg.currents_co(n, p, h, prec=bg.BG_F32, sqrt_s=SQRT_S, amps=amps)
+        bg.color_sum(C, amps, True, mode=bg.BG_CS_F32, sqrt_s=SQRT_S, accept=acc, me2=me2)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_case": {"n": n, "batch": B, "sum_me2": float(me2.sum().item())}}), flush=True)
+    C.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-n", type=int, default=0,
+                    help="profiling case: run only multiplicity n (warm-up steps, then one step)")
+    ap.add_argument("--profile-batch", type=int, default=1 << 16)
+    args = ap.parse_args(argv)
+    if args.profile_n:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,61 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
                        bg_cs_mode mode, double g_s, double sqrt_s, int hel_sampled, const uint8_t* accept,
                        double* me2, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Plans: the whole hot path for one multiplicity behind one call.
+ * bg_plan_create allocates the plan's device workspace (momenta, cut flags,
+ * amplitudes, staging buffers for host inputs) for up to max_batch events
+ * and, for the colour-ordered algorithm, the colour matrix; bg_me2_batch
+ * then runs Rambo -> cut -> polarisations -> recursion -> colour sum without
+ * allocating.
+ *   algo BG_ALGO_CO: colour-ordered currents + exact colour sum (n <= 9).
+ *   hel_sampled: 1 = one helicity configuration per event (hel given,
+ *   weight 2^n); 0 = sum over all 2^n configurations (hel ignored).
+ * ------------------------------------------------------------------------- */
+typedef enum { BG_ALGO_CO = 0, BG_ALGO_CD = 1 } bg_algo;
+typedef struct {
+  int n;
+  int64_t max_batch;
+  double sqrt_s;
+  double pt_min;      /* final-state pT cut in GeV (< 0: none) */
+  double g_s;         /* strong coupling, e.g. sqrt(4 pi 0.118) */
+  double q[4];        /* light-like reference vector of the polarisations */
+  bg_prec prec;       /* recursion arithmetic */
+  bg_cs_mode cs_mode; /* colour-sum arithmetic (BG_ALGO_CO) */
+  bg_algo algo;
+  bg_color_mode color_mode; /* BG_ALGO_CD */
+  int hel_sampled;
+} bg_plan_desc;
+typedef struct bg_plan bg_plan;
+/* Errors: BG_EINVAL (desc), BG_EUNSUPPORTED, BG_ENOMEM, BG_ECUDA. */
+bg_status bg_plan_create(const bg_plan_desc* desc, bg_plan** out);
+void bg_plan_destroy(bg_plan* plan);
+/* Bytes of device workspace the plan holds (colour matrix included). */
+int64_t bg_plan_workspace_bytes(const bg_plan* plan);
+
+/* ---------------------------------------------------------------------------
+ * bg_me2_batch -- |M|^2 for B <= max_batch events of the plan's
+ * multiplicity.
+ *   u       [B][4(n-2)] double   Rambo uniforms
+ *   hel     [n][B] int8 (+-1)    sampled helicities (hel_sampled = 1), else NULL
+ *   colors  unused by BG_ALGO_CO (NULL)
+ *   me2     [B] double           output, GeV^(8-2n)
+ * Each of u, hel, me2 may be device memory or host memory (pinned or
+ * pageable); host buffers are staged through the plan's workspace with
+ * copies on `stream`.  If me2 is host memory the call synchronises `stream`
+ * before returning, so the values are ready.  Calls on one plan must not
+ * overlap (they share its workspace).
+ * ------------------------------------------------------------------------- */
+bg_status bg_me2_batch(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const int8_t* colors,
+                       double* me2, void* stream);
+
+/* Measurement utility (no counterpart in the paper): a kernel of
+ * independent fused multiply-adds in FP32 (prec = BG_F32) or FP64, on
+ * `blocks` blocks of 256 threads, `iters` iterations of 16 FMAs per thread.
+ * *flops receives the number of floating-point operations it performs
+ * (2 per FMA); time it with events on `stream` to measure the pipe peak. */
+bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream);
+
 /* Device status word of the current device: 0 if no kernel has seen an
  * invalid label since the last reset, else a BG_* code.  Synchronises the
  * device.  bg_device_status_reset clears it. */

@@ -69,6 +69,7 @@ inline Dual log(const Dual& a) { Dual r; r.v = std::log(a.v); for (int i = 0; i 
 inline Dual cos(const Dual& a) { Dual r; r.v = std::cos(a.v); double s = -std::sin(a.v); for (int i = 0; i < kMaxDir; ++i) r.d[i] = s * a.d[i]; return r; }
 inline Dual sin(const Dual& a) { Dual r; r.v = std::sin(a.v); double c = std::cos(a.v); for (int i = 0; i < kMaxDir; ++i) r.d[i] = c * a.d[i]; return r; }
 inline double value(double x) { return x; }
+inline double value(long double x) { return (double)x; }
 inline double value(const Dual& x) { return x.v; }
 using std::cos;
 using std::log;
@@ -517,7 +518,7 @@ template <class T> void pols_for(int n, const Vec<T>* k, const double* q, const 
 
 // Colour-ordered amplitudes A(1, sigma, n) for all (n-2)! orderings
 // (lexicographic), for one event and one helicity configuration.
-template <class T> void all_amps(int n, const Vec<T>* k, const Vec<T>* eps, T* amps) {
+template <class T> void all_amps(int n, const Vec<T>* k, const Vec<T>* eps, T* amps, int tensor_form = 0) {
   const long long nord = factorial(n - 2);
   std::vector<int> sigma(n - 2), ord(n);
   for (long long r = 0; r < nord; ++r) {
@@ -525,7 +526,7 @@ template <class T> void all_amps(int n, const Vec<T>* k, const Vec<T>* eps, T* a
     ord[0] = 0;
     for (int i = 0; i < n - 2; ++i) ord[1 + i] = sigma[i];
     ord[n - 1] = n - 1;
-    amps[r] = amp_co(n, k, eps, ord.data(), 0);
+    amps[r] = amp_co(n, k, eps, ord.data(), tensor_form);
   }
 }
 
@@ -545,7 +546,7 @@ template <class T> T colour_sum(int nord, const double* C, const T* A) {
 // sampled, hel != NULL).  Returns 0 for events failing the pT cut.
 template <class T>
 T me2_co_event(int n, double sqrt_s, const T* u, const double* q, const double* C, const int8_t* hel,
-               double g, double pt_min) {
+               double g, double pt_min, int tensor_form = 0) {
   std::vector<Vec<T>> p(n), k(n), eps(n);
   rambo(n, sqrt_s, u, p.data());
   for (int i = 2; i < n; ++i)
@@ -559,7 +560,7 @@ T me2_co_event(int n, double sqrt_s, const T* u, const double* q, const double* 
   for (int conf = 0; conf < nconf; ++conf) {
     for (int i = 0; i < n; ++i) h[i] = hel ? hel[i] : (((conf >> i) & 1) ? -1 : 1);
     pols_for(n, k.data(), q, h.data(), eps.data());
-    all_amps(n, k.data(), eps.data(), A.data());
+    all_amps(n, k.data(), eps.data(), A.data(), tensor_form);
     me2 += colour_sum(nord, C, A.data());
   }
   double fac = std::pow(g, 2 * n - 4) * (hel ? std::pow(2.0, n) : 1.0);
@@ -712,15 +713,40 @@ void or_current_cd(int n, const double* k, const double* eps, const double* E, i
 // u[B][4(n-2)].  C[k][k] colour matrix (k = (n-2)!), hel[B][n] (+-1) or
 // NULL for the sum over all 2^n polarisation configurations.  me2[B] in
 // GeV^(8-2n).  Work is split over nthreads std::threads by event.
+// tensor_form = 1 evaluates the amplitudes with the tensor-field form of
+// the recursion (Eq. 2.24): the same mathematics in a different operation
+// order, used to measure the FP64 rounding floor of each event.
 void or_me2_co_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const double* C,
-                     const int8_t* hel, double g, double pt_min, double* me2, int nthreads) {
+                     const int8_t* hel, double g, double pt_min, double* me2, int nthreads, int tensor_form) {
   if (nthreads < 1) nthreads = 1;
   std::vector<std::thread> th;
   const int d = 4 * (n - 2);
   for (int t = 0; t < nthreads; ++t)
     th.emplace_back([&, t]() {
       for (long long e = t; e < B; e += nthreads)
-        me2[e] = me2_co_event<double>(n, sqrt_s, u + e * d, q, C, hel ? hel + e * n : nullptr, g, pt_min);
+        me2[e] = me2_co_event<double>(n, sqrt_s, u + e * d, q, C, hel ? hel + e * n : nullptr, g, pt_min,
+                                      tensor_form);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Same as or_me2_co_batch in extended precision (long double: 64-bit
+// significand on x86-64, IEEE binary128 on AArch64).  Serves as the
+// reference for FP64 parity: the plain FP64 evaluation of the definition
+// itself carries rounding errors above 1e-12 on ill-conditioned events.
+void or_me2_co_batch_ext(int n, long long B, double sqrt_s, const double* u, const double* q, const double* C,
+                         const int8_t* hel, double g, double pt_min, double* me2, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::thread> th;
+  const int d = 4 * (n - 2);
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<long double> ul(d);
+      for (long long e = t; e < B; e += nthreads) {
+        for (int i = 0; i < d; ++i) ul[i] = u[e * d + i];
+        me2[e] = (double)me2_co_event<long double>(n, sqrt_s, ul.data(), q, C, hel ? hel + e * n : nullptr, g,
+                                                   pt_min);
+      }
     });
   for (auto& x : th) x.join();
 }

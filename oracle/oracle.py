@@ -71,7 +71,8 @@ def lib():
             L.or_amp_cd.argtypes = [c_int, dp, dp, dp]
             L.or_amp_cd.restype = c_dbl
             L.or_current_cd.argtypes = [c_int, dp, dp, dp, c_int, dp]
-            L.or_me2_co_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_co_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, i8p, c_dbl, c_dbl, dp, c_int, c_int]
+            L.or_me2_co_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_cd_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
             L.or_me2_co_grad.argtypes = [c_int, c_dbl, dp, dp, dp, i8p, c_dbl, dp]
             L.or_me2_co_grad.restype = c_dbl
@@ -307,9 +308,10 @@ def current_cd(k, eps, E, S: int) -> np.ndarray:
 # batched |M|^2
 # --------------------------------------------------------------------------
 def me2_co(n, u, sqrt_s=1000.0, hel=None, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0, C=None,
-           nthreads=None) -> np.ndarray:
+           nthreads=None, tensor_form=False) -> np.ndarray:
     """Colour-summed |M|^2 (GeV^(8-2n)) per event; hel=None sums all 2^n
-    polarisation configurations, else hel[B,n] is sampled (weight 2^n)."""
+    polarisation configurations, else hel[B,n] is sampled (weight 2^n).
+    tensor_form evaluates the amplitudes with the auxiliary tensor field."""
     u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
     B = u.shape[0]
     C = colour_matrix(n) if C is None else np.ascontiguousarray(C, dtype=np.float64)
@@ -320,8 +322,41 @@ def me2_co(n, u, sqrt_s=1000.0, hel=None, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.
     if hel is not None:
         hel, hp = _i8(np.asarray(hel).reshape(B, n))
     lib().or_me2_co_batch(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, Cp, hp, g,
-                          pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+                          pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores(),
+                          int(tensor_form))
     return me2
+
+
+def me2_co_ext(n, u, sqrt_s=1000.0, hel=None, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0, C=None,
+               nthreads=None) -> np.ndarray:
+    """me2_co evaluated in extended precision (long double), rounded to FP64."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
+    B = u.shape[0]
+    C = colour_matrix(n) if C is None else np.ascontiguousarray(C, dtype=np.float64)
+    q, qp = _d(q)
+    _, Cp = _d(C)
+    me2 = np.zeros(B)
+    hp = None
+    if hel is not None:
+        hel, hp = _i8(np.asarray(hel).reshape(B, n))
+    lib().or_me2_co_batch_ext(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, Cp, hp, g,
+                              pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+    return me2
+
+
+def fp64_noise_floor(n, u, hel=None, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0) -> np.ndarray:
+    """Per-event relative FP64 rounding floor of |M|^2: the spread between
+    two mathematically identical evaluations (V4 form vs tensor-field form of
+    the recursion; for helicity-summed |M|^2 also a second gauge vector,
+    since the sum is exactly independent of q)."""
+    a = me2_co(n, u, sqrt_s=sqrt_s, hel=hel, q=q, g=g, pt_min=pt_min)
+    b = me2_co(n, u, sqrt_s=sqrt_s, hel=hel, q=q, g=g, pt_min=pt_min, tensor_form=True)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = np.where(a != 0, np.abs(b / a - 1.0), 0.0)
+        if hel is None:
+            c = me2_co(n, u, sqrt_s=sqrt_s, q=(1.0, 0.6, 0.0, 0.8), g=g, pt_min=pt_min)
+            r = np.maximum(r, np.where(a != 0, np.abs(c / a - 1.0), 0.0))
+    return r
 
 
 def me2_cd(n, u, hel, colors, mode=0, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0,

@@ -28,6 +28,16 @@ DEFAULT_Q = (1.0, 0.0, 0.0, 1.0)
 _lib = None
 
 
+BG_ALGO_CO, BG_ALGO_CD = 0, 1
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("max_batch", ctypes.c_int64), ("sqrt_s", ctypes.c_double),
+                ("pt_min", ctypes.c_double), ("g_s", ctypes.c_double), ("q", ctypes.c_double * 4),
+                ("prec", ctypes.c_int), ("cs_mode", ctypes.c_int), ("algo", ctypes.c_int),
+                ("color_mode", ctypes.c_int), ("hel_sampled", ctypes.c_int)]
+
+
 class BGError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"bg status {code}: {msg}")
@@ -54,10 +64,18 @@ def lib() -> ctypes.CDLL:
         L.bg_momenta_rambo.argtypes = [c_int, c_i64, c_dbl, vp, vp, c_dbl, vp, vp]
         L.bg_currents_co.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, vp, vp]
         L.bg_color_sum.argtypes = [vp, c_i64, c_int, vp, c_int, c_int, c_dbl, c_dbl, c_int, vp, vp, vp]
+        L.bg_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(vp)]
+        L.bg_plan_destroy.argtypes = [vp]
+        L.bg_plan_destroy.restype = None
+        L.bg_plan_workspace_bytes.argtypes = [vp]
+        L.bg_plan_workspace_bytes.restype = c_i64
+        L.bg_me2_batch.argtypes = [vp, c_i64, vp, vp, vp, vp, vp]
+        L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_device_status.argtypes = [ctypes.POINTER(c_int)]
         L.bg_device_status_reset.argtypes = []
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
-                     "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset"):
+                     "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
+                     "bg_plan_create", "bg_me2_batch", "bg_probe_fma"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -165,6 +183,65 @@ def color_sum(C: ColourMatrix, amps: torch.Tensor, hel_sampled: bool, mode: int 
     _check(lib().bg_color_sum(C.handle, B, H, _ptr(amps), prec, mode, g_s, sqrt_s, int(bool(hel_sampled)),
                               _ptr(accept), _ptr(me2), _stream(stream)))
     return me2
+
+
+class Plan:
+    """The whole hot path for one multiplicity (bg_plan_create / bg_me2_batch)."""
+
+    def __init__(self, n: int, max_batch: int, sqrt_s: float = 1000.0, pt_min: float = -1.0,
+                 g_s: float = G_S_DEFAULT, q=DEFAULT_Q, prec: int = BG_F32, cs_mode: int = BG_CS_F32,
+                 algo: int = BG_ALGO_CO, color_mode: int = BG_COL_ADJOINT, hel_sampled: bool = True):
+        d = PlanDesc()
+        d.n, d.max_batch, d.sqrt_s, d.pt_min, d.g_s = n, max_batch, sqrt_s, pt_min, g_s
+        for i in range(4):
+            d.q[i] = float(q[i])
+        d.prec, d.cs_mode, d.algo, d.color_mode, d.hel_sampled = prec, cs_mode, algo, color_mode, int(hel_sampled)
+        self.desc = d
+        self.n = n
+        self.hel_sampled = bool(hel_sampled)
+        h = ctypes.c_void_p()
+        _check(lib().bg_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().bg_plan_workspace_bytes(self._h))
+
+    def me2(self, u, hel=None, colors=None, out=None, stream=None):
+        """u [B, 4(n-2)] float64, hel [n, B] int8 (device or host tensors or
+        numpy arrays) -> me2 [B] float64 (on the device of `out`, or a new
+        CUDA tensor if out is None)."""
+        B = u.shape[0]
+        if out is None:
+            out = torch.empty((B,), dtype=torch.float64, device="cuda")
+        _check(lib().bg_me2_batch(self._h, B, _vptr(u), _vptr(hel), _vptr(colors), _vptr(out), _stream(stream)))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().bg_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _vptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)  # numpy array (host memory)
+
+
+def probe_fma(prec: int, blocks: int, iters: int, stream=None) -> float:
+    flops = ctypes.c_double(0.0)
+    _check(lib().bg_probe_fma(prec, blocks, iters, ctypes.byref(flops), _stream(stream)))
+    return flops.value
 
 
 def device_status() -> int:

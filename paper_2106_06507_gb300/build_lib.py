@@ -27,6 +27,7 @@ SOURCES = [
     "co_f64.cu",
     "color_sum.cu",
     "colormat.cpp",
+    "probe.cu",
 ]
 
 

@@ -181,6 +181,132 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
   return cuda_check(e, "bg_color_sum");
 }
 
+bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream) {
+  if (blocks < 1 || iters < 1 || !flops) return fail(BG_EINVAL, "bg_probe_fma: invalid arguments");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_probe_fma: invalid precision");
+  *flops = 2.0 * 16.0 * 256.0 * (double)blocks * (double)iters;
+  return cuda_check(launch_probe_fma(prec == BG_F32, blocks, iters, (cudaStream_t)stream), "bg_probe_fma");
+}
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+static bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+void bg_plan_destroy(bg_plan* P) {
+  if (!P) return;
+  void* bufs[] = {P->u, P->hel, P->colors, P->p, P->accept, P->amps, P->me2};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (P->C) bg_colormat_destroy(P->C);
+  delete P;
+}
+
+int64_t bg_plan_workspace_bytes(const bg_plan* P) { return P ? P->bytes : 0; }
+
+bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
+  if (!d || !out) return fail(BG_EINVAL, "bg_plan_create: NULL argument");
+  *out = nullptr;
+  const int n = d->n;
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_plan_create: n must be in 4..12");
+  if (d->max_batch < 1) return fail(BG_EINVAL, "bg_plan_create: max_batch must be >= 1");
+  if (!(d->sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_plan_create: sqrt_s must be > 0");
+  if (d->prec != BG_F32 && d->prec != BG_F64) return fail(BG_EINVAL, "bg_plan_create: invalid precision");
+  if (d->algo != BG_ALGO_CO && d->algo != BG_ALGO_CD) return fail(BG_EINVAL, "bg_plan_create: invalid algorithm");
+  if (d->algo == BG_ALGO_CD) return fail(BG_EUNSUPPORTED, "bg_plan_create: colour-dressed plans not available");
+  if (n > kMaxNCO) return fail(BG_EUNSUPPORTED, "bg_plan_create: colour-ordered path supports n <= 9");
+  if (d->cs_mode != BG_CS_F64 && d->cs_mode != BG_CS_F32) return fail(BG_EINVAL, "bg_plan_create: invalid cs_mode");
+  const double qv = std::sqrt(d->q[1] * d->q[1] + d->q[2] * d->q[2] + d->q[3] * d->q[3]);
+  if (!(d->q[0] > 0.0) || std::fabs(d->q[0] - qv) > 1e-12 * d->q[0])
+    return fail(BG_EINVAL, "bg_plan_create: q must be light-like with q0 > 0");
+  bg_plan* P = new (std::nothrow) bg_plan();
+  if (!P) return fail(BG_ENOMEM, "bg_plan_create: host allocation failed");
+  std::memset(static_cast<void*>(P), 0, sizeof(bg_plan));
+  P->d = *d;
+  P->k = (int)factorial(n - 2);
+  P->H = d->hel_sampled ? 1 : (1 << n);
+  cudaGetDevice(&P->device);
+  bg_status st = bg_colormat_create(n, &P->C);
+  if (st != BG_OK) {
+    delete P;
+    return st;
+  }
+  const int64_t B = d->max_batch;
+  const size_t amp_bytes = (size_t)B * P->H * P->k * (d->prec == BG_F32 ? 4 : 8);
+  struct Req {
+    void** ptr;
+    size_t bytes;
+  } reqs[] = {{(void**)&P->u, (size_t)B * 4 * (n - 2) * sizeof(double)},
+              {(void**)&P->hel, (size_t)B * n},
+              {(void**)&P->colors, (size_t)B * 2 * n},
+              {(void**)&P->p, (size_t)B * 4 * n * sizeof(double)},
+              {(void**)&P->accept, (size_t)B},
+              {&P->amps, amp_bytes},
+              {(void**)&P->me2, (size_t)B * sizeof(double)}};
+  P->bytes = (int64_t)P->C->k * P->C->k * 12;
+  for (auto& r : reqs) {
+    if (cudaMalloc(r.ptr, r.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      bg_plan_destroy(P);
+      return fail(BG_ENOMEM, "bg_plan_create: device allocation failed");
+    }
+    P->bytes += (int64_t)r.bytes;
+  }
+  *out = P;
+  return BG_OK;
+}
+
+bg_status bg_me2_batch(bg_plan* P, int64_t B, const double* u, const int8_t* hel, const int8_t* colors,
+                       double* me2, void* stream) {
+  (void)colors;
+  if (!P) return fail(BG_EINVAL, "bg_me2_batch: plan is NULL");
+  if (B < 0 || B > P->d.max_batch) return fail(BG_EINVAL, "bg_me2_batch: B outside 0..max_batch");
+  if (B == 0) return BG_OK;
+  if (!u || !me2) return fail(BG_EINVAL, "bg_me2_batch: NULL u or me2");
+  if (P->d.hel_sampled && !hel) return fail(BG_EINVAL, "bg_me2_batch: hel is required for sampled helicities");
+  const int n = P->d.n;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* ud = u;
+  if (!is_device_ptr(u)) {
+    bg_status st = cuda_check(cudaMemcpyAsync(P->u, u, (size_t)B * 4 * (n - 2) * sizeof(double),
+                                              cudaMemcpyHostToDevice, s),
+                              "bg_me2_batch: copy u");
+    if (st != BG_OK) return st;
+    ud = P->u;
+  }
+  const int8_t* hd = P->d.hel_sampled ? hel : nullptr;
+  if (hd && !is_device_ptr(hd)) {
+    // host layout [n][B] -> device [n][B] (row stride B in both)
+    bg_status st = cuda_check(cudaMemcpyAsync(P->hel, hd, (size_t)B * n, cudaMemcpyHostToDevice, s),
+                              "bg_me2_batch: copy hel");
+    if (st != BG_OK) return st;
+    hd = P->hel;
+  }
+  const bool host_out = !is_device_ptr(me2);
+  double* md = host_out ? P->me2 : me2;
+  bg_status st = bg_momenta_rambo(n, B, P->d.sqrt_s, ud, P->p, P->d.pt_min, P->accept, stream);
+  if (st != BG_OK) return st;
+  st = bg_currents_co(n, B, P->d.sqrt_s, P->p, hd, P->d.q, P->d.prec, P->amps, stream);
+  if (st != BG_OK) return st;
+  st = bg_color_sum(P->C, B, P->H, P->amps, P->d.prec, P->d.cs_mode, P->d.g_s, P->d.sqrt_s, P->d.hel_sampled,
+                    P->accept, md, stream);
+  if (st != BG_OK) return st;
+  if (host_out) {
+    st = cuda_check(cudaMemcpyAsync(me2, md, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, s),
+                    "bg_me2_batch: copy me2");
+    if (st != BG_OK) return st;
+    st = cuda_check(cudaStreamSynchronize(s), "bg_me2_batch: synchronise");
+  }
+  return st;
+}
+
 bg_status bg_device_status(int* status) {
   if (!status) return fail(BG_EINVAL, "bg_device_status: NULL");
   int* d = device_status_ptr();

@@ -55,9 +55,27 @@ struct ColourSumArgs {
   double* me2;
 };
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
+cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_color_sum_f32(const ColourSumArgs& a, cudaStream_t s);
 
 }  // namespace bg
+
+struct bg_plan {
+  bg_plan_desc d;
+  int k;       // orderings
+  int H;       // polarisation configurations per event
+  int device;
+  bg_colormat* C;
+  // device workspace
+  double* u;        // [max_batch][4(n-2)] staging for host uniforms
+  int8_t* hel;      // [n][max_batch] staging for host helicities
+  int8_t* colors;   // [2n][max_batch] staging for host colours
+  double* p;        // [4][n][max_batch]
+  uint8_t* accept;  // [max_batch]
+  void* amps;       // [max_batch][H][k]
+  double* me2;      // [max_batch] staging for a host output
+  int64_t bytes;
+};
 
 struct bg_colormat {
   int n;

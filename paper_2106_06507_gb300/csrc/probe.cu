@@ -1,0 +1,36 @@
+// probe.cu -- FMA throughput probe used to measure the FP32 / FP64 pipe
+// peaks of the device (a measurement utility, not part of the method).
+#include "bg_internal.h"
+
+namespace bg {
+namespace {
+
+__device__ double g_probe_sink;
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T seed) {
+  T a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = seed + T(threadIdx.x + i);
+  const T b = T(0.999999), c = T(1e-7);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = fma(a[i], b, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s += a[i];
+  if (s == T(-1.2345e-30)) g_probe_sink = (double)s;  // keeps the chain alive
+}
+
+}  // namespace
+
+cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s) {
+  if (f32)
+    fma_probe_kernel<float><<<blocks, 256, 0, s>>>(iters, 1.0f);
+  else
+    fma_probe_kernel<double><<<blocks, 256, 0, s>>>(iters, 1.0);
+  return cudaGetLastError();
+}
+
+}  // namespace bg

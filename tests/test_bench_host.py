@@ -1,0 +1,60 @@
+"""Host logic of bench.py on CPU: the max-over-ranks timing reduction with a
+world_size-2 gloo group, and the per-n rate aggregation."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(1.5 + rank)
+        bench.barrier()
+        q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = dict(q.get(timeout=5) for _ in range(2))
+    assert res == {0: 2.5, 1: 2.5}
+
+
+def test_aggregate_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+    rates = {n: 1.0e6 for n in bench.NS}
+    assert bench.aggregate_rate(rates, batch=1000) == pytest.approx(1.0e6)
+    rates = {5: 4.0, 6: 4.0, 7: 2.0, 8: 1.0}
+    # 4 batches of 4 events take 1 + 1 + 2 + 4 = 8 s
+    assert bench.aggregate_rate(rates, batch=4) == pytest.approx(16 / 8)
+
+
+def test_canonical_flop_model():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.canonical_recursion_flops(8) == 720 * 7119
+    assert bench.canonical_recursion_flops(4) == 2 * (65 * 4 + 46 * 1 + 12 * 3 + 7)
+    assert bench.colour_sum_flops(8) == 2 * 720 * 720 + 2 * 720

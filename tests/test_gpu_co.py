@@ -1,12 +1,17 @@
 """GPU parity of the colour-ordered path (Rambo -> currents -> colour sum)
-against the FP64 oracle on identical host-generated inputs.
+against the oracle on identical host-generated inputs.
 
 Tolerances (written here, derived in the design notes):
-  FP64 path: 1e-12 relative per event on |M|^2; amplitudes to 1e-11 of the
-  event's largest ordering amplitude.
-  FP32 currents: |M|^2 per event within 2e-4 relative for 99.9% of events and
-  within 1e-2 for all (the tail comes from nearly collinear phase-space points,
-  where cancellations amplify FP32 rounding); median below 2e-6.
+  FP64 path: |M|^2 is compared with the oracle evaluated in extended
+  precision.  At least 99% of events agree to 1e-12 relative, and every event
+  agrees to max(1e-12, 4 x the error of the plain FP64 oracle on that event):
+  the FP64 evaluation of the definition itself loses up to ~3e-11 on
+  ill-conditioned events (gluons close to the gauge vector's axis, where the
+  light-cone polarisations grow and diagrams cancel).  Amplitudes agree to
+  1e-11 of the event's largest ordering amplitude.
+  FP32 currents: median relative error below 2e-6, 99.9% of events below
+  1e-4, all below 1e-3 (the tail is nearly collinear phase space, where
+  cancellations amplify FP32 rounding).
 """
 import math
 
@@ -41,6 +46,17 @@ def torch_dev():
 def to_dev(x, dev):
     import torch
     return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def assert_fp64_parity(oracle, got, n, u, hel, pt_min=-1.0):
+    ext = oracle.me2_co_ext(n, u, sqrt_s=SQRT_S, hel=hel, pt_min=pt_min)
+    f64 = oracle.me2_co(n, u, sqrt_s=SQRT_S, hel=hel, pt_min=pt_min)
+    assert np.array_equal(got == 0, ext == 0)
+    nz = ext != 0
+    rel = np.abs(got[nz] / ext[nz] - 1.0)
+    floor = np.abs(f64[nz] / ext[nz] - 1.0)
+    assert np.mean(rel <= 1e-12) >= 0.99
+    assert np.all(rel <= np.maximum(1e-12, 4.0 * floor))
 
 
 @pytest.mark.parametrize("n", [4, 5, 6, 8, 10, 12])
@@ -82,23 +98,19 @@ def test_helicity_summed_fp64_n4_full_config(bg, oracle, torch_dev):
     amps = bg.currents_co(n, p, None, prec=bg.BG_F64, sqrt_s=SQRT_S)
     assert tuple(amps.shape) == (B, 16, 2)
     me2 = bg.color_sum(C, amps, hel_sampled=False, mode=bg.BG_CS_F64, sqrt_s=SQRT_S).cpu().numpy()
-    ref = oracle.me2_co(n, u, sqrt_s=SQRT_S)
-    assert np.abs(me2 / ref - 1.0).max() < 1e-12
+    assert_fp64_parity(oracle, me2, n, u, None)
 
 
 @pytest.mark.parametrize("n", [5, 6, 7, 8])
 def test_me2_fp64_parity_sampled_helicity(bg, oracle, torch_dev, n):
-    B = {5: 2000, 6: 600, 7: 150, 8: 37}[n]  # ragged: not a multiple of the event tile
+    B = {5: 1000, 6: 300, 7: 70, 8: 21}[n]  # ragged: not a multiple of the event tile
     u = inputs.rambo_uniforms(n, B, seed=23)
     hel = inputs.helicities(n, B, seed=23)
     C = bg.ColourMatrix(n)
     p, acc = bg.momenta_rambo(n, to_dev(u, torch_dev), SQRT_S, PT_MIN)
     amps = bg.currents_co(n, p, to_dev(hel.T, torch_dev), prec=bg.BG_F64, sqrt_s=SQRT_S)
     me2 = bg.color_sum(C, amps, hel_sampled=True, mode=bg.BG_CS_F64, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
-    ref = oracle.me2_co(n, u, sqrt_s=SQRT_S, hel=hel, pt_min=PT_MIN)
-    assert np.array_equal(me2 == 0, ref == 0)
-    nz = ref != 0
-    assert np.abs(me2[nz] / ref[nz] - 1.0).max() < 1e-12
+    assert_fp64_parity(oracle, me2, n, u, hel, PT_MIN)
 
 
 @pytest.mark.parametrize("n", [5, 6, 7, 8])
@@ -116,8 +128,8 @@ def test_me2_fp32_parity_sampled_helicity(bg, oracle, torch_dev, n):
         assert np.array_equal(me2 == 0, ref == 0)
         rel = np.abs(me2[nz] / ref[nz] - 1.0)
         assert np.median(rel) < 2e-6
-        assert np.quantile(rel, 0.999) < 2e-4
-        assert rel.max() < 1e-2
+        assert np.quantile(rel, 0.999) < 1e-4
+        assert rel.max() < 1e-3
 
 
 def test_edge_cases(bg, torch_dev):
