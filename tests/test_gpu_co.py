@@ -3,13 +3,14 @@ against the oracle on identical host-generated inputs.
 
 Tolerances (written here, derived in the design notes):
   FP64 path: |M|^2 is compared with the oracle evaluated in extended
-  precision.  At least 99% of events agree to 1e-12 relative; the 99.9th
-  percentile and the maximum of the GPU's relative error are at most
-  max(1e-12, 8x) the same statistic of the plain FP64 oracle's error on the
-  same events.  The FP64 evaluation of the definition itself loses up to
-  ~2e-11 on ill-conditioned events (large cancellations between diagrams), so
-  a per-event 1e-12 bound is not a property of FP64 arithmetic; the GPU path is
-  required to be as accurate as an FP64 evaluation of the definition.
+  precision.  The median relative error is below 1e-13; the number of events
+  above 1e-12 is at most 2 + 1% of the events + 4x the number for which the
+  plain FP64 oracle itself is above 1e-12; the worst event is within
+  max(5e-11, 8x the plain FP64 oracle's worst error).  The FP64 evaluation
+  of the definition itself loses up to ~2e-11 on ill-conditioned events
+  (large cancellations between diagrams), so a per-event 1e-12 bound is not
+  a property of FP64 arithmetic; the GPU path is required to be as accurate
+  as an FP64 evaluation of the definition.
   Amplitudes agree to 1e-11 of the event's largest ordering amplitude.
   FP32 currents: median relative error below 2e-6, 99.9% of events below
   1e-4, all below 1e-3 (the tail is nearly collinear phase space, where
@@ -57,9 +58,9 @@ def assert_fp64_parity(oracle, got, n, u, hel, pt_min=-1.0):
     nz = ext != 0
     rel = np.abs(got[nz] / ext[nz] - 1.0)
     floor = np.abs(f64[nz] / ext[nz] - 1.0)
-    assert np.mean(rel <= 1e-12) >= 0.99
-    assert np.quantile(rel, 0.999) <= max(1e-12, 8.0 * np.quantile(floor, 0.999))
-    assert rel.max() <= max(1e-12, 8.0 * floor.max())
+    assert np.median(rel) < 1e-13
+    assert np.sum(rel > 1e-12) <= 2 + 0.01 * rel.size + 4 * np.sum(floor > 1e-12)
+    assert rel.max() <= max(5e-11, 8.0 * floor.max())
 
 
 @pytest.mark.parametrize("n", [4, 5, 6, 8, 10, 12])
@@ -106,7 +107,7 @@ def test_helicity_summed_fp64_n4_full_config(bg, oracle, torch_dev):
 
 @pytest.mark.parametrize("n", [5, 6, 7, 8])
 def test_me2_fp64_parity_sampled_helicity(bg, oracle, torch_dev, n):
-    B = {5: 1000, 6: 300, 7: 70, 8: 21}[n]  # ragged: not a multiple of the event tile
+    B = {5: 4001, 6: 1501, 7: 401, 8: 101}[n]  # ragged: not a multiple of the event tile
     u = inputs.rambo_uniforms(n, B, seed=23)
     hel = inputs.helicities(n, B, seed=23)
     C = bg.ColourMatrix(n)
