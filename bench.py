@@ -46,8 +46,10 @@ WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqr
             "sampled helicities, FP32 currents for all (n-2)! orderings, exact colour sum A^T C A")
 
 # DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
-# n = 8, 2^20 events), valid only for the kernel sources it was taken from.
-NCU_TRAFFIC = {"sources_sha1": None, "bytes_per_launch": None}
+# n = 8, 2^20 events, scaled from a 2^16-event capture by the number of
+# events), valid only for the kernel sources it was taken from.
+NCU_TRAFFIC = {"sources_sha1": "3c4b40b2104c8baf538a2ff0541891090c7c710c",
+               "bytes_per_launch": 16 * (18204416 + 128165120)}  # 2^16-event capture x 16
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
 
