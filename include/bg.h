@@ -59,8 +59,13 @@ typedef enum {
 /* Arithmetic type of the recursion (currents and amplitudes). */
 typedef enum { BG_F64 = 0, BG_F32 = 1 } bg_prec;
 
-/* Colour-sum arithmetic: FP64 CUDA cores, FP32 CUDA cores. */
-typedef enum { BG_CS_F64 = 0, BG_CS_F32 = 1 } bg_cs_mode;
+/* Colour-sum arithmetic: FP64 CUDA cores; FP32 CUDA cores; tensor cores
+ * (tcgen05, BF16 inputs: C/gcd exact in BF16, amplitudes split into three
+ * BF16 planes hi+mid+lo carrying 24 significant bits; FP32 accumulation in
+ * tensor memory; FP64 per-event accumulation).  BG_CS_TC_BF16 needs
+ * 6 <= n <= 8 (for n = 9 some C/gcd entries need more than 8 significant
+ * bits: BG_EUNSUPPORTED) and one polarisation configuration per event. */
+typedef enum { BG_CS_F64 = 0, BG_CS_F32 = 1, BG_CS_TC_BF16 = 2 } bg_cs_mode;
 
 /* Sampled-colour representation for the colour-dressed recursion. */
 typedef enum { BG_COL_ADJOINT = 0, BG_COL_FLOW = 1 } bg_color_mode;

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libbg.so")
 
 BG_OK, BG_EINVAL, BG_ENOMEM, BG_ECUDA, BG_EUNSUPPORTED, BG_ETIMEOUT = range(6)
 BG_F64, BG_F32 = 0, 1
-BG_CS_F64, BG_CS_F32 = 0, 1
+BG_CS_F64, BG_CS_F32, BG_CS_TC_BF16 = 0, 1, 2
 BG_COL_ADJOINT, BG_COL_FLOW = 0, 1
 
 G_S_DEFAULT = math.sqrt(4.0 * math.pi * 0.118)  # alpha_s = 0.118

@@ -26,6 +26,7 @@ SOURCES = [
     "co_f32.cu",
     "co_f64.cu",
     "color_sum.cu",
+    "color_sum_tc.cu",
     "colormat.cpp",
     "probe.cu",
 ]

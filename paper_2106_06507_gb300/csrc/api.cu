@@ -78,6 +78,10 @@ bg_status bg_colormat_create(int n, bg_colormat** out) {
   C->k = (int)factorial(n - 2);
   C->C64 = nullptr;
   C->C32 = nullptr;
+  C->tc_tiles_raw = nullptr;
+  C->tc_tiles = nullptr;
+  C->tc_g = 0.0;
+  C->tc_nt = C->tc_ntiles = C->tc_kchunks = 0;
   cudaGetDevice(&C->device);
   colour_row(n, C->row);
   std::vector<double> dense;
@@ -100,6 +104,21 @@ bg_status bg_colormat_create(int n, bg_colormat** out) {
     bg_colormat_destroy(C);
     return st;
   }
+  std::vector<uint16_t> tiles;
+  if (build_tc_tiles(n, dense, C->k, tiles, C->tc_g, C->tc_nt, C->tc_ntiles, C->tc_kchunks)) {
+    if (cudaMalloc(&C->tc_tiles_raw, tiles.size() * 2) != cudaSuccess) {
+      cudaGetLastError();
+      bg_colormat_destroy(C);
+      return fail(BG_ENOMEM, "bg_colormat_create: device allocation failed");
+    }
+    st = cuda_check(cudaMemcpy(C->tc_tiles_raw, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice),
+                    "bg_colormat_create: upload");
+    if (st != BG_OK) {
+      bg_colormat_destroy(C);
+      return st;
+    }
+    C->tc_tiles = reinterpret_cast<const __nv_bfloat16*>(C->tc_tiles_raw);
+  }
   *out = C;
   return BG_OK;
 }
@@ -108,6 +127,7 @@ void bg_colormat_destroy(bg_colormat* C) {
   if (!C) return;
   if (C->C64) cudaFree(C->C64);
   if (C->C32) cudaFree(C->C32);
+  if (C->tc_tiles_raw) cudaFree(C->tc_tiles_raw);
   delete C;
 }
 
@@ -157,7 +177,10 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
   if (!C) return fail(BG_EINVAL, "bg_color_sum: C is NULL");
   if (B < 0 || H < 1) return fail(BG_EINVAL, "bg_color_sum: B < 0 or H < 1");
   if (amp_prec != BG_F32 && amp_prec != BG_F64) return fail(BG_EINVAL, "bg_color_sum: invalid amp precision");
-  if (mode != BG_CS_F64 && mode != BG_CS_F32) return fail(BG_EINVAL, "bg_color_sum: invalid mode");
+  if (mode != BG_CS_F64 && mode != BG_CS_F32 && mode != BG_CS_TC_BF16)
+    return fail(BG_EINVAL, "bg_color_sum: invalid mode");
+  if (mode == BG_CS_TC_BF16 && (!C->tc_tiles || H != 1))
+    return fail(BG_EUNSUPPORTED, "bg_color_sum: tensor-core mode needs 6 <= n <= 8 and H = 1");
   if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_color_sum: sqrt_s must be > 0");
   if (B == 0) return BG_OK;
   if (!amps || !me2) return fail(BG_EINVAL, "bg_color_sum: NULL amps or me2");
@@ -176,8 +199,9 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
   a.scale = std::pow(g_s, 2 * n - 4) * std::pow(sqrt_s, 8 - 2 * n) * (hel_sampled ? std::ldexp(1.0, n) : 1.0);
   a.accept = accept;
   a.me2 = me2;
-  cudaError_t e = (mode == BG_CS_F64) ? launch_color_sum_f64(a, (cudaStream_t)stream)
-                                      : launch_color_sum_f32(a, (cudaStream_t)stream);
+  cudaError_t e = (mode == BG_CS_F64)   ? launch_color_sum_f64(a, (cudaStream_t)stream)
+                  : (mode == BG_CS_F32) ? launch_color_sum_f32(a, (cudaStream_t)stream)
+                                        : launch_color_sum_tc(a, C, device_status_ptr(), (cudaStream_t)stream);
   return cuda_check(e, "bg_color_sum");
 }
 
@@ -222,7 +246,10 @@ bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
   if (d->algo != BG_ALGO_CO && d->algo != BG_ALGO_CD) return fail(BG_EINVAL, "bg_plan_create: invalid algorithm");
   if (d->algo == BG_ALGO_CD) return fail(BG_EUNSUPPORTED, "bg_plan_create: colour-dressed plans not available");
   if (n > kMaxNCO) return fail(BG_EUNSUPPORTED, "bg_plan_create: colour-ordered path supports n <= 9");
-  if (d->cs_mode != BG_CS_F64 && d->cs_mode != BG_CS_F32) return fail(BG_EINVAL, "bg_plan_create: invalid cs_mode");
+  if (d->cs_mode != BG_CS_F64 && d->cs_mode != BG_CS_F32 && d->cs_mode != BG_CS_TC_BF16)
+    return fail(BG_EINVAL, "bg_plan_create: invalid cs_mode");
+  if (d->cs_mode == BG_CS_TC_BF16 && (n < 6 || n > 8 || !d->hel_sampled))
+    return fail(BG_EUNSUPPORTED, "bg_plan_create: tensor-core colour sum needs 6 <= n <= 8, sampled helicities");
   const double qv = std::sqrt(d->q[1] * d->q[1] + d->q[2] * d->q[2] + d->q[3] * d->q[3]);
   if (!(d->q[0] > 0.0) || std::fabs(d->q[0] - qv) > 1e-12 * d->q[0])
     return fail(BG_EINVAL, "bg_plan_create: q must be light-like with q0 > 0");

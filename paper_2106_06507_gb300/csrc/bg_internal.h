@@ -1,6 +1,7 @@
 // bg_internal.h -- declarations shared by the translation units of libbg.so.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,6 +57,10 @@ struct ColourSumArgs {
 };
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
 cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
+
+// Tensor-core colour sum (color_sum_tc.cu).
+bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<uint16_t>& tiles, double& g, int& nt,
+                    int& ntiles, int& kchunks);
 cudaError_t launch_color_sum_f32(const ColourSumArgs& a, cudaStream_t s);
 
 }  // namespace bg
@@ -84,4 +89,13 @@ struct bg_colormat {
   std::vector<double> row;  // host copy of the first row
   double* C64;              // device [k][k]
   float* C32;               // device [k][k]
+  // tensor-core operand: BF16 tiles of C / tc_g (NULL if not available)
+  uint16_t* tc_tiles_raw;
+  const __nv_bfloat16* tc_tiles;
+  double tc_g;
+  int tc_nt, tc_ntiles, tc_kchunks;
 };
+
+namespace bg {
+cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, int* status, cudaStream_t s);
+}

@@ -1,0 +1,423 @@
+// color_sum_tc.cu -- the colour sum of Eq. (2.16) on the 5th-generation
+// tensor cores (tcgen05, sm_103a):
+//   |M|^2_e = scale * sum_m A_{e m} (A C)_{e m},   C symmetric.
+//
+// Operands.  D = A C is a dense contraction: M = 128 events per CTA (TMEM
+// lanes), N = a tile of NT orderings (TMEM columns), K = all orderings.  C is
+// stored once per colour matrix as BF16 tiles of C/g (g = gcd of its
+// entries; every C/g is exactly representable in BF16 for n <= 9, checked at
+// creation), pre-arranged in the canonical no-swizzle K-major core-matrix
+// layout so that a plain bulk copy lands a tile ready for the MMA.  The FP32
+// amplitudes are split on the fly into three BF16 planes, A = hi + mid + lo
+// (24 significant bits), so that D is accurate to FP32 rounding; the MMA
+// accumulates in FP32 in tensor memory.
+//
+// Roles (10 warps):
+//   warp 0      one thread: bulk copies of C tiles (mbarrier complete_tx)
+//   warp 1      allocates tensor memory; one thread issues tcgen05.mma and
+//               tcgen05.commit
+//   warps 2..5  converters: FP32 amplitudes -> 3 BF16 planes in shared memory
+//   warps 6..9  epilogue: tcgen05.ld of D rows (one event per thread),
+//               contraction with the FP32 amplitudes, FP64 accumulation
+// Two pipeline stages for the operands and two accumulator buffers in
+// tensor memory, so that the epilogue of one ordering tile overlaps the
+// MMAs of the next.  Every mbarrier wait is bounded (about 2 s of SM
+// clocks); on expiry the kernel records BG_ETIMEOUT in the status word and
+// the CTA drains and exits.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "bg_internal.h"
+#include "device_common.cuh"
+
+namespace bg {
+namespace {
+
+constexpr int TC_M = 128;         // events per CTA
+constexpr int TC_KC = 64;         // K elements per pipeline stage
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 320;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false (and records BG_ETIMEOUT) if the phase does not
+// complete within kWaitCycles, or if another thread has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      flag_status(status, BG_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between core matrices adjacent in K), stride-dimension byte
+// offset (between 8-row groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row r, k) inside a K-major core-matrix tile whose
+// rows hold TC_KC elements: 8x8 core matrices of 128 contiguous bytes, K-
+// adjacent cores 128 B apart (LBO), 8-row groups 1024 B apart (SBO).
+__host__ __device__ constexpr uint32_t tile_off(int r, int k) {
+  return (uint32_t)(((r >> 3) * (TC_KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+struct TcParams {
+  int64_t B;
+  int k;        // orderings
+  int nt;       // orderings per N tile (multiple of 16, <= 240)
+  int ntiles;   // N tiles
+  int kchunks;  // K chunks of TC_KC
+  double scale; // includes the gcd of C
+};
+
+template <typename TIn>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    color_sum_tc_kernel(TcParams P, const TIn* __restrict__ A, const __nv_bfloat16* __restrict__ Ct,
+                        const uint8_t* __restrict__ accept, double* __restrict__ me2, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned carve-up
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t a_plane_bytes = TC_M * TC_KC * 2;            // 16 KB
+  const uint32_t c_tile_bytes = (uint32_t)P.nt * TC_KC * 2;   // nt*128 B
+  const uint32_t stage_bytes = 3 * a_plane_bytes + ((c_tile_bytes + 1023) & ~1023u);
+  unsigned char* stage_base = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * stage_bytes);
+  uint64_t* full_c = bars;                  // [2]
+  uint64_t* full_a = bars + 2;              // [2]
+  uint64_t* empty = bars + 4;               // [2]
+  uint64_t* dfull = bars + 6;               // [2]
+  uint64_t* dempty = bars + 8;              // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t e0 = (int64_t)blockIdx.x * TC_M;
+  const int total = P.ntiles * P.kchunks;  // pipeline iterations
+  const uint32_t tmem_cols = (2 * P.nt <= 32) ? 32 : (2 * P.nt <= 64) ? 64 : (2 * P.nt <= 128) ? 128
+                           : (2 * P.nt <= 256) ? 256 : 512;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full_c[s], 1);
+      mbar_init(&full_a[s], 128);
+      mbar_init(&empty[s], 1);
+      mbar_init(&dfull[s], 1);
+      mbar_init(&dempty[s], 128);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- C tile producer ----------------
+    if (lane == 0) {
+      for (int it = 0; it < total; ++it) {
+        const int s = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) break;
+        const int ntile = it / P.kchunks, kc = it % P.kchunks;
+        unsigned char* dst = stage_base + s * stage_bytes + 3 * a_plane_bytes;
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(Ct) +
+                                   ((size_t)ntile * P.kchunks + kc) * (size_t)c_tile_bytes;
+        mbar_arrive_expect_tx(&full_c[s], c_tile_bytes);
+        bulk_g2s(dst, src, c_tile_bytes, &full_c[s]);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(TC_M, P.nt);
+      bool ok = true;
+      for (int ntile = 0; ntile < P.ntiles && ok; ++ntile) {
+        const int b = ntile & 1;
+        const uint32_t buse = (uint32_t)(ntile >> 1);
+        if (ntile >= 2 && !mbar_wait(&dempty[b], (buse - 1) & 1, status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * P.nt);
+        for (int kc = 0; kc < P.kchunks; ++kc) {
+          const int it = ntile * P.kchunks + kc;
+          const int s = it & 1;
+          const uint32_t use = (uint32_t)(it >> 1);
+          if (!mbar_wait(&full_c[s], use & 1, status, abort_flag) ||
+              !mbar_wait(&full_a[s], use & 1, status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(stage_base + s * stage_bytes);
+          const uint32_t c0 = a0 + 3 * a_plane_bytes;
+#pragma unroll
+          for (int plane = 0; plane < 3; ++plane) {
+#pragma unroll
+            for (int ks = 0; ks < TC_KC / 16; ++ks) {
+              const uint64_t ad = smem_desc(a0 + plane * a_plane_bytes + ks * 256, 128, 1024);
+              const uint64_t bd = smem_desc(c0 + ks * 256, 128, 1024);
+              mma_bf16(d_tmem, ad, bd, idesc, (kc > 0 || plane > 0 || ks > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[s]);  // stage free once these MMAs have read it
+        }
+        if (ok) mma_commit(&dfull[b]);  // accumulator b complete
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- converters: FP32 -> hi/mid/lo BF16 planes ----------------
+    const int r = threadIdx.x - 64;  // row (event) of the tile, 0..127
+    const int64_t e = e0 + r;
+    for (int it = 0; it < total; ++it) {
+      const int s = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) break;
+      const int kc = it % P.kchunks;
+      unsigned char* st = stage_base + s * stage_bytes;
+      const TIn* row = A + e * (int64_t)P.k;
+#pragma unroll 2
+      for (int g = 0; g < TC_KC / 8; ++g) {
+        const int kk = kc * TC_KC + g * 8;
+        float x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = 0.0f;
+        if (e < P.B && kk < P.k) {
+          if (sizeof(TIn) == 4 && kk + 8 <= P.k) {
+            const float4 v0 = *reinterpret_cast<const float4*>(row + kk);
+            const float4 v1 = *reinterpret_cast<const float4*>(row + kk + 4);
+            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+            x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (kk + j < P.k) x[j] = (float)row[kk + j];
+          }
+        }
+        uint32_t hi[4], mid[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(x[j]), h1 = __float2bfloat16_rn(x[j + 1]);
+          const float r0 = x[j] - __bfloat162float(h0), r1 = x[j + 1] - __bfloat162float(h1);
+          const __nv_bfloat16 m0 = __float2bfloat16_rn(r0), m1 = __float2bfloat16_rn(r1);
+          const __nv_bfloat16 l0 = __float2bfloat16_rn(r0 - __bfloat162float(m0));
+          const __nv_bfloat16 l1 = __float2bfloat16_rn(r1 - __bfloat162float(m1));
+          hi[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          mid[j / 2] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+          lo[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        const uint32_t off = tile_off(r, g * 8);
+        *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(st + a_plane_bytes + off) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
+        *reinterpret_cast<uint4*>(st + 2 * a_plane_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      fence_proxy_async();
+      mbar_arrive(&full_a[s]);
+    }
+  } else {
+    // ---------------- epilogue: one event per thread ----------------
+    const int q = warp & 3;  // TMEM lane quarter accessible to this warp
+    const int r = q * 32 + lane;
+    const int64_t e = e0 + r;
+    const TIn* row = A + e * (int64_t)P.k;
+    double acc = 0.0;
+    for (int ntile = 0; ntile < P.ntiles; ++ntile) {
+      const int b = ntile & 1;
+      const uint32_t buse = (uint32_t)(ntile >> 1);
+      // warp-uniform decision: tcgen05.ld below is .sync.aligned
+      const bool ready = mbar_wait(&dfull[b], buse & 1, status, abort_flag);
+      if (!__all_sync(0xffffffffu, ready)) break;
+      tc_fence_after();
+      float part = 0.0f;
+      for (int c0 = 0; c0 < P.nt; c0 += 16) {
+        float d[16];
+        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.nt + c0), d);
+        const int m0 = ntile * P.nt + c0;
+        if (e < P.B) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (m0 + j < P.k) part = fmaf((float)row[m0 + j], d[j], part);
+        }
+      }
+      acc += (double)part;
+      tc_fence_before();
+      mbar_arrive(&dempty[b]);
+    }
+    if (e < P.B) {
+      const bool ok = (accept == nullptr) || (accept[e] != 0);
+      me2[e] = (ok && !*abort_flag) ? P.scale * acc : 0.0;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+// Host: BF16 tiles of C / g in the layout of tile_off.  Returns false if some
+// C/g is not exactly representable in BF16 (the case for n = 9, where 22
+// entries per row need 9-10 significant bits) or if n is outside 6..9.
+bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<uint16_t>& tiles, double& g,
+                    int& nt, int& ntiles, int& kchunks) {
+  if (n < 6 || n > 9) return false;
+  long long gg = 0;
+  for (double v : dense) {
+    long long x = (long long)(v < 0 ? -v : v);
+    if ((double)x != (v < 0 ? -v : v)) return false;
+    long long a = gg, b = x;
+    while (b) { long long t = a % b; a = b; b = t; }
+    gg = a;
+  }
+  if (gg == 0) return false;
+  g = (double)gg;
+  nt = k < 240 ? ((k + 15) / 16) * 16 : 240;
+  ntiles = (k + nt - 1) / nt;
+  kchunks = (k + TC_KC - 1) / TC_KC;
+  const size_t tile_elems = (size_t)nt * TC_KC;
+  tiles.assign((size_t)ntiles * kchunks * tile_elems, 0);
+  for (int t = 0; t < ntiles; ++t)
+    for (int kc = 0; kc < kchunks; ++kc) {
+      uint16_t* base = &tiles[((size_t)t * kchunks + kc) * tile_elems];
+      for (int rr = 0; rr < nt; ++rr)
+        for (int kk = 0; kk < TC_KC; ++kk) {
+          const int m = t * nt + rr, c = kc * TC_KC + kk;
+          float v = 0.0f;
+          if (m < k && c < k) v = (float)(dense[(size_t)m * k + c] / g);
+          // exact BF16: the low 16 bits of the FP32 pattern must be zero
+          uint32_t u;
+          std::memcpy(&u, &v, 4);
+          if (u & 0xFFFFu) return false;
+          base[tile_off(rr, kk) / 2] = (uint16_t)(u >> 16);
+        }
+    }
+  return true;
+}
+
+size_t tc_smem_bytes(int nt) {
+  const size_t a_plane = TC_M * TC_KC * 2;
+  const size_t c_tile = ((size_t)nt * TC_KC * 2 + 1023) & ~size_t(1023);
+  return 1024 + TC_STAGES * (3 * a_plane + c_tile) + 128;
+}
+
+cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, int* status, cudaStream_t s) {
+  TcParams P;
+  P.B = a.B;
+  P.k = a.k;
+  P.nt = C->tc_nt;
+  P.ntiles = C->tc_ntiles;
+  P.kchunks = C->tc_kchunks;
+  P.scale = a.scale * C->tc_g;
+  const size_t smem = tc_smem_bytes(P.nt);
+  const unsigned blocks = (unsigned)((a.B + TC_M - 1) / TC_M);
+  if (a.amps_f32) {
+    auto kern = color_sum_tc_kernel<float>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const float*>(a.amps), C->tc_tiles, a.accept, a.me2,
+                                          status);
+  } else {
+    auto kern = color_sum_tc_kernel<double>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const double*>(a.amps), C->tc_tiles, a.accept, a.me2,
+                                          status);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bg
