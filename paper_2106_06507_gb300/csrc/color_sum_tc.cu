@@ -5,7 +5,7 @@
 // Operands.  D = A C is a dense contraction: M = 128 events per CTA (TMEM
 // lanes), N = a tile of NT orderings (TMEM columns), K = all orderings.  C is
 // stored once per colour matrix as BF16 tiles of C/g (g = gcd of its
-// entries; every C/g is exactly representable in BF16 for n <= 9, checked at
+// entries; every C/g is exactly representable in BF16 for n <= 8, checked at
 // creation), pre-arranged in the canonical no-swizzle K-major core-matrix
 // layout so that a plain bulk copy lands a tile ready for the MMA.  The FP32
 // amplitudes are split on the fly into three BF16 planes, A = hi + mid + lo
