@@ -54,6 +54,12 @@ DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
 
 
+def cs_mode_for(bg, n: int) -> int:
+    """Colour-sum arithmetic per multiplicity: tensor cores (tcgen05) where
+    available (6 <= n <= 8), FP32 CUDA cores for the 6x6 matrix of n = 5."""
+    return bg.BG_CS_TC_BF16 if 6 <= n <= 8 else bg.BG_CS_F32
+
+
 def canonical_recursion_flops(n: int) -> int:
     """Canonical FLOPs per event of the colour-ordered recursion (all (n-2)!
     orderings, one polarisation configuration): V3 = 65, V4 = 46,
@@ -164,7 +170,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
-CPU_SAMPLE = {5: 1 << 20, 6: 1 << 19, 7: 1 << 17, 8: 1 << 15}
+CPU_SAMPLE = {5: 1 << 22, 6: 1 << 21, 7: 1 << 19, 8: 1 << 17}
 REF_STEP_SAMPLE = {5: 1 << 16, 6: 1 << 14, 7: 1 << 12, 8: 1 << 10}
 
 
@@ -281,8 +287,8 @@ def run_ours(args) -> None:
             bg.currents_co(n, P[n], HEL[n], prec=bg.BG_F32, sqrt_s=SQRT_S, amps=AMPS[n], stream=stream)
             if record:
                 ev[n][2].record(stream)
-            bg.color_sum(CM[n], AMPS[n], True, mode=bg.BG_CS_F32, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
-                         stream=stream)
+            bg.color_sum(CM[n], AMPS[n], True, mode=cs_mode_for(bg, n), sqrt_s=SQRT_S, accept=ACC[n],
+                         me2=ME2[n], stream=stream)
             if record:
                 ev[n][3].record(stream)
 
@@ -331,7 +337,7 @@ def run_ours(args) -> None:
     value = events / elapsed
 
     # e2e: the public plan API with HOST buffers, copies inside the timed region
-    plans = {n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_F32, hel_sampled=True)
+    plans = {n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=cs_mode_for(bg, n), hel_sampled=True)
              for n in NS}
     host_u = {n: U[n].cpu().pin_memory() for n in NS}
     host_h = {n: HEL[n].cpu().pin_memory() for n in NS}
@@ -374,7 +380,9 @@ def run_ours(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S,
                        "pt_min_gev": PT_MIN, "helicities": "sampled, weight 2^n",
-                       "precision": "FP32 currents and colour sum, FP64 Rambo/polarisations/accumulation",
+                       "precision": ("FP32 currents; colour sum on tcgen05 tensor cores (BF16x3 amplitude split, "
+                                     "FP32 accumulate) for n=6..8, FP32 CUDA cores for n=5; "
+                                     "FP64 Rambo/polarisations/per-event accumulation"),
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB of uniforms per step"},
             "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS},
@@ -421,7 +429,7 @@ def run_profile_case(args) -> None:
     for _ in range(args.warmup + 1):
         bg.momenta_rambo(n, u, SQRT_S, PT_MIN, p=p, accept=acc)
         bg.currents_co(n, p, h, prec=bg.BG_F32, sqrt_s=SQRT_S, amps=amps)
-        bg.color_sum(C, amps, True, mode=bg.BG_CS_F32, sqrt_s=SQRT_S, accept=acc, me2=me2)
+        bg.color_sum(C, amps, True, mode=cs_mode_for(bg, n), sqrt_s=SQRT_S, accept=acc, me2=me2)
     torch.cuda.synchronize(dev)
     print(json.dumps({"profile_case": {"n": n, "batch": B, "sum_me2": float(me2.sum().item())}}), flush=True)
     C.close()
