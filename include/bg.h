@@ -197,6 +197,40 @@ int64_t bg_plan_workspace_bytes(const bg_plan* plan);
 bg_status bg_me2_batch(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const int8_t* colors,
                        double* me2, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * bg_me2_batch_noalloc -- the same pipeline as bg_me2_batch (Rambo -> cut ->
+ * polarisations -> colour-ordered recursion -> colour sum) for callers that
+ * cannot allocate device memory when they need |M|^2: for example a host
+ * program whose memory pool has already reserved the GPU's memory, an event
+ * loop that must not stall on the device-wide synchronisation cudaMalloc
+ * and cudaFree imply, or a plug-in that a host framework calls through this
+ * C interface and that owns no memory of its own.  The paper has no
+ * counterpart; it is a deployment variant of the same computation.
+ *   C       colour matrix from bg_colormat_create (made once, at set-up)
+ *   u       [B][4(n-2)] double DEVICE   Rambo uniforms
+ *   hel     [n][B] int8 DEVICE (+-1)    sampled helicities, or NULL for the
+ *                                       sum over all 2^n configurations
+ *   me2     [B] double DEVICE           output, GeV^(8-2n)
+ * prec, cs_mode as for bg_currents_co / bg_color_sum; n = C's multiplicity.
+ * The momenta, cut flags and amplitudes between the kernels live in one
+ * fixed 64 MiB array of device memory that is part of the library image:
+ * every GPU that loads libbg.so holds it until the process exits.  B is
+ * limited by that size (at n = 8 with FP32 amplitudes and sampled
+ * helicities, about 21000 events per call); a larger B returns BG_EINVAL
+ * with the limit in bg_last_error().  The call allocates nothing.  Its first
+ * call on each device looks up the array's device address with the runtime
+ * (that device must be current); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (different streams or threads without ordering between them) race on it
+ * and give wrong results.  Nothing in the array needs to start at zero: a
+ * call writes every byte it reads.  Invalid helicity labels are not
+ * reported in the device status word by this entry point.
+ * Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, double pt_min, double g_s,
+                               const double* q, bg_prec prec, bg_cs_mode cs_mode, const double* u,
+                               const int8_t* hel, double* me2, void* stream);
+
 /* Measurement utility (no counterpart in the paper): a kernel of
  * independent fused multiply-adds in FP32 (prec = BG_F32) or FP64, on
  * `blocks` blocks of 256 threads, `iters` iterations of 16 FMAs per thread.

@@ -29,6 +29,7 @@ SOURCES = [
     "color_sum_tc.cu",
     "colormat.cpp",
     "probe.cu",
+    "noalloc.cu",
 ]
 
 
