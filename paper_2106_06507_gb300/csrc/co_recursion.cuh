@@ -35,10 +35,6 @@
 
 namespace bg {
 
-struct Q4 {
-  double v[4];
-};
-
 __host__ __device__ constexpr int ct_fact(int m) { return m <= 1 ? 1 : m * ct_fact(m - 1); }
 __host__ __device__ constexpr int ct_gcd(int a, int b) { return b == 0 ? a : ct_gcd(b, a % b); }
 

@@ -6,6 +6,11 @@
 
 namespace bg {
 
+// A light-like reference vector passed to kernels by value.
+struct Q4 {
+  double v[4];
+};
+
 // Minkowski product, metric (+,-,-,-), written as a chain of fused
 // multiply-adds: x0 y0 - x1 y1 - x2 y2 - x3 y3.
 template <typename T>
