@@ -238,6 +238,33 @@ bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, d
  * (2 per FMA); time it with events on `stream` to measure the pipe peak. */
 bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * bg_currents_cd -- colour-dressed Berends-Giele recursion with sampled
+ * colours, Eqs. (2.28)-(2.32) (auxiliary tensor field of Eqs. 2.23-2.26 for
+ * the four-gluon vertex), one sampled helicity and colour configuration per
+ * event, returning the Monte-Carlo estimate of the colour- and
+ * helicity-summed |M|^2:
+ *   me2 = w_col * 2^n * g_s^(2n-4) * |A(colours, helicities)|^2,
+ *   w_col = 8^n (adjoint) or 9^n (colour flow).
+ *   p       [4][n][B]    lab momenta (bg_momenta_rambo)
+ *   hel     [n][B] int8  helicity labels +-1
+ *   colors  BG_COL_ADJOINT: [n][B] int8 adjoint index 1..8 (external colour
+ *           matrix T^a, with -i T^a for a = 2, 5, 7: a phase only);
+ *           BG_COL_FLOW: [2n][B] int8, rows 2i and 2i+1 the pair (r_i, c_i)
+ *           in 1..3 (external colour matrix |r_i><c_i|)
+ *   accept  [B] or NULL  events with accept == 0 get 0
+ *   me2     [B] double   output, GeV^(8-2n)
+ *   workspace, workspace_bytes: caller-owned device scratch of at least
+ *           bg_cd_workspace_bytes(n, prec) bytes (per-CTA tables of the
+ *           subset currents); nothing needs to be zeroed.
+ * Supported: 4 <= n <= 12.  Errors: BG_EINVAL, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_cd_workspace_bytes(int n, bg_prec prec, int64_t* bytes);
+bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
+                         const int8_t* colors, bg_color_mode cm, const double* q, bg_prec prec, double g_s,
+                         const uint8_t* accept, double* me2, void* workspace, int64_t workspace_bytes,
+                         void* stream);
+
 /* Device status word of the current device: 0 if no kernel has seen an
  * invalid label since the last reset, else a BG_* code.  Synchronises the
  * device.  bg_device_status_reset clears it. */

@@ -567,6 +567,47 @@ T me2_co_event(int n, double sqrt_s, const T* u, const double* q, const double* 
   return T(fac) * me2;
 }
 
+// Batch colour-dressed |M|^2 estimator with sampled colours and helicities:
+// mode 0 adjoint (colors[B][n] in 1..8, weight 8^n), mode 1 colour flow
+// (colors[B][2n] pairs in 1..3, weight 9^n); helicity weight 2^n; times
+// g^(2n-4).  Events failing the pT cut get 0.  T = double, or long double
+// for the extended-precision reference.
+template <class T>
+void me2_cd_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
+                  const int8_t* colors, int mode, double g, double pt_min, double* me2, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::thread> th;
+  const int d = 4 * (n - 2);
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<Vec<T>> p(n), k(n), eps(n);
+      std::vector<T> ul(d);
+      std::vector<double> E(n * 9);
+      for (long long e = t; e < B; e += nthreads) {
+        for (int i = 0; i < d; ++i) ul[i] = T(u[e * d + i]);
+        rambo(n, sqrt_s, ul.data(), p.data());
+        bool cut = false;
+        for (int i = 2; i < n; ++i)
+          if (std::sqrt(value(p[i].c[1]) * value(p[i].c[1]) + value(p[i].c[2]) * value(p[i].c[2])) <= pt_min)
+            cut = true;
+        if (cut) { me2[e] = 0.0; continue; }
+        outgoing(n, p.data(), k.data());
+        pols_for(n, k.data(), q, hel + e * n, eps.data());
+        for (int i = 0; i < n; ++i) {
+          double M[3][3];
+          if (mode == 0) colour_matrix_adjoint(colors[e * n + i], M);
+          else colour_matrix_flow(colors[e * 2 * n + 2 * i], colors[e * 2 * n + 2 * i + 1], M);
+          for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) E[i * 9 + r * 3 + c] = M[r][c];
+        }
+        T a = amp_cd(n, k.data(), eps.data(), reinterpret_cast<const double(*)[3][3]>(E.data()));
+        double w = std::pow(mode == 0 ? 8.0 : 9.0, n) * std::pow(2.0, n) * std::pow(g, 2 * n - 4);
+        me2[e] = (double)(T(w) * a * a);
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -751,40 +792,14 @@ void or_me2_co_batch_ext(int n, long long B, double sqrt_s, const double* u, con
   for (auto& x : th) x.join();
 }
 
-// Batch colour-dressed |M|^2 estimator with sampled colours and helicities:
-// mode 0 adjoint (colors[B][n] in 1..8, weight 8^n), mode 1 colour flow
-// (colors[B][2n] pairs in 1..3, weight 9^n); helicity weight 2^n; times
-// g^(2n-4).  Events failing the pT cut get 0.
 void or_me2_cd_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
                      const int8_t* colors, int mode, double g, double pt_min, double* me2, int nthreads) {
-  if (nthreads < 1) nthreads = 1;
-  std::vector<std::thread> th;
-  const int d = 4 * (n - 2);
-  for (int t = 0; t < nthreads; ++t)
-    th.emplace_back([&, t]() {
-      std::vector<Vec<double>> p(n), k(n), eps(n);
-      std::vector<double> E(n * 9);
-      for (long long e = t; e < B; e += nthreads) {
-        rambo(n, sqrt_s, u + e * d, p.data());
-        bool cut = false;
-        for (int i = 2; i < n; ++i)
-          if (std::sqrt(p[i].c[1] * p[i].c[1] + p[i].c[2] * p[i].c[2]) <= pt_min) cut = true;
-        if (cut) { me2[e] = 0.0; continue; }
-        outgoing(n, p.data(), k.data());
-        pols_for(n, k.data(), q, hel + e * n, eps.data());
-        for (int i = 0; i < n; ++i) {
-          double M[3][3];
-          if (mode == 0) colour_matrix_adjoint(colors[e * n + i], M);
-          else colour_matrix_flow(colors[e * 2 * n + 2 * i], colors[e * 2 * n + 2 * i + 1], M);
-          for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) E[i * 9 + r * 3 + c] = M[r][c];
-        }
-        double a = amp_cd(n, k.data(), eps.data(), reinterpret_cast<const double(*)[3][3]>(E.data()));
-        double w = std::pow(mode == 0 ? 8.0 : 9.0, n) * std::pow(2.0, n) * std::pow(g, 2 * n - 4);
-        me2[e] = w * a * a;
-      }
-    });
-  for (auto& x : th) x.join();
+  me2_cd_batch<double>(n, B, sqrt_s, u, q, hel, colors, mode, g, pt_min, me2, nthreads);
+}
+
+void or_me2_cd_batch_ext(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
+                         const int8_t* colors, int mode, double g, double pt_min, double* me2, int nthreads) {
+  me2_cd_batch<long double>(n, B, sqrt_s, u, q, hel, colors, mode, g, pt_min, me2, nthreads);
 }
 
 // Gradient of the colour-summed |M|^2 (sampled helicity hel[n]) with

@@ -74,6 +74,7 @@ def lib():
             L.or_me2_co_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, i8p, c_dbl, c_dbl, dp, c_int, c_int]
             L.or_me2_co_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_cd_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_cd_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
             L.or_me2_co_grad.argtypes = [c_int, c_dbl, dp, dp, dp, i8p, c_dbl, dp]
             L.or_me2_co_grad.restype = c_dbl
             _lib = L
@@ -360,16 +361,18 @@ def fp64_noise_floor(n, u, hel=None, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, 
 
 
 def me2_cd(n, u, hel, colors, mode=0, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0,
-           nthreads=None) -> np.ndarray:
-    """Colour-dressed |M|^2 estimator per event with sampled colours."""
+           nthreads=None, ext=False) -> np.ndarray:
+    """Colour-dressed |M|^2 estimator per event with sampled colours
+    (ext: evaluated in extended precision)."""
     u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
     B = u.shape[0]
     q, qp = _d(q)
     hel, hp = _i8(np.asarray(hel).reshape(B, n))
     colors, cp = _i8(np.asarray(colors).reshape(B, -1))
     me2 = np.zeros(B)
-    lib().or_me2_cd_batch(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, cp, mode, g,
-                          pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+    fn = lib().or_me2_cd_batch_ext if ext else lib().or_me2_cd_batch
+    fn(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, cp, mode, g,
+       pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
     return me2
 
 

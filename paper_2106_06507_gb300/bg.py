@@ -71,11 +71,14 @@ def lib() -> ctypes.CDLL:
         L.bg_plan_workspace_bytes.restype = c_i64
         L.bg_me2_batch.argtypes = [vp, c_i64, vp, vp, vp, vp, vp]
         L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
+        L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
+        L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_device_status.argtypes = [ctypes.POINTER(c_int)]
         L.bg_device_status_reset.argtypes = []
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
-                     "bg_plan_create", "bg_me2_batch", "bg_probe_fma"):
+                     "bg_plan_create", "bg_me2_batch", "bg_probe_fma", "bg_cd_workspace_bytes",
+                     "bg_currents_cd"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -182,6 +185,38 @@ def color_sum(C: ColourMatrix, amps: torch.Tensor, hel_sampled: bool, mode: int 
         me2 = torch.empty((B,), dtype=torch.float64, device=amps.device)
     _check(lib().bg_color_sum(C.handle, B, H, _ptr(amps), prec, mode, g_s, sqrt_s, int(bool(hel_sampled)),
                               _ptr(accept), _ptr(me2), _stream(stream)))
+    return me2
+
+
+_cd_ws_cache: dict = {}
+
+
+def cd_workspace_bytes(n: int, prec: int = BG_F32) -> int:
+    b = ctypes.c_int64(0)
+    _check(lib().bg_cd_workspace_bytes(n, prec, ctypes.byref(b)))
+    return int(b.value)
+
+
+def currents_cd(n: int, p: torch.Tensor, hel: torch.Tensor, colors: torch.Tensor, flow: bool = False,
+                prec: int = BG_F32, sqrt_s: float = 1000.0, g_s: float = G_S_DEFAULT, q=DEFAULT_Q,
+                accept: torch.Tensor | None = None, me2=None, workspace: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Colour-dressed |M|^2 estimator per event: p [4, n, B] float64, hel [n, B]
+    int8, colors [n, B] (adjoint, 1..8) or [2n, B] (flow pairs, 1..3) int8.
+    The workspace (bg_cd_workspace_bytes) is cached per (n, prec, device) if
+    not given."""
+    B = p.shape[2]
+    if me2 is None:
+        me2 = torch.empty((B,), dtype=torch.float64, device=p.device)
+    if workspace is None:
+        key = (n, prec, p.device.index)
+        workspace = _cd_ws_cache.get(key)
+        if workspace is None:
+            workspace = torch.empty((cd_workspace_bytes(n, prec),), dtype=torch.uint8, device=p.device)
+            _cd_ws_cache[key] = workspace
+    _check(lib().bg_currents_cd(n, B, sqrt_s, _ptr(p), _ptr(hel), _ptr(colors),
+                                BG_COL_FLOW if flow else BG_COL_ADJOINT, _q(q), prec, g_s, _ptr(accept), _ptr(me2),
+                                _ptr(workspace), workspace.numel(), _stream(stream)))
     return me2
 
 

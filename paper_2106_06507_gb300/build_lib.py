@@ -27,6 +27,8 @@ SOURCES = [
     "co_f64.cu",
     "color_sum.cu",
     "color_sum_tc.cu",
+    "cd_f32.cu",
+    "cd_f64.cu",
     "colormat.cpp",
     "probe.cu",
     "noalloc.cu",

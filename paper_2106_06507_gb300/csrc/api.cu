@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "bg_internal.h"
+#include "cd_recursion.cuh"
 
 namespace bg {
 
@@ -203,6 +204,62 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
                   : (mode == BG_CS_F32) ? launch_color_sum_f32(a, (cudaStream_t)stream)
                                         : launch_color_sum_tc(a, C, device_status_ptr(), (cudaStream_t)stream);
   return cuda_check(e, "bg_color_sum");
+}
+
+static int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+bg_status bg_cd_workspace_bytes(int n, bg_prec prec, int64_t* bytes) {
+  if (!bytes) return fail(BG_EINVAL, "bg_cd_workspace_bytes: NULL");
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_cd_workspace_bytes: n must be in 4..12");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_cd_workspace_bytes: invalid precision");
+  const int sms = device_sms();
+  if (sms <= 0) return fail(BG_ECUDA, "bg_cd_workspace_bytes: no device");
+  const size_t slab = (prec == BG_F32) ? cd_slab_bytes_f32(n) : cd_slab_bytes_f64(n);
+  *bytes = (int64_t)slab * cd_grid_ctas(sms);
+  return BG_OK;
+}
+
+bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
+                         const int8_t* colors, bg_color_mode cm, const double* q, bg_prec prec, double g_s,
+                         const uint8_t* accept, double* me2, void* workspace, int64_t workspace_bytes,
+                         void* stream) {
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_currents_cd: n must be in 4..12");
+  if (B < 0) return fail(BG_EINVAL, "bg_currents_cd: B < 0");
+  if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_currents_cd: sqrt_s must be > 0");
+  if (cm != BG_COL_ADJOINT && cm != BG_COL_FLOW) return fail(BG_EINVAL, "bg_currents_cd: invalid colour mode");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_currents_cd: invalid precision");
+  if (!q) return fail(BG_EINVAL, "bg_currents_cd: q is NULL");
+  const double qv = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(q[0] > 0.0) || std::fabs(q[0] - qv) > 1e-12 * q[0])
+    return fail(BG_EINVAL, "bg_currents_cd: q must be light-like with q0 > 0");
+  if (B == 0) return BG_OK;
+  if (!p || !hel || !colors || !me2 || !workspace) return fail(BG_EINVAL, "bg_currents_cd: NULL argument");
+  int64_t need = 0;
+  bg_status st = bg_cd_workspace_bytes(n, prec, &need);
+  if (st != BG_OK) return st;
+  if (workspace_bytes < need)
+    return fail(BG_EINVAL, "bg_currents_cd: workspace smaller than bg_cd_workspace_bytes(n, prec)");
+  if (!aligned(workspace, 256) || !aligned(p, 8) || !aligned(me2, 8))
+    return fail(BG_EINVAL, "bg_currents_cd: misaligned pointer (workspace needs 256-byte alignment)");
+  CdParams prm;
+  prm.B = B;
+  prm.inv_sqrt_s = 1.0 / sqrt_s;
+  const double wcol = std::pow(cm == BG_COL_FLOW ? 9.0 : 8.0, n);
+  prm.scale = wcol * std::ldexp(1.0, n) * std::pow(g_s, 2 * n - 4) * std::pow(sqrt_s, 8 - 2 * n) *
+              std::ldexp(1.0, -(n - 2));
+  prm.flow = (cm == BG_COL_FLOW) ? 1 : 0;
+  for (int m = 0; m < 4; ++m) prm.q.v[m] = q[m];
+  const int sms = device_sms();
+  cudaError_t e = (prec == BG_F32) ? launch_cd_f32(n, prm, p, hel, colors, accept, me2, workspace,
+                                                   device_status_ptr(), sms, (cudaStream_t)stream)
+                                   : launch_cd_f64(n, prm, p, hel, colors, accept, me2, workspace,
+                                                   device_status_ptr(), sms, (cudaStream_t)stream);
+  return cuda_check(e, "bg_currents_cd");
 }
 
 bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream) {

@@ -58,6 +58,17 @@ struct ColourSumArgs {
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
 cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
 
+// Colour-dressed recursion (cd_f32.cu, cd_f64.cu): per-CTA workspace slab
+// bytes and launchers; CdParams is defined in cd_recursion.cuh.
+struct CdParams;
+size_t cd_slab_bytes_f32(int n);
+size_t cd_slab_bytes_f64(int n);
+int cd_grid_ctas(int sms);
+cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
+                          const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
+cudaError_t launch_cd_f64(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
+                          const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
+
 // Tensor-core colour sum (color_sum_tc.cu).
 bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<uint16_t>& tiles, double& g, int& nt,
                     int& ntiles, int& kchunks);

@@ -2,6 +2,7 @@
 #include "cd_recursion.cuh"
 
 namespace bg {
+int cd_grid_ctas(int sms) { return cd_grid(sms); }
 size_t cd_slab_bytes_f32(int n) { return cd_slab_bytes_t<float>(n); }
 cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
