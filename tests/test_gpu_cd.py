@@ -3,6 +3,11 @@
 the brute-force identity sum over all colours = colour-ordered |M|^2 on the
 GPU itself.
 
+Colour assignments whose amplitude vanishes by colour algebra come out as
+rounding noise (~1e-33 of a typical |M|^2 in FP64) rather than exactly 0:
+events whose extended-precision value is below 1e-16 of the batch's median
+non-zero |M|^2 are treated as zeros and must stay below 1e-10 of it.
+
 Tolerances (derived in the design notes):
   FP64: compared with the oracle in extended precision; as accurate as the
   plain FP64 oracle (median < 1e-13, events above 1e-12 at most 2 + 1% + 4x
@@ -49,9 +54,19 @@ def colours(n, B, seed, flow):
     return inputs.flow_colours(n, B, seed=seed) if flow else inputs.adjoint_colours(n, B, seed=seed)
 
 
+def split_zeros(got, ref):
+    """Mask of the events that are not structural zeros; checks the zeros."""
+    pos = ref[ref > 0]
+    scale = np.median(pos) if pos.size else 1.0
+    zero = ref <= 1e-16 * scale
+    assert np.all(np.abs(got[zero]) <= 1e-10 * scale)
+    return ~zero
+
+
 def assert_fp64_like(got, ext, f64):
-    assert np.array_equal(got == 0, ext == 0)
-    nz = ext != 0
+    nz = split_zeros(got, ext)
+    if not nz.any():
+        return
     rel = np.abs(got[nz] / ext[nz] - 1.0)
     floor = np.abs(f64[nz] / ext[nz] - 1.0)
     assert np.median(rel) < 1e-13
@@ -84,8 +99,7 @@ def test_cd_fp32_parity(bg, oracle, n, B, flow):
     cols = colours(n, B, 80 + n, flow)
     got = run_cd(bg, n, u, hel, cols, flow, bg.BG_F32)
     ref = oracle.me2_cd(n, u, hel, cols, 1 if flow else 0, sqrt_s=SQRT_S, pt_min=PT_MIN)
-    nz = ref != 0
-    assert np.all(got[~nz] == 0)
+    nz = split_zeros(got, ref)
     assert nz.sum() >= 2
     rel = np.abs(got[nz] / ref[nz] - 1.0)
     assert np.median(rel) < 1e-5
@@ -99,8 +113,7 @@ def test_cd_fp64_n10_sampled(bg, oracle):
     cols = colours(n, B, 90, False)
     got = run_cd(bg, n, u, hel, cols, False, bg.BG_F64)
     ref = oracle.me2_cd(n, u, hel, cols, 0, sqrt_s=SQRT_S, pt_min=PT_MIN)
-    nz = ref != 0
-    assert np.array_equal(got == 0, ref == 0)
+    nz = split_zeros(got, ref)
     assert np.all(np.abs(got[nz] / ref[nz] - 1.0) < 1e-9)
 
 
