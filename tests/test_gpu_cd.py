@@ -5,8 +5,9 @@ GPU itself.
 
 Colour assignments whose amplitude vanishes by colour algebra come out as
 rounding noise (~1e-33 of a typical |M|^2 in FP64) rather than exactly 0:
-events whose extended-precision value is below 1e-16 of the batch's largest
-|M|^2 are treated as zeros and must stay below 1e-10 of it.
+events whose reference value is below 1e-16 of the batch's largest |M|^2 are
+treated as zeros and must stay below 1e-10 (FP64) or 1e-6 (FP32: the squared
+FP32 noise of an amplitude that cancels) of it.
 
 Tolerances (derived in the design notes):
   FP64: compared with the oracle in extended precision; as accurate as the
@@ -54,11 +55,11 @@ def colours(n, B, seed, flow):
     return inputs.flow_colours(n, B, seed=seed) if flow else inputs.adjoint_colours(n, B, seed=seed)
 
 
-def split_zeros(got, ref):
+def split_zeros(got, ref, tol=1e-10):
     """Mask of the events that are not structural zeros; checks the zeros."""
     scale = ref.max() if ref.size and ref.max() > 0 else 1.0
     zero = ref <= 1e-16 * scale
-    assert np.all(np.abs(got[zero]) <= 1e-10 * scale)
+    assert np.all(np.abs(got[zero]) <= tol * scale)
     return ~zero
 
 
@@ -98,7 +99,7 @@ def test_cd_fp32_parity(bg, oracle, n, B, flow):
     cols = colours(n, B, 80 + n, flow)
     got = run_cd(bg, n, u, hel, cols, flow, bg.BG_F32)
     ref = oracle.me2_cd(n, u, hel, cols, 1 if flow else 0, sqrt_s=SQRT_S, pt_min=PT_MIN)
-    nz = split_zeros(got, ref)
+    nz = split_zeros(got, ref, tol=1e-6)
     assert nz.sum() >= 2
     rel = np.abs(got[nz] / ref[nz] - 1.0)
     assert np.median(rel) < 1e-5
