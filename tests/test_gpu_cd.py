@@ -90,7 +90,7 @@ def test_cd_fp64_parity(bg, oracle, n, B, flow):
 
 
 @pytest.mark.parametrize("flow", [False, True])
-@pytest.mark.parametrize("n,B", [(6, 400), (8, 200), (10, 24), (12, 4)])
+@pytest.mark.parametrize("n,B", [(6, 400), (8, 200), (10, 24), (12, 12)])
 def test_cd_fp32_parity(bg, oracle, n, B, flow):
     # only 3-7 % of sampled colour flows are balanced (others give exactly 0)
     B = (40 if n >= 10 else 25) * B if flow else B
