@@ -68,6 +68,20 @@ def flow_colours(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.
     return (1 + np.minimum((u * 3.0).astype(np.int64), 2)).astype(np.int8).reshape(batch, 2 * n)
 
 
+def balanced_flow_colours(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.ndarray:
+    """[batch, 2n] int8 colour-flow pairs whose column indices are a random
+    permutation of the row indices (every colour appears equally often as a
+    row and as a column index): uniform rows, uniformly permuted columns."""
+    rows = flow_colours(n, batch, seed=seed, first_event=first_event)[:, 0::2].astype(np.int64)
+    keys = raw64(seed, STREAM_COLOUR + 16 * n + 12, batch * n, first_event * n).reshape(batch, n)
+    perm = np.argsort(keys, axis=1, kind="stable")
+    cols = np.take_along_axis(rows, perm, axis=1)
+    out = np.empty((batch, 2 * n), dtype=np.int8)
+    out[:, 0::2] = rows
+    out[:, 1::2] = cols
+    return out
+
+
 def multiplicities(batch: int, n_min: int, n_max: int, seed: int = 0) -> np.ndarray:
     """[batch] int32 multiplicities uniform in n_min..n_max."""
     u = uniforms(seed, STREAM_MULTIPLICITY, batch)
