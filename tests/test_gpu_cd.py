@@ -90,10 +90,11 @@ def test_cd_fp64_parity(bg, oracle, n, B, flow):
 
 
 @pytest.mark.parametrize("flow", [False, True])
-@pytest.mark.parametrize("n,B", [(6, 400), (8, 200), (10, 48), (12, 24)])
+@pytest.mark.parametrize("n,B", [(6, 400), (8, 200), (10, 64), (12, 96)])
 def test_cd_fp32_parity(bg, oracle, n, B, flow):
     # colour flows drawn balanced (unbalanced ones give exactly 0); no cut, so
-    # that the few-event high-multiplicity samples have non-zero |M|^2
+    # that the few-event high-multiplicity samples have non-zero |M|^2 (at
+    # n = 12 only ~6 % of adjoint colour samples do)
     u = inputs.rambo_uniforms(n, B, seed=80 + n)
     hel = inputs.helicities(n, B, seed=80 + n)
     cols = inputs.balanced_flow_colours(n, B, seed=80 + n) if flow else colours(n, B, 80 + n, False)
