@@ -107,15 +107,18 @@ def test_cd_fp32_parity(bg, oracle, n, B, flow):
     assert np.quantile(rel, 0.99) < 1e-3
 
 
-def test_cd_fp64_n10_sampled(bg, oracle):
-    n, B = 10, 6
+@pytest.mark.parametrize("flow", [False, True])
+def test_cd_fp64_n10(bg, oracle, flow):
+    n, B = 10, 64
     u = inputs.rambo_uniforms(n, B, seed=90)
     hel = inputs.helicities(n, B, seed=90)
-    cols = colours(n, B, 90, False)
-    got = run_cd(bg, n, u, hel, cols, False, bg.BG_F64)
-    ref = oracle.me2_cd(n, u, hel, cols, 0, sqrt_s=SQRT_S, pt_min=PT_MIN)
-    nz = split_zeros(got, ref)
-    assert np.all(np.abs(got[nz] / ref[nz] - 1.0) < 1e-9)
+    cols = inputs.balanced_flow_colours(n, B, seed=90) if flow else colours(n, B, 90, False)
+    got = run_cd(bg, n, u, hel, cols, flow, bg.BG_F64, pt_min=-1.0)
+    mode = 1 if flow else 0
+    ext = oracle.me2_cd(n, u, hel, cols, mode, sqrt_s=SQRT_S, pt_min=-1.0, ext=True)
+    f64 = oracle.me2_cd(n, u, hel, cols, mode, sqrt_s=SQRT_S, pt_min=-1.0)
+    assert (ext > 1e-16 * ext.max()).sum() >= 2
+    assert_fp64_like(got, ext, f64)
 
 
 @pytest.mark.parametrize("flow", [False, True])
