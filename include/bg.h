@@ -173,6 +173,7 @@ typedef struct {
   bg_algo algo;
   bg_color_mode color_mode; /* BG_ALGO_CD */
   int hel_sampled;
+  int grad;           /* 1: also allocate the workspace of bg_me2_grad */
 } bg_plan_desc;
 typedef struct bg_plan bg_plan;
 /* Errors: BG_EINVAL (desc), BG_EUNSUPPORTED, BG_ENOMEM, BG_ECUDA. */
@@ -230,6 +231,26 @@ bg_status bg_me2_batch(bg_plan* plan, int64_t B, const double* u, const int8_t* 
 bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, double pt_min, double g_s,
                                const double* q, bg_prec prec, bg_cs_mode cs_mode, const double* u,
                                const int8_t* hel, double* me2, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * bg_me2_grad -- |M|^2 and its gradient with respect to the 4(n-2) Rambo
+ * uniforms of each event, d|M|^2/du, by reverse mode through the colour sum
+ * (Eq. 2.16: d|M|^2/dA = 2 scale C A), the colour-ordered recursion (Eqs.
+ * 2.20-2.22, one ordering per thread, adjoint currents in shared memory),
+ * the light-cone polarisations (Eq. 2.7) and Rambo (forward-mode Jacobian,
+ * FP64).  The paper computes no gradients; this serves gradient-trained
+ * phase-space mappings.
+ *   plan      created with algo BG_ALGO_CO, hel_sampled = 1, grad = 1, n <= 8
+ *   u         [B][4(n-2)] double DEVICE
+ *   hel       [n][B] int8 DEVICE
+ *   upstream  [B] double DEVICE, dL/d|M|^2 per event, or NULL for 1
+ *   me2       [B] double DEVICE output, or NULL
+ *   grad_u    [B][4(n-2)] double DEVICE output: upstream * d|M|^2/du
+ * Events failing the cut get |M|^2 = 0 and a zero gradient (the cut is a
+ * step function).  Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_me2_grad(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const double* upstream,
+                      double* me2, double* grad_u, void* stream);
 
 /* Measurement utility (no counterpart in the paper): a kernel of
  * independent fused multiply-adds in FP32 (prec = BG_F32) or FP64, on

@@ -35,7 +35,7 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("max_batch", ctypes.c_int64), ("sqrt_s", ctypes.c_double),
                 ("pt_min", ctypes.c_double), ("g_s", ctypes.c_double), ("q", ctypes.c_double * 4),
                 ("prec", ctypes.c_int), ("cs_mode", ctypes.c_int), ("algo", ctypes.c_int),
-                ("color_mode", ctypes.c_int), ("hel_sampled", ctypes.c_int)]
+                ("color_mode", ctypes.c_int), ("hel_sampled", ctypes.c_int), ("grad", ctypes.c_int)]
 
 
 class BGError(RuntimeError):
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
         L.bg_plan_workspace_bytes.argtypes = [vp]
         L.bg_plan_workspace_bytes.restype = c_i64
         L.bg_me2_batch.argtypes = [vp, c_i64, vp, vp, vp, vp, vp]
+        L.bg_me2_grad.argtypes = [vp, c_i64, vp, vp, vp, vp, vp, vp]
         L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
@@ -78,7 +79,7 @@ def lib() -> ctypes.CDLL:
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_probe_fma", "bg_cd_workspace_bytes",
-                     "bg_currents_cd"):
+                     "bg_currents_cd", "bg_me2_grad"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -225,8 +226,10 @@ class Plan:
 
     def __init__(self, n: int, max_batch: int, sqrt_s: float = 1000.0, pt_min: float = -1.0,
                  g_s: float = G_S_DEFAULT, q=DEFAULT_Q, prec: int = BG_F32, cs_mode: int = BG_CS_F32,
-                 algo: int = BG_ALGO_CO, color_mode: int = BG_COL_ADJOINT, hel_sampled: bool = True):
+                 algo: int = BG_ALGO_CO, color_mode: int = BG_COL_ADJOINT, hel_sampled: bool = True,
+                 grad: bool = False):
         d = PlanDesc()
+        d.grad = int(grad)
         d.n, d.max_batch, d.sqrt_s, d.pt_min, d.g_s = n, max_batch, sqrt_s, pt_min, g_s
         for i in range(4):
             d.q[i] = float(q[i])
@@ -252,6 +255,17 @@ class Plan:
         _check(lib().bg_me2_batch(self._h, B, _vptr(u), _vptr(hel), _vptr(colors), _vptr(out), _stream(stream)))
         return out
 
+    def grad(self, u: torch.Tensor, hel: torch.Tensor, upstream: torch.Tensor | None = None,
+             me2: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """d|M|^2/du (times `upstream`) for u [B, 4(n-2)] float64 CUDA, hel
+        [n, B] int8 CUDA; optionally also writes |M|^2 into `me2`."""
+        B = u.shape[0]
+        if out is None:
+            out = torch.empty_like(u)
+        _check(lib().bg_me2_grad(self._h, B, _vptr(u), _vptr(hel), _vptr(upstream), _vptr(me2), _vptr(out),
+                                 _stream(stream)))
+        return out
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().bg_plan_destroy(self._h)
@@ -262,6 +276,27 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Me2Function(torch.autograd.Function):
+    """|M|^2(u) as a differentiable function of the Rambo uniforms: forward
+    runs bg_me2_batch, backward bg_me2_grad with the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, u, hel, plan):
+        ctx.plan = plan
+        ctx.save_for_backward(u, hel)
+        return plan.me2(u.contiguous(), hel)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        u, hel = ctx.saved_tensors
+        g = ctx.plan.grad(u.contiguous(), hel, upstream=grad_out.contiguous())
+        return g, None, None
+
+
+def me2_autograd(u: torch.Tensor, hel: torch.Tensor, plan: "Plan") -> torch.Tensor:
+    return Me2Function.apply(u, hel, plan)
 
 
 def _vptr(x):

@@ -32,6 +32,8 @@ SOURCES = [
     "colormat.cpp",
     "probe.cu",
     "noalloc.cu",
+    "co_grad.cu",
+    "grad_rambo.cu",
 ]
 
 

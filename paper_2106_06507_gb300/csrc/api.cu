@@ -283,7 +283,7 @@ static bool is_device_ptr(const void* ptr) {
 
 void bg_plan_destroy(bg_plan* P) {
   if (!P) return;
-  void* bufs[] = {P->u, P->hel, P->colors, P->p, P->accept, P->amps, P->me2};
+  void* bufs[] = {P->u, P->hel, P->colors, P->p, P->accept, P->amps, P->me2, P->Y, P->kbar, P->ebar};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->C) bg_colormat_destroy(P->C);
@@ -305,6 +305,8 @@ bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
   if (n > kMaxNCO) return fail(BG_EUNSUPPORTED, "bg_plan_create: colour-ordered path supports n <= 9");
   if (d->cs_mode != BG_CS_F64 && d->cs_mode != BG_CS_F32 && d->cs_mode != BG_CS_TC_BF16)
     return fail(BG_EINVAL, "bg_plan_create: invalid cs_mode");
+  if (d->grad && (n > 8 || !d->hel_sampled))
+    return fail(BG_EUNSUPPORTED, "bg_plan_create: gradients need n <= 8 and sampled helicities");
   if (d->cs_mode == BG_CS_TC_BF16 && (n < 6 || n > 8 || !d->hel_sampled))
     return fail(BG_EUNSUPPORTED, "bg_plan_create: tensor-core colour sum needs 6 <= n <= 8, sampled helicities");
   const double qv = std::sqrt(d->q[1] * d->q[1] + d->q[2] * d->q[2] + d->q[3] * d->q[3]);
@@ -333,9 +335,13 @@ bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
               {(void**)&P->p, (size_t)B * 4 * n * sizeof(double)},
               {(void**)&P->accept, (size_t)B},
               {&P->amps, amp_bytes},
-              {(void**)&P->me2, (size_t)B * sizeof(double)}};
+              {(void**)&P->me2, (size_t)B * sizeof(double)},
+              {&P->Y, d->grad ? amp_bytes : 0},
+              {(void**)&P->kbar, d->grad ? (size_t)B * n * 4 * sizeof(double) : 0},
+              {(void**)&P->ebar, d->grad ? (size_t)B * n * 4 * sizeof(double) : 0}};
   P->bytes = (int64_t)P->C->k * P->C->k * 12;
   for (auto& r : reqs) {
+    if (r.bytes == 0) continue;
     if (cudaMalloc(r.ptr, r.bytes) != cudaSuccess) {
       cudaGetLastError();
       bg_plan_destroy(P);
@@ -389,6 +395,52 @@ bg_status bg_me2_batch(bg_plan* P, int64_t B, const double* u, const int8_t* hel
     st = cuda_check(cudaStreamSynchronize(s), "bg_me2_batch: synchronise");
   }
   return st;
+}
+
+bg_status bg_me2_grad(bg_plan* P, int64_t B, const double* u, const int8_t* hel, const double* upstream,
+                      double* me2, double* grad_u, void* stream) {
+  if (!P) return fail(BG_EINVAL, "bg_me2_grad: plan is NULL");
+  if (!P->d.grad || !P->kbar) return fail(BG_EINVAL, "bg_me2_grad: plan was not created with grad = 1");
+  if (B < 0 || B > P->d.max_batch) return fail(BG_EINVAL, "bg_me2_grad: B outside 0..max_batch");
+  if (B == 0) return BG_OK;
+  if (!u || !hel || !grad_u) return fail(BG_EINVAL, "bg_me2_grad: NULL u, hel or grad_u");
+  if (!is_device_ptr(u) || !is_device_ptr(hel) || !is_device_ptr(grad_u) || (me2 && !is_device_ptr(me2)) ||
+      (upstream && !is_device_ptr(upstream)))
+    return fail(BG_EINVAL, "bg_me2_grad: all buffers must be device memory");
+  const int n = P->d.n;
+  cudaStream_t s = (cudaStream_t)stream;
+  bg_status st = bg_momenta_rambo(n, B, P->d.sqrt_s, u, P->p, P->d.pt_min, P->accept, stream);
+  if (st != BG_OK) return st;
+  st = bg_currents_co(n, B, P->d.sqrt_s, P->p, hel, P->d.q, P->d.prec, P->amps, stream);
+  if (st != BG_OK) return st;
+  ColourSumArgs a;
+  a.n = n;
+  a.B = B;
+  a.H = 1;
+  a.k = P->k;
+  a.amps = P->amps;
+  a.amps_f32 = (P->d.prec == BG_F32);
+  a.C64 = P->C->C64;
+  a.C32 = P->C->C32;
+  a.scale = std::pow(P->d.g_s, 2 * n - 4) * std::pow(P->d.sqrt_s, 8 - 2 * n) * std::ldexp(1.0, n);
+  a.accept = P->accept;
+  a.me2 = me2 ? me2 : P->me2;
+  a.Y = P->Y;
+  cudaError_t e = (P->d.cs_mode == BG_CS_F64)   ? launch_color_sum_f64(a, s)
+                  : (P->d.cs_mode == BG_CS_F32) ? launch_color_sum_f32(a, s)
+                                                : launch_color_sum_tc(a, P->C, device_status_ptr(), s);
+  st = cuda_check(e, "bg_me2_grad: colour sum");
+  if (st != BG_OK) return st;
+  e = (P->d.prec == BG_F32)
+          ? launch_co_grad_f32(n, B, P->d.sqrt_s, P->p, hel, P->d.q, static_cast<const float*>(P->Y), P->kbar,
+                               P->ebar, device_status_ptr(), s)
+          : launch_co_grad_f64(n, B, P->d.sqrt_s, P->p, hel, P->d.q, static_cast<const double*>(P->Y), P->kbar,
+                               P->ebar, device_status_ptr(), s);
+  st = cuda_check(e, "bg_me2_grad: reverse recursion");
+  if (st != BG_OK) return st;
+  return cuda_check(launch_rambo_grad(n, B, P->d.sqrt_s, u, P->p, hel, P->d.q, P->kbar, P->ebar, a.scale, upstream,
+                                      P->accept, grad_u, s),
+                    "bg_me2_grad: polarisations and Rambo");
 }
 
 bg_status bg_device_status(int* status) {

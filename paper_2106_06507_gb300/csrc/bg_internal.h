@@ -54,6 +54,7 @@ struct ColourSumArgs {
   double scale;       // g^(2n-4) sqrt_s^(8-2n) w
   const uint8_t* accept;
   double* me2;
+  void* Y = nullptr;   // optional output (C A)[B][H][k], same type as amps
 };
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
 cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
@@ -68,6 +69,15 @@ cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
 cudaError_t launch_cd_f64(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
+
+// Gradient (co_grad.cu, grad_rambo.cu).
+cudaError_t launch_co_grad_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                               const float* Y, double* kbar, double* ebar, int* status, cudaStream_t s);
+cudaError_t launch_co_grad_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                               const double* Y, double* kbar, double* ebar, int* status, cudaStream_t s);
+cudaError_t launch_rambo_grad(int n, int64_t B, double sqrt_s, const double* u, const double* p, const int8_t* hel,
+                              const double* q, const double* kbar, const double* ebar, double scale,
+                              const double* upstream, const uint8_t* accept, double* grad_u, cudaStream_t s);
 
 // Tensor-core colour sum (color_sum_tc.cu).
 bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<uint16_t>& tiles, double& g, int& nt,
@@ -90,6 +100,9 @@ struct bg_plan {
   uint8_t* accept;  // [max_batch]
   void* amps;       // [max_batch][H][k]
   double* me2;      // [max_batch] staging for a host output
+  void* Y;          // [max_batch][k] (C A), gradient plans only
+  double* kbar;     // [max_batch][n][4] momentum adjoints, gradient plans only
+  double* ebar;     // [max_batch][n][4] polarisation adjoints, gradient plans only
   int64_t bytes;
 };
 

@@ -21,7 +21,7 @@ template <typename TIn, typename TC>
 __global__ void __launch_bounds__(NT) color_sum_kernel(int64_t B, int H, int k, const TIn* __restrict__ A,
                                                        const TC* __restrict__ C, double scale,
                                                        const uint8_t* __restrict__ accept,
-                                                       double* __restrict__ me2) {
+                                                       double* __restrict__ me2, TIn* __restrict__ Y) {
   __shared__ __align__(16) TC Cs[KT][TA];
   __shared__ __align__(16) TC As[KT][TE];
   __shared__ double red[16][TE];
@@ -81,7 +81,10 @@ __global__ void __launch_bounds__(NT) color_sum_kernel(int64_t B, int H, int k, 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int a = a0 + ty * 4 + i;
-          if (a < k) s += (double)A[e * strideE + (int64_t)h * k + a] * (double)acc[i][j];
+          if (a < k) {
+            s += (double)A[e * strideE + (int64_t)h * k + a] * (double)acc[i][j];
+            if (Y) Y[e * strideE + (int64_t)h * k + a] = (TIn)acc[i][j];
+          }
         }
         part[j] += s;
       }
@@ -106,7 +109,7 @@ template <typename TIn, typename TC>
 cudaError_t launch_cs(const ColourSumArgs& a, const TC* C, cudaStream_t s) {
   const int64_t blocks = (a.B + TE - 1) / TE;
   color_sum_kernel<TIn, TC><<<(unsigned)blocks, NT, 0, s>>>(a.B, a.H, a.k, static_cast<const TIn*>(a.amps), C,
-                                                           a.scale, a.accept, a.me2);
+                                                           a.scale, a.accept, a.me2, static_cast<TIn*>(a.Y));
   return cudaGetLastError();
 }
 

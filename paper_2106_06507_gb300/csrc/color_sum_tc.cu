@@ -151,12 +151,14 @@ struct TcParams {
   int ntiles;   // N tiles
   int kchunks;  // K chunks of TC_KC
   double scale; // includes the gcd of C
+  float g;      // gcd of C (Y = g D)
 };
 
 template <typename TIn>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     color_sum_tc_kernel(TcParams P, const TIn* __restrict__ A, const __nv_bfloat16* __restrict__ Ct,
-                        const uint8_t* __restrict__ accept, double* __restrict__ me2, int* __restrict__ status) {
+                        const uint8_t* __restrict__ accept, double* __restrict__ me2, int* __restrict__ status,
+                        TIn* __restrict__ Y) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned carve-up
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -325,7 +327,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (e < P.B) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (m0 + j < P.k) part = fmaf((float)row[m0 + j], d[j], part);
+            if (m0 + j < P.k) {
+              part = fmaf((float)row[m0 + j], d[j], part);
+              if (Y) Y[e * (int64_t)P.k + m0 + j] = (TIn)(P.g * d[j]);
+            }
         }
       }
       acc += (double)part;
@@ -402,6 +407,7 @@ cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, in
   P.ntiles = C->tc_ntiles;
   P.kchunks = C->tc_kchunks;
   P.scale = a.scale * C->tc_g;
+  P.g = (float)C->tc_g;
   const size_t smem = tc_smem_bytes(P.nt);
   const unsigned blocks = (unsigned)((a.B + TC_M - 1) / TC_M);
   if (a.amps_f32) {
@@ -409,13 +415,13 @@ cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, in
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const float*>(a.amps), C->tc_tiles, a.accept, a.me2,
-                                          status);
+                                          status, static_cast<float*>(a.Y));
   } else {
     auto kern = color_sum_tc_kernel<double>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const double*>(a.amps), C->tc_tiles, a.accept, a.me2,
-                                          status);
+                                          status, static_cast<double*>(a.Y));
   }
   return cudaGetLastError();
 }
