@@ -247,7 +247,9 @@ bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, d
  *   me2       [B] double DEVICE output, or NULL
  *   grad_u    [B][4(n-2)] double DEVICE output: upstream * d|M|^2/du
  * Events failing the cut get |M|^2 = 0 and a zero gradient (the cut is a
- * step function).  Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
+ * step function).  The sums over orderings use shared-memory atomics:
+ * repeated calls agree to rounding of the recursion's type, not bit for bit.
+ * Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
  * ------------------------------------------------------------------------- */
 bg_status bg_me2_grad(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const double* upstream,
                       double* me2, double* grad_u, void* stream);
