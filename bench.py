@@ -48,8 +48,11 @@ WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqr
 # DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
 # n = 8, 2^20 events, scaled from a 2^16-event capture by the number of
 # events), valid only for the kernel sources it was taken from.
-NCU_TRAFFIC = {"sources_sha1": "3c4b40b2104c8baf538a2ff0541891090c7c710c",
-               "bytes_per_launch": 16 * (18204416 + 128165120)}  # 2^16-event capture x 16
+NCU_TRAFFIC = {"sources_sha1": "c98db25cb47d095815fb005026892cd207c32c9e",
+               "bytes_per_launch": 16 * (17393408 + 127698432)}  # 2^16-event capture x 16
+# Executed FP32 operations per event of the dominant kernel at n = 8 (ncu sass
+# counts of the same capture: 2 x FFMA + FADD + FMUL), valid for the same sources.
+NCU_EXECUTED = {"sources_sha1": "c98db25cb47d095815fb005026892cd207c32c9e", "flops_per_event": 2524568}
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
 
@@ -367,8 +370,14 @@ def run_ours(args) -> None:
     achieved = flops / dom_s / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     traffic = None
+    executed = None
     if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
+    if NCU_EXECUTED["sources_sha1"] == sources_sha1() and n_dom == 8:
+        ex = NCU_EXECUTED["flops_per_event"] * BATCH / dom_s / 1e12
+        executed = {"achieved": ex, "frac": ex / (NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
+                    "flops_per_event": NCU_EXECUTED["flops_per_event"],
+                    "source": "ncu sass counts 2*FFMA+FADD+FMUL of a 2^16-event capture"}
     total_ms = sum(sum(v) for v in kernel_ms.values()) / args.steps
     shares = {f"n{n}_{name}": kernel_ms[n][j] / args.steps / total_ms
               for n in NS for j, name in enumerate(("rambo", "co_recursion", "colour_sum"))}
@@ -392,6 +401,7 @@ def run_ours(args) -> None:
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "flops_per_launch": flops, "flops_model": "canonical (V3=65, V4=46, prop=12, final=7)",
+                         "executed": executed,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts, max clock)",
                          "probe_fp32_tflops": probe_f32, "probe_fp64_tflops": probe_f64},
             "cpu_baseline": None,

@@ -62,9 +62,10 @@ typedef enum { BG_F64 = 0, BG_F32 = 1 } bg_prec;
 /* Colour-sum arithmetic: FP64 CUDA cores; FP32 CUDA cores; tensor cores
  * (tcgen05, BF16 inputs: C/gcd exact in BF16, amplitudes split into three
  * BF16 planes hi+mid+lo carrying 24 significant bits; FP32 accumulation in
- * tensor memory; FP64 per-event accumulation).  BG_CS_TC_BF16 needs
- * 6 <= n <= 8 (for n = 9 some C/gcd entries need more than 8 significant
- * bits: BG_EUNSUPPORTED) and one polarisation configuration per event. */
+ * tensor memory; FP64 per-event accumulation).  At n = 9 some C/gcd entries
+ * need 9-10 significant bits and C is split into two exact BF16 planes
+ * (hi + lo).  BG_CS_TC_BF16 needs 6 <= n <= 9 and one polarisation
+ * configuration per event. */
 typedef enum { BG_CS_F64 = 0, BG_CS_F32 = 1, BG_CS_TC_BF16 = 2 } bg_cs_mode;
 
 /* Sampled-colour representation for the colour-dressed recursion. */

@@ -83,6 +83,7 @@ bg_status bg_colormat_create(int n, bg_colormat** out) {
   C->tc_tiles = nullptr;
   C->tc_g = 0.0;
   C->tc_nt = C->tc_ntiles = C->tc_kchunks = 0;
+  C->tc_cpl = 1;
   cudaGetDevice(&C->device);
   colour_row(n, C->row);
   std::vector<double> dense;
@@ -106,7 +107,7 @@ bg_status bg_colormat_create(int n, bg_colormat** out) {
     return st;
   }
   std::vector<uint16_t> tiles;
-  if (build_tc_tiles(n, dense, C->k, tiles, C->tc_g, C->tc_nt, C->tc_ntiles, C->tc_kchunks)) {
+  if (build_tc_tiles(n, dense, C->k, tiles, C->tc_g, C->tc_nt, C->tc_ntiles, C->tc_kchunks, C->tc_cpl)) {
     if (cudaMalloc(&C->tc_tiles_raw, tiles.size() * 2) != cudaSuccess) {
       cudaGetLastError();
       bg_colormat_destroy(C);
@@ -181,7 +182,7 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
   if (mode != BG_CS_F64 && mode != BG_CS_F32 && mode != BG_CS_TC_BF16)
     return fail(BG_EINVAL, "bg_color_sum: invalid mode");
   if (mode == BG_CS_TC_BF16 && (!C->tc_tiles || H != 1))
-    return fail(BG_EUNSUPPORTED, "bg_color_sum: tensor-core mode needs 6 <= n <= 8 and H = 1");
+    return fail(BG_EUNSUPPORTED, "bg_color_sum: tensor-core mode needs 6 <= n <= 9 and H = 1");
   if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_color_sum: sqrt_s must be > 0");
   if (B == 0) return BG_OK;
   if (!amps || !me2) return fail(BG_EINVAL, "bg_color_sum: NULL amps or me2");
@@ -307,8 +308,8 @@ bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
     return fail(BG_EINVAL, "bg_plan_create: invalid cs_mode");
   if (d->grad && (n > 8 || !d->hel_sampled))
     return fail(BG_EUNSUPPORTED, "bg_plan_create: gradients need n <= 8 and sampled helicities");
-  if (d->cs_mode == BG_CS_TC_BF16 && (n < 6 || n > 8 || !d->hel_sampled))
-    return fail(BG_EUNSUPPORTED, "bg_plan_create: tensor-core colour sum needs 6 <= n <= 8, sampled helicities");
+  if (d->cs_mode == BG_CS_TC_BF16 && (n < 6 || !d->hel_sampled))
+    return fail(BG_EUNSUPPORTED, "bg_plan_create: tensor-core colour sum needs 6 <= n <= 9, sampled helicities");
   const double qv = std::sqrt(d->q[1] * d->q[1] + d->q[2] * d->q[2] + d->q[3] * d->q[3]);
   if (!(d->q[0] > 0.0) || std::fabs(d->q[0] - qv) > 1e-12 * d->q[0])
     return fail(BG_EINVAL, "bg_plan_create: q must be light-like with q0 > 0");

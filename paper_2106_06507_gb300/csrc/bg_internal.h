@@ -81,7 +81,7 @@ cudaError_t launch_rambo_grad(int n, int64_t B, double sqrt_s, const double* u, 
 
 // Tensor-core colour sum (color_sum_tc.cu).
 bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<uint16_t>& tiles, double& g, int& nt,
-                    int& ntiles, int& kchunks);
+                    int& ntiles, int& kchunks, int& cpl);
 cudaError_t launch_color_sum_f32(const ColourSumArgs& a, cudaStream_t s);
 
 }  // namespace bg
@@ -117,7 +117,7 @@ struct bg_colormat {
   uint16_t* tc_tiles_raw;
   const __nv_bfloat16* tc_tiles;
   double tc_g;
-  int tc_nt, tc_ntiles, tc_kchunks;
+  int tc_nt, tc_ntiles, tc_kchunks, tc_cpl;
 };
 
 namespace bg {

@@ -5,8 +5,8 @@
 // Operands.  D = A C is a dense contraction: M = 128 events per CTA (TMEM
 // lanes), N = a tile of NT orderings (TMEM columns), K = all orderings.  C is
 // stored once per colour matrix as BF16 tiles of C/g (g = gcd of its
-// entries; every C/g is exactly representable in BF16 for n <= 8, checked at
-// creation), pre-arranged in the canonical no-swizzle K-major core-matrix
+// entries; every C/g is exactly representable in BF16 for n <= 8, and as a
+// sum of two BF16 planes hi + lo for n = 9, checked at creation), pre-arranged in the canonical no-swizzle K-major core-matrix
 // layout so that a plain bulk copy lands a tile ready for the MMA.  The FP32
 // amplitudes are split on the fly into three BF16 planes, A = hi + mid + lo
 // (24 significant bits), so that D is accurate to FP32 rounding; the MMA
@@ -154,7 +154,7 @@ struct TcParams {
   float g;      // gcd of C (Y = g D)
 };
 
-template <typename TIn>
+template <typename TIn, int CPL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     color_sum_tc_kernel(TcParams P, const TIn* __restrict__ A, const __nv_bfloat16* __restrict__ Ct,
                         const uint8_t* __restrict__ accept, double* __restrict__ me2, int* __restrict__ status,
@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // 1024-byte aligned carve-up
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t a_plane_bytes = TC_M * TC_KC * 2;            // 16 KB
-  const uint32_t c_tile_bytes = (uint32_t)P.nt * TC_KC * 2;   // nt*128 B
+  const uint32_t c_tile_bytes = (uint32_t)P.nt * TC_KC * 2 * CPL;   // CPL planes of nt*128 B
+  const uint32_t c_plane_bytes = (uint32_t)P.nt * TC_KC * 2;
   const uint32_t stage_bytes = 3 * a_plane_bytes + ((c_tile_bytes + 1023) & ~1023u);
   unsigned char* stage_base = smem;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * stage_bytes);
@@ -243,12 +244,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t a0 = smem_u32(stage_base + s * stage_bytes);
           const uint32_t c0 = a0 + 3 * a_plane_bytes;
 #pragma unroll
-          for (int plane = 0; plane < 3; ++plane) {
+          for (int cp = 0; cp < CPL; ++cp) {
 #pragma unroll
-            for (int ks = 0; ks < TC_KC / 16; ++ks) {
-              const uint64_t ad = smem_desc(a0 + plane * a_plane_bytes + ks * 256, 128, 1024);
-              const uint64_t bd = smem_desc(c0 + ks * 256, 128, 1024);
-              mma_bf16(d_tmem, ad, bd, idesc, (kc > 0 || plane > 0 || ks > 0) ? 1u : 0u);
+            for (int plane = 0; plane < 3; ++plane) {
+#pragma unroll
+              for (int ks = 0; ks < TC_KC / 16; ++ks) {
+                const uint64_t ad = smem_desc(a0 + plane * a_plane_bytes + ks * 256, 128, 1024);
+                const uint64_t bd = smem_desc(c0 + cp * c_plane_bytes + ks * 256, 128, 1024);
+                mma_bf16(d_tmem, ad, bd, idesc, (kc > 0 || cp > 0 || plane > 0 || ks > 0) ? 1u : 0u);
+              }
             }
           }
           mma_commit(&empty[s]);  // stage free once these MMAs have read it
@@ -354,11 +358,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 }  // namespace
 
-// Host: BF16 tiles of C / g in the layout of tile_off.  Returns false if some
-// C/g is not exactly representable in BF16 (the case for n = 9, where 22
-// entries per row need 9-10 significant bits) or if n is outside 6..9.
+// Host: BF16 tiles of C / g in the layout of tile_off.  C/g is split into
+// cpl = 1 or 2 exactly representable BF16 planes (hi + lo): for n <= 8 one
+// plane suffices; at n = 9, 22 entries per row need 9-10 significant bits and
+// a second plane carries the low bits.  Each tile stores its planes back to
+// back.  Returns false if two planes are not enough or n is outside 6..9.
+static bool bf16_exact(float v, uint16_t& bits) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  bits = (uint16_t)(u >> 16);
+  return (u & 0xFFFFu) == 0;
+}
+
 bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<uint16_t>& tiles, double& g,
-                    int& nt, int& ntiles, int& kchunks) {
+                    int& nt, int& ntiles, int& kchunks, int& cpl) {
   if (n < 6 || n > 9) return false;
   long long gg = 0;
   for (double v : dense) {
@@ -370,32 +383,43 @@ bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<
   }
   if (gg == 0) return false;
   g = (double)gg;
+  // planes: hi = C/g rounded to BF16, lo = remainder (must be exact)
+  cpl = 1;
+  for (double v : dense) {
+    uint16_t bits;
+    if (!bf16_exact((float)(v / g), bits)) { cpl = 2; break; }
+  }
   nt = k < 240 ? ((k + 15) / 16) * 16 : 240;
   ntiles = (k + nt - 1) / nt;
   kchunks = (k + TC_KC - 1) / TC_KC;
-  const size_t tile_elems = (size_t)nt * TC_KC;
-  tiles.assign((size_t)ntiles * kchunks * tile_elems, 0);
+  const size_t plane_elems = (size_t)nt * TC_KC;
+  tiles.assign((size_t)ntiles * kchunks * plane_elems * cpl, 0);
   for (int t = 0; t < ntiles; ++t)
     for (int kc = 0; kc < kchunks; ++kc) {
-      uint16_t* base = &tiles[((size_t)t * kchunks + kc) * tile_elems];
+      uint16_t* base = &tiles[((size_t)t * kchunks + kc) * plane_elems * cpl];
       for (int rr = 0; rr < nt; ++rr)
         for (int kk = 0; kk < TC_KC; ++kk) {
           const int m = t * nt + rr, c = kc * TC_KC + kk;
-          float v = 0.0f;
-          if (m < k && c < k) v = (float)(dense[(size_t)m * k + c] / g);
-          // exact BF16: the low 16 bits of the FP32 pattern must be zero
-          uint32_t u;
-          std::memcpy(&u, &v, 4);
-          if (u & 0xFFFFu) return false;
-          base[tile_off(rr, kk) / 2] = (uint16_t)(u >> 16);
+          const double v = (m < k && c < k) ? dense[(size_t)m * k + c] / g : 0.0;
+          const float hi = __bfloat162float(__float2bfloat16_rn((float)v));
+          uint16_t hb, lb;
+          if (!bf16_exact(hi, hb)) return false;
+          const double rem = v - (double)hi;
+          if (cpl == 1) {
+            if (rem != 0.0) return false;
+          } else {
+            if (!bf16_exact((float)rem, lb) || (double)(float)rem != rem) return false;
+            base[plane_elems + tile_off(rr, kk) / 2] = lb;
+          }
+          base[tile_off(rr, kk) / 2] = hb;
         }
     }
   return true;
 }
 
-size_t tc_smem_bytes(int nt) {
+size_t tc_smem_bytes(int nt, int cpl) {
   const size_t a_plane = TC_M * TC_KC * 2;
-  const size_t c_tile = ((size_t)nt * TC_KC * 2 + 1023) & ~size_t(1023);
+  const size_t c_tile = ((size_t)nt * TC_KC * 2 * cpl + 1023) & ~size_t(1023);
   return 1024 + TC_STAGES * (3 * a_plane + c_tile) + 128;
 }
 
@@ -408,21 +432,22 @@ cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, in
   P.kchunks = C->tc_kchunks;
   P.scale = a.scale * C->tc_g;
   P.g = (float)C->tc_g;
-  const size_t smem = tc_smem_bytes(P.nt);
+  const size_t smem = tc_smem_bytes(P.nt, C->tc_cpl);
   const unsigned blocks = (unsigned)((a.B + TC_M - 1) / TC_M);
-  if (a.amps_f32) {
-    auto kern = color_sum_tc_kernel<float>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const float*>(a.amps), C->tc_tiles, a.accept, a.me2,
-                                          status, static_cast<float*>(a.Y));
-  } else {
-    auto kern = color_sum_tc_kernel<double>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const double*>(a.amps), C->tc_tiles, a.accept, a.me2,
-                                          status, static_cast<double*>(a.Y));
+#define BG_TC_LAUNCH(TIN, CPL)                                                                                 \
+  {                                                                                                            \
+    auto kern = color_sum_tc_kernel<TIN, CPL>;                                                                 \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    if (e != cudaSuccess) return e;                                                                            \
+    kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const TIN*>(a.amps), C->tc_tiles, a.accept, a.me2,    \
+                                          status, static_cast<TIN*>(a.Y));                                     \
   }
+  if (a.amps_f32) {
+    if (C->tc_cpl == 1) BG_TC_LAUNCH(float, 1) else BG_TC_LAUNCH(float, 2)
+  } else {
+    if (C->tc_cpl == 1) BG_TC_LAUNCH(double, 1) else BG_TC_LAUNCH(double, 2)
+  }
+#undef BG_TC_LAUNCH
   return cudaGetLastError();
 }
 

@@ -69,7 +69,7 @@ extern "C" bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, doubl
     return fail(BG_EINVAL, "bg_me2_batch_noalloc: q must be light-like with q0 > 0");
   const int H = hel ? 1 : (1 << n);
   if (cs_mode == BG_CS_TC_BF16 && (!C->tc_tiles || H != 1))
-    return fail(BG_EUNSUPPORTED, "bg_me2_batch_noalloc: tensor-core mode needs 6 <= n <= 8 and sampled helicities");
+    return fail(BG_EUNSUPPORTED, "bg_me2_batch_noalloc: tensor-core mode needs 6 <= n <= 9 and sampled helicities");
   // scratch layout: momenta [4][n][B] double | amplitudes [B][H][k] | cut flags [B]
   const size_t amp_size = (prec == BG_F32) ? 4 : 8;
   const size_t per_event = 4 * (size_t)n * 8 + (size_t)H * C->k * amp_size + 1;
