@@ -3,10 +3,17 @@ CUDA-core colour sum on the same amplitudes, and against the oracle.
 
 Tolerance: the amplitudes enter as three BF16 planes (24 significant bits)
 and C/gcd is exact in BF16, so every product is exact; the error is the
-tensor cores' FP32 accumulation, 3 * ceil(k/16) accumulator updates per
-element of A C (135 at n = 8, k = 720), each rounding at ~2^-24 of the
-running sum.  Bound: median relative error of |M|^2 below 5e-6 and every
-event below 2e-4 (measured at n = 8: median 1.3e-6)."""
+tensor cores' FP32 accumulation, U = 3 * planes(C) * ceil(k/16) accumulator
+updates per element of A C (135 at n = 8; 1890 at n = 9, where C needs two
+BF16 planes), each rounding at ~2^-24 of the running sum.  Bound: median
+relative error of |M|^2 below max(5e-6, 3e-8 U) and every event below
+max(2e-4, 1e-6 U) (measured: median 1.3e-6 at n = 8, 1.0e-5 at n = 9)."""
+
+
+def tc_tolerances(n):
+    k = math.factorial(n - 2)
+    U = 3 * (2 if n == 9 else 1) * math.ceil(k / 16)
+    return max(5e-6, 3e-8 * U), max(2e-4, 1e-6 * U)
 import math
 
 import numpy as np
@@ -52,8 +59,9 @@ def test_tc_colour_sum_matches_fp64_colour_sum(bg, n, B):
     nz = ref != 0
     if nz.any():
         rel = np.abs(got[nz] / ref[nz] - 1.0)
-        assert np.median(rel) < 5e-6
-        assert rel.max() < 2e-4
+        med_tol, max_tol = tc_tolerances(n)
+        assert np.median(rel) < med_tol
+        assert rel.max() < max_tol
     C.close()
 
 
