@@ -289,6 +289,70 @@ bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const
                          const uint8_t* accept, double* me2, void* workspace, int64_t workspace_bytes,
                          void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Mixed multiplicities: a batch whose events each have their own n in
+ * n_min..n_max (Sec. 5 times every n from 4 to 12; a generator of events
+ * with several jet multiplicities feeds such batches).  bg_mixed_create
+ * allocates input, output and per-multiplicity buffers for up to max_batch
+ * events and records the whole path as one CUDA graph: binning of the
+ * events by n on the device, then one branch per multiplicity (concurrent
+ * streams), each Rambo -> cut -> colour-ordered recursion + colour sum
+ * (n <= n_co_max, Eqs. 2.16-2.22, sampled helicities) or colour-dressed
+ * recursion with sampled colours (n > n_co_max, Eqs. 2.28-2.32), then a
+ * scatter of |M|^2 back to the events' positions.  A branch handles its
+ * events in chunks of at most cap_n events, cap_n chosen so that a chunk's
+ * buffers stay within chunk_bytes (0: 8 GiB; at most 64 chunks).
+ * bg_mixed_run replays the graph with one launch for B <= max_batch events.
+ *   n_co_max: largest n on the colour-ordered path (<= 9; below n_min: all
+ *             events on the colour-dressed path)
+ *   cs_mode:  colour-sum arithmetic of the colour-ordered branches; the
+ *             tensor-core mode applies to 6 <= n <= 9, smaller n use FP32
+ *   color_mode: colour sampling of the colour-dressed branches
+ * The paper has no single-launch counterpart: it runs one multiplicity at
+ * a time.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int n_min, n_max;
+  int64_t max_batch;
+  double sqrt_s;
+  double pt_min;
+  double g_s;
+  double q[4];
+  bg_prec prec;
+  bg_cs_mode cs_mode;
+  bg_color_mode color_mode;
+  int n_co_max;
+  int64_t chunk_bytes;
+} bg_mixed_desc;
+typedef struct bg_mixed bg_mixed;
+/* Errors: BG_EINVAL (desc), BG_ENOMEM, BG_ECUDA.  Synchronises the device. */
+bg_status bg_mixed_create(const bg_mixed_desc* desc, bg_mixed** out);
+void bg_mixed_destroy(bg_mixed* plan);
+/* The plan-owned DEVICE buffers the graph reads and writes (any pointer may
+ * be NULL):
+ *   n_per_event [max_batch] int32               multiplicity of each event
+ *   u           [max_batch][4(n_max-2)] double  Rambo uniforms; event e uses
+ *                                               its first 4(n_e-2)
+ *   hel         [n_max][max_batch] int8 (+-1)   sampled helicities, rows
+ *                                               0..n_e-1
+ *   colors      [2 n_max][max_batch] int8       sampled colours of the
+ *                                               colour-dressed branches, as
+ *                                               for bg_currents_cd (rows
+ *                                               0..n_e-1 adjoint, 0..2n_e-1
+ *                                               flow)
+ *   me2         [max_batch] double              output, GeV^(8-2n_e) */
+bg_status bg_mixed_buffers(bg_mixed* plan, int32_t** n_per_event, double** u, int8_t** hel, int8_t** colors,
+                           double** me2);
+int64_t bg_mixed_workspace_bytes(const bg_mixed* plan);
+/* Runs the graph for the first B events of the buffers on `stream` (copies
+ * B to the device, then one graph launch).  Events with n outside
+ * n_min..n_max set BG_EINVAL in the device status word and keep their me2
+ * entry unchanged.  Runs on one plan must be ordered (one stream): they
+ * share its buffers. */
+bg_status bg_mixed_run(bg_mixed* plan, int64_t B, void* stream);
+/* counts[13]: events of each n in the last run (synchronises the device). */
+bg_status bg_mixed_counts(bg_mixed* plan, int64_t* counts);
+
 /* Device status word of the current device: 0 if no kernel has seen an
  * invalid label since the last reset, else a BG_* code.  Synchronises the
  * device.  bg_device_status_reset clears it. */

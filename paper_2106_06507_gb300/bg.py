@@ -38,6 +38,13 @@ class PlanDesc(ctypes.Structure):
                 ("color_mode", ctypes.c_int), ("hel_sampled", ctypes.c_int), ("grad", ctypes.c_int)]
 
 
+class MixedDesc(ctypes.Structure):
+    _fields_ = [("n_min", ctypes.c_int), ("n_max", ctypes.c_int), ("max_batch", ctypes.c_int64),
+                ("sqrt_s", ctypes.c_double), ("pt_min", ctypes.c_double), ("g_s", ctypes.c_double),
+                ("q", ctypes.c_double * 4), ("prec", ctypes.c_int), ("cs_mode", ctypes.c_int),
+                ("color_mode", ctypes.c_int), ("n_co_max", ctypes.c_int), ("chunk_bytes", ctypes.c_int64)]
+
+
 class BGError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"bg status {code}: {msg}")
@@ -74,12 +81,21 @@ def lib() -> ctypes.CDLL:
         L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
+        L.bg_mixed_create.argtypes = [ctypes.POINTER(MixedDesc), ctypes.POINTER(vp)]
+        L.bg_mixed_destroy.argtypes = [vp]
+        L.bg_mixed_destroy.restype = None
+        L.bg_mixed_buffers.argtypes = [vp] + [ctypes.POINTER(vp)] * 5
+        L.bg_mixed_workspace_bytes.argtypes = [vp]
+        L.bg_mixed_workspace_bytes.restype = c_i64
+        L.bg_mixed_run.argtypes = [vp, c_i64, vp]
+        L.bg_mixed_counts.argtypes = [vp, ctypes.POINTER(c_i64)]
         L.bg_device_status.argtypes = [ctypes.POINTER(c_int)]
         L.bg_device_status_reset.argtypes = []
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_probe_fma", "bg_cd_workspace_bytes",
-                     "bg_currents_cd", "bg_me2_grad"):
+                     "bg_currents_cd", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
+                     "bg_mixed_counts"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -269,6 +285,69 @@ class Plan:
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().bg_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """A plan-owned device buffer exposed through __cuda_array_interface__
+    (torch.as_tensor makes a view without copying)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Mixed:
+    """Mixed-multiplicity batches in one CUDA-graph launch (bg_mixed_*).
+    The inputs live in plan-owned device buffers, exposed as tensors:
+    n_per_event [max_batch] int32, u [max_batch, 4(n_max-2)] float64,
+    hel [n_max, max_batch] int8, colors [2 n_max, max_batch] int8, and the
+    output me2 [max_batch] float64."""
+
+    def __init__(self, n_min: int, n_max: int, max_batch: int, sqrt_s: float = 1000.0, pt_min: float = -1.0,
+                 g_s: float = G_S_DEFAULT, q=DEFAULT_Q, prec: int = BG_F32, cs_mode: int = BG_CS_F32,
+                 color_mode: int = BG_COL_ADJOINT, n_co_max: int = 9, chunk_bytes: int = 0):
+        d = MixedDesc()
+        d.n_min, d.n_max, d.max_batch, d.sqrt_s, d.pt_min, d.g_s = n_min, n_max, max_batch, sqrt_s, pt_min, g_s
+        for i in range(4):
+            d.q[i] = float(q[i])
+        d.prec, d.cs_mode, d.color_mode, d.n_co_max, d.chunk_bytes = prec, cs_mode, color_mode, n_co_max, chunk_bytes
+        self.desc = d
+        h = ctypes.c_void_p()
+        _check(lib().bg_mixed_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(lib().bg_mixed_buffers(h, *[ctypes.byref(x) for x in ptrs]))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        shapes = [((max_batch,), "<i4"), ((max_batch, 4 * (n_max - 2)), "<f8"), ((n_max, max_batch), "|i1"),
+                  ((2 * n_max, max_batch), "|i1"), ((max_batch,), "<f8")]
+        views = [torch.as_tensor(_DeviceArray(p.value, sh, ts), device=dev) for p, (sh, ts) in zip(ptrs, shapes)]
+        self.n_per_event, self.u, self.hel, self.colors, self.me2 = views
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(lib().bg_mixed_workspace_bytes(self._h))
+
+    def run(self, B: int, stream=None) -> torch.Tensor:
+        """Replays the graph for the first B events; returns the me2 view."""
+        _check(lib().bg_mixed_run(self._h, B, _stream(stream)))
+        return self.me2[:B]
+
+    def counts(self) -> list[int]:
+        c = (ctypes.c_int64 * 13)()
+        _check(lib().bg_mixed_counts(self._h, c))
+        return list(c)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.n_per_event = self.u = self.hel = self.colors = self.me2 = None
+            lib().bg_mixed_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):  # pragma: no cover

@@ -34,6 +34,7 @@ SOURCES = [
     "noalloc.cu",
     "co_grad.cu",
     "grad_rambo.cu",
+    "mixed.cu",
 ]
 
 

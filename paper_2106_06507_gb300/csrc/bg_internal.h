@@ -34,13 +34,16 @@ void colour_dense(int n, const std::vector<double>& row, std::vector<double>& de
 int* device_status_ptr();
 
 // Kernel launchers (one per .cu file).
+// Kernels take a capacity B (row stride of event-indexed SoA arrays) and an
+// optional device-side event count dB (<= B; NULL means B), so that a launch
+// can be recorded once in a CUDA graph and replayed for varying counts.
 cudaError_t launch_rambo(int n, int64_t B, double sqrt_s, const double* u, double* p, double pt_min,
-                         uint8_t* accept, cudaStream_t s);
+                         uint8_t* accept, cudaStream_t s, const int64_t* dB = nullptr);
 
 cudaError_t launch_co_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                          float* amps, int* status, cudaStream_t s);
+                          float* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr);
 cudaError_t launch_co_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                          double* amps, int* status, cudaStream_t s);
+                          double* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr);
 
 struct ColourSumArgs {
   int n;
@@ -55,6 +58,7 @@ struct ColourSumArgs {
   const uint8_t* accept;
   double* me2;
   void* Y = nullptr;   // optional output (C A)[B][H][k], same type as amps
+  const int64_t* dB = nullptr;  // optional device-side event count (<= B)
 };
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
 cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
@@ -69,6 +73,7 @@ cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
 cudaError_t launch_cd_f64(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
+// (CdParams carries the capacity B and an optional device-side count dB.)
 
 // Gradient (co_grad.cu, grad_rambo.cu).
 cudaError_t launch_co_grad_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,

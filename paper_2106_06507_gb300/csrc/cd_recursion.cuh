@@ -79,7 +79,8 @@ struct CdSlab {
 };
 
 struct CdParams {
-  int64_t B;
+  int64_t B;              // capacity (row stride of p, hel, colours)
+  const int64_t* dB = nullptr;  // optional device-side event count
   double inv_sqrt_s;
   double scale;  // g^(2n-4) sqrt_s^(8-2n) * colour and helicity weights * 2^-(n-2)
   int flow;      // 0: adjoint colours [n][B] in 1..8; 1: flow pairs [2n][B] in 1..3
@@ -196,6 +197,8 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
   __shared__ double s_red[NT / 32];
 
   const int tid = threadIdx.x;
+  const int64_t S_ = prm.B;
+  const int64_t Bn = prm.dB ? (*prm.dB < S_ ? *prm.dB : S_) : S_;
   // subsets grouped by size (event independent)
   if (tid == 0) {
     int pos = 0;
@@ -208,20 +211,20 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
   }
   __syncthreads();
 
-  for (int64_t e = blockIdx.x; e < prm.B; e += gridDim.x) {
+  for (int64_t e = blockIdx.x; e < Bn; e += gridDim.x) {
     // ---- external states (FP64) ----
     if (tid < N) {
       const int g = tid;
       double k[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * prm.B + e] * prm.inv_sqrt_s;
+      for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * S_ + e] * prm.inv_sqrt_s;
       if (g < 2) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) k[m] = -k[m];
       }
       double e1[4], e2[4];
       lc_polarisations(k, prm.q.v, e1, e2);
-      const int h = hel[(int64_t)g * prm.B + e];
+      const int h = hel[(int64_t)g * S_ + e];
       if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
@@ -229,12 +232,12 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
         s_e[g][m] = (h < 0) ? e2[m] : e1[m];
       }
       if (prm.flow) {
-        const int rr = col[(int64_t)(2 * g) * prm.B + e], cc = col[(int64_t)(2 * g + 1) * prm.B + e];
+        const int rr = col[(int64_t)(2 * g) * S_ + e], cc = col[(int64_t)(2 * g + 1) * S_ + e];
         if (rr < 1 || rr > 3 || cc < 1 || cc > 3) flag_status(status, BG_EINVAL);
         for (int i = 0; i < 3; ++i)
           for (int j = 0; j < 3; ++j) s_E[g][i][j] = (i == rr - 1 && j == cc - 1) ? 1.0 : 0.0;
       } else {
-        int a = col[(int64_t)g * prm.B + e];
+        int a = col[(int64_t)g * S_ + e];
         if (a < 1 || a > 8) {
           flag_status(status, BG_EINVAL);
           a = 1;

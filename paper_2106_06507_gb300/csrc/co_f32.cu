@@ -3,7 +3,7 @@
 
 namespace bg {
 cudaError_t launch_co_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                          float* amps, int* status, cudaStream_t s) {
-  return launch_co_t<float>(n, B, sqrt_s, p, hel, q, amps, status, s);
+                          float* amps, int* status, cudaStream_t s, const int64_t* dB) {
+  return launch_co_t<float>(n, B, sqrt_s, p, hel, q, amps, status, s, dB);
 }
 }  // namespace bg

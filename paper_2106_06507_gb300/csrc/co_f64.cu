@@ -3,7 +3,7 @@
 
 namespace bg {
 cudaError_t launch_co_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                          double* amps, int* status, cudaStream_t s) {
-  return launch_co_t<double>(n, B, sqrt_s, p, hel, q, amps, status, s);
+                          double* amps, int* status, cudaStream_t s, const int64_t* dB) {
+  return launch_co_t<double>(n, B, sqrt_s, p, hel, q, amps, status, s, dB);
 }
 }  // namespace bg

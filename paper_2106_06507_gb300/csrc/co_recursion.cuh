@@ -141,9 +141,11 @@ __device__ __forceinline__ T co_recursion(T (&J)[N - 1][N - 1][4], const T (&Sp)
 }
 
 template <int N, typename T, bool SUMHEL>
-__global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, const double* __restrict__ p,
-                                                 const int8_t* __restrict__ hel, Q4 q, T* __restrict__ amps,
-                                                 int* __restrict__ status) {
+__global__ void __launch_bounds__(256) co_kernel(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
+                                                 const double* __restrict__ p, const int8_t* __restrict__ hel, Q4 q,
+                                                 T* __restrict__ amps, int* __restrict__ status) {
+  // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
+  const int64_t B = dB ? (*dB < S_ ? *dB : S_) : S_;
   using S = CoShape<N, SUMHEL>;
   using L = CoSmem<N, T, SUMHEL>;
   constexpr int M = S::M, K = S::K, H = S::H, EB = S::EB, NPOL = S::NPOL;
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, c
 
   const int64_t e0 = (int64_t)blockIdx.x * EB;
   const int tid = threadIdx.x;
+  if (e0 >= B) return;
 
   // ---- phase 1a: ordering table (packed 4-bit labels), momenta, polarisations
   for (int r = tid; r < K; r += S::NT) {
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, c
     if (e >= B) continue;
     double k[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * B + e] * inv_sqrt_s;
+    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * S_ + e] * inv_sqrt_s;
     if (g < 2) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) k[m] = -k[m];
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, c
         s_e[((el * 2 + 1) * N + g) * 4 + m] = T(e2[m]);
       }
     } else {
-      const int h = hel[(int64_t)g * B + e];
+      const int h = hel[(int64_t)g * S_ + e];
       if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
       const double* ev = (h < 0) ? e2 : e1;
 #pragma unroll
@@ -219,8 +222,8 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, c
     double ka[4], kb[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      ka[m] = p[((int64_t)m * N + a) * B + e];
-      kb[m] = p[((int64_t)m * N + b) * B + e];
+      ka[m] = p[((int64_t)m * N + a) * S_ + e];
+      kb[m] = p[((int64_t)m * N + b) * S_ + e];
     }
     // both beams or neither flipped -> +, one flipped -> - (k = -p for gluons 1, 2)
     const double sgn = ((a < 2) != (b < 2)) ? -1.0 : 1.0;
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t B, double inv_sqrt_s, c
 
 template <int N, typename T, bool SUMHEL>
 cudaError_t launch_co_n(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
-                        int* status, cudaStream_t s) {
+                        int* status, cudaStream_t s, const int64_t* dB) {
   using S = CoShape<N, SUMHEL>;
   using L = CoSmem<N, T, SUMHEL>;
   auto kern = co_kernel<N, T, SUMHEL>;
@@ -304,7 +307,7 @@ cudaError_t launch_co_n(int64_t B, double sqrt_s, const double* p, const int8_t*
   Q4 qq;
   for (int m = 0; m < 4; ++m) qq.v[m] = q[m];
   const int64_t blocks = (B + S::EB - 1) / S::EB;
-  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, 1.0 / sqrt_s, p, hel, qq, amps, status);
+  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, dB, 1.0 / sqrt_s, p, hel, qq, amps, status);
   return cudaGetLastError();
 }
 
@@ -340,9 +343,11 @@ struct CoDfsSmem {
 };
 
 template <int N, typename T>
-__global__ void __launch_bounds__(256) co_kernel_dfs(int64_t B, double inv_sqrt_s, const double* __restrict__ p,
-                                                     const int8_t* __restrict__ hel, Q4 q, T* __restrict__ amps,
-                                                     int* __restrict__ status) {
+__global__ void __launch_bounds__(256) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
+                                                     const double* __restrict__ p, const int8_t* __restrict__ hel,
+                                                     Q4 q, T* __restrict__ amps, int* __restrict__ status) {
+  // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
+  const int64_t B = dB ? (*dB < S_ ? *dB : S_) : S_;
   using S = CoDfsShape<N>;
   using L = CoDfsSmem<N, T>;
   constexpr int M = S::M, K = S::K, G = S::G, EB = S::EB, NT = S::NT;
@@ -355,6 +360,7 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t B, double inv_sqrt_
 
   const int64_t e0 = (int64_t)blockIdx.x * EB;
   const int tid = threadIdx.x;
+  if (e0 >= B) return;
 
   // ---- phase 1: ordering of the first member of each group, momenta,
   //      polarisations, pair invariants, inverse propagators (FP64 -> T)
@@ -384,14 +390,14 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t B, double inv_sqrt_
     if (e >= B) continue;
     double k[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * B + e] * inv_sqrt_s;
+    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * S_ + e] * inv_sqrt_s;
     if (g < 2) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) k[m] = -k[m];
     }
     double e1[4], e2[4];
     lc_polarisations(k, q.v, e1, e2);
-    const int h = hel[(int64_t)g * B + e];
+    const int h = hel[(int64_t)g * S_ + e];
     if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
     const double* ev = (h < 0) ? e2 : e1;
 #pragma unroll
@@ -411,8 +417,8 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t B, double inv_sqrt_
     double ka[4], kb[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      ka[m] = p[((int64_t)m * N + a) * B + e];
-      kb[m] = p[((int64_t)m * N + b) * B + e];
+      ka[m] = p[((int64_t)m * N + a) * S_ + e];
+      kb[m] = p[((int64_t)m * N + b) * S_ + e];
     }
     const double sgn = ((a < 2) != (b < 2)) ? -1.0 : 1.0;
     s_pair[el * S::NPAIR + it % S::NPAIR] =
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t B, double inv_sqrt_
 
 template <int N, typename T>
 cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
-                          int* status, cudaStream_t s) {
+                          int* status, cudaStream_t s, const int64_t* dB) {
   using S = CoDfsShape<N>;
   using L = CoDfsSmem<N, T>;
   auto kern = co_kernel_dfs<N, T>;
@@ -558,19 +564,19 @@ cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_
   Q4 qq;
   for (int m = 0; m < 4; ++m) qq.v[m] = q[m];
   const int64_t blocks = (B + S::EB - 1) / S::EB;
-  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, 1.0 / sqrt_s, p, hel, qq, amps, status);
+  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, dB, 1.0 / sqrt_s, p, hel, qq, amps, status);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                        T* amps, int* status, cudaStream_t s) {
+                        T* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr) {
   const bool sum = (hel == nullptr);
 #define BG_CO_CASE(NN)                                                                    \
   case NN:                                                                                \
-    return sum ? launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s)         \
-               : (NN >= 6 ? launch_co_dfs<(NN >= 6 ? NN : 6), T>(B, sqrt_s, p, hel, q, amps, status, s) \
-                          : launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s));
+    return sum ? launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB)     \
+               : (NN >= 6 ? launch_co_dfs<(NN >= 6 ? NN : 6), T>(B, sqrt_s, p, hel, q, amps, status, s, dB) \
+                          : launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB));
   switch (n) {
     BG_CO_CASE(4)
     BG_CO_CASE(5)

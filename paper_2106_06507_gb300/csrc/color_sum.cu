@@ -18,10 +18,12 @@ constexpr int KT = 16;   // reduction step
 constexpr int NT = 256;  // threads: 16 x 16, each 4 rows x 4 events
 
 template <typename TIn, typename TC>
-__global__ void __launch_bounds__(NT) color_sum_kernel(int64_t B, int H, int k, const TIn* __restrict__ A,
-                                                       const TC* __restrict__ C, double scale,
-                                                       const uint8_t* __restrict__ accept,
+__global__ void __launch_bounds__(NT) color_sum_kernel(int64_t Bcap, const int64_t* __restrict__ dB, int H, int k,
+                                                       const TIn* __restrict__ A, const TC* __restrict__ C,
+                                                       double scale, const uint8_t* __restrict__ accept,
                                                        double* __restrict__ me2, TIn* __restrict__ Y) {
+  const int64_t B = dB ? (*dB < Bcap ? *dB : Bcap) : Bcap;
+  if ((int64_t)blockIdx.x * 64 >= B) return;
   __shared__ __align__(16) TC Cs[KT][TA];
   __shared__ __align__(16) TC As[KT][TE];
   __shared__ double red[16][TE];
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(NT) color_sum_kernel(int64_t B, int H, int k, 
 template <typename TIn, typename TC>
 cudaError_t launch_cs(const ColourSumArgs& a, const TC* C, cudaStream_t s) {
   const int64_t blocks = (a.B + TE - 1) / TE;
-  color_sum_kernel<TIn, TC><<<(unsigned)blocks, NT, 0, s>>>(a.B, a.H, a.k, static_cast<const TIn*>(a.amps), C,
+  color_sum_kernel<TIn, TC><<<(unsigned)blocks, NT, 0, s>>>(a.B, a.dB, a.H, a.k, static_cast<const TIn*>(a.amps), C,
                                                            a.scale, a.accept, a.me2, static_cast<TIn*>(a.Y));
   return cudaGetLastError();
 }

@@ -145,7 +145,8 @@ __host__ __device__ constexpr uint32_t tile_off(int r, int k) {
 }
 
 struct TcParams {
-  int64_t B;
+  int64_t B;             // capacity
+  const int64_t* dB;     // optional device-side event count
   int k;        // orderings
   int nt;       // orderings per N tile (multiple of 16, <= 240)
   int ntiles;   // N tiles
@@ -179,6 +180,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t e0 = (int64_t)blockIdx.x * TC_M;
+  if (P.dB) {
+    const int64_t cnt = *P.dB < P.B ? *P.dB : P.B;
+    if (e0 >= cnt) return;  // whole CTA beyond the events of this launch
+    P.B = cnt;
+  }
   const int total = P.ntiles * P.kchunks;  // pipeline iterations
   const uint32_t tmem_cols = (2 * P.nt <= 32) ? 32 : (2 * P.nt <= 64) ? 64 : (2 * P.nt <= 128) ? 128
                            : (2 * P.nt <= 256) ? 256 : 512;
@@ -426,6 +432,7 @@ size_t tc_smem_bytes(int nt, int cpl) {
 cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, int* status, cudaStream_t s) {
   TcParams P;
   P.B = a.B;
+  P.dB = a.dB;
   P.k = a.k;
   P.nt = C->tc_nt;
   P.ntiles = C->tc_ntiles;

@@ -8,11 +8,13 @@ namespace bg {
 namespace {
 
 template <int N>
-__global__ void __launch_bounds__(128) rambo_kernel(int64_t B, double sqrt_s, const double* __restrict__ u,
-                                                    double* __restrict__ p, double pt_min,
-                                                    uint8_t* __restrict__ accept) {
+__global__ void __launch_bounds__(128) rambo_kernel(int64_t S, const int64_t* __restrict__ dB, double sqrt_s,
+                                                    const double* __restrict__ u, double* __restrict__ p,
+                                                    double pt_min, uint8_t* __restrict__ accept) {
+  // S: capacity (row stride of p); dB: device-side event count (NULL: S)
   constexpr int NOUT = N - 2;
   constexpr int D = 4 * NOUT;
+  const int64_t B = dB ? (*dB < S ? *dB : S) : S;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B) return;
   const double* ue = u + e * D;
@@ -40,14 +42,14 @@ __global__ void __launch_bounds__(128) rambo_kernel(int64_t B, double sqrt_s, co
   const double a = 1.0 / (1.0 + gamma);
   const double E = 0.5 * sqrt_s;
   // p layout [4][N][B]
-  p[(0 * N + 0) * B + e] = E;
-  p[(1 * N + 0) * B + e] = 0.0;
-  p[(2 * N + 0) * B + e] = 0.0;
-  p[(3 * N + 0) * B + e] = E;
-  p[(0 * N + 1) * B + e] = E;
-  p[(1 * N + 1) * B + e] = 0.0;
-  p[(2 * N + 1) * B + e] = 0.0;
-  p[(3 * N + 1) * B + e] = -E;
+  p[(0 * N + 0) * S + e] = E;
+  p[(1 * N + 0) * S + e] = 0.0;
+  p[(2 * N + 0) * S + e] = 0.0;
+  p[(3 * N + 0) * S + e] = E;
+  p[(0 * N + 1) * S + e] = E;
+  p[(1 * N + 1) * S + e] = 0.0;
+  p[(2 * N + 1) * S + e] = 0.0;
+  p[(3 * N + 1) * S + e] = -E;
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < NOUT; ++i) {
@@ -56,10 +58,10 @@ __global__ void __launch_bounds__(128) rambo_kernel(int64_t B, double sqrt_s, co
     const double p1 = x * (q[i][1] + b[0] * q[i][0] + a * bq * b[0]);
     const double p2 = x * (q[i][2] + b[1] * q[i][0] + a * bq * b[1]);
     const double p3 = x * (q[i][3] + b[2] * q[i][0] + a * bq * b[2]);
-    p[(0 * N + 2 + i) * B + e] = p0;
-    p[(1 * N + 2 + i) * B + e] = p1;
-    p[(2 * N + 2 + i) * B + e] = p2;
-    p[(3 * N + 2 + i) * B + e] = p3;
+    p[(0 * N + 2 + i) * S + e] = p0;
+    p[(1 * N + 2 + i) * S + e] = p1;
+    p[(2 * N + 2 + i) * S + e] = p2;
+    p[(3 * N + 2 + i) * S + e] = p3;
     ok = ok && (sqrt(p1 * p1 + p2 * p2) > pt_min);
   }
   if (accept) accept[e] = ok ? 1 : 0;
@@ -67,27 +69,27 @@ __global__ void __launch_bounds__(128) rambo_kernel(int64_t B, double sqrt_s, co
 
 template <int N>
 cudaError_t launch(int64_t B, double sqrt_s, const double* u, double* p, double pt_min, uint8_t* accept,
-                   cudaStream_t s) {
+                   cudaStream_t s, const int64_t* dB) {
   const int threads = 128;
   const int64_t blocks = (B + threads - 1) / threads;
-  rambo_kernel<N><<<(unsigned)blocks, threads, 0, s>>>(B, sqrt_s, u, p, pt_min, accept);
+  rambo_kernel<N><<<(unsigned)blocks, threads, 0, s>>>(B, dB, sqrt_s, u, p, pt_min, accept);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_rambo(int n, int64_t B, double sqrt_s, const double* u, double* p, double pt_min,
-                         uint8_t* accept, cudaStream_t s) {
+                         uint8_t* accept, cudaStream_t s, const int64_t* dB) {
   switch (n) {
-    case 4: return launch<4>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 5: return launch<5>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 6: return launch<6>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 7: return launch<7>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 8: return launch<8>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 9: return launch<9>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 10: return launch<10>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 11: return launch<11>(B, sqrt_s, u, p, pt_min, accept, s);
-    case 12: return launch<12>(B, sqrt_s, u, p, pt_min, accept, s);
+    case 4: return launch<4>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 5: return launch<5>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 6: return launch<6>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 7: return launch<7>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 8: return launch<8>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 9: return launch<9>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 10: return launch<10>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 11: return launch<11>(B, sqrt_s, u, p, pt_min, accept, s, dB);
+    case 12: return launch<12>(B, sqrt_s, u, p, pt_min, accept, s, dB);
     default: return cudaErrorInvalidValue;
   }
 }

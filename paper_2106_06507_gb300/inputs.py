@@ -38,6 +38,17 @@ def raw64(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
         return _mix(key + idx * _GOLDEN)
 
 
+def raw64_at(seed: int, stream: int, idx: np.ndarray) -> np.ndarray:
+    """The words of one (seed, stream) sequence at the counters `idx`."""
+    with np.errstate(over="ignore"):
+        key = _mix(np.array([seed], dtype=np.uint64) * _GOLDEN + np.uint64(stream))[0]
+        return _mix(key + np.asarray(idx, dtype=np.uint64) * _GOLDEN)
+
+
+def _unit(r: np.ndarray) -> np.ndarray:
+    return ((r >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
 def uniforms(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
     """Doubles in the open interval (0, 1)."""
     r = raw64(seed, stream, count, offset) >> np.uint64(11)
@@ -87,3 +98,48 @@ def multiplicities(batch: int, n_min: int, n_max: int, seed: int = 0) -> np.ndar
     u = uniforms(seed, STREAM_MULTIPLICITY, batch)
     span = n_max - n_min + 1
     return (n_min + np.minimum((u * span).astype(np.int64), span - 1)).astype(np.int32)
+
+
+def mixed_events(batch: int, n_min: int, n_max: int, seed: int = 0, colours: str = "adjoint") -> dict:
+    """A mixed-multiplicity batch in the padded layout of the mixed plan.
+
+    Event e has multiplicity nev[e] (multiplicities()); its uniforms,
+    helicities and colours are the row e of rambo_uniforms(n, ...),
+    helicities(n, ...) and adjoint_colours / flow_colours /
+    balanced_flow_colours(n, ...) for that n (the generator is counter-based,
+    so event e draws the same numbers as in a single-multiplicity batch that
+    contains it at position e).  Returns nev [B] int32, u [B, 4(n_max-2)]
+    float64 (columns past 4(n_e-2) are 0.5), hel [B, n_max] int8 (columns
+    past n_e are +1), colors [B, 2 n_max] int8 (columns past the event's
+    colour labels are 1)."""
+    nev = multiplicities(batch, n_min, n_max, seed=seed)
+    dmax = 4 * (n_max - 2)
+    u = np.full((batch, dmax), 0.5)
+    hel = np.ones((batch, n_max), dtype=np.int8)
+    col = np.ones((batch, 2 * n_max), dtype=np.int8)
+    for n in range(n_min, n_max + 1):
+        idx = np.nonzero(nev == n)[0].astype(np.uint64)
+        if idx.size == 0:
+            continue
+        d = 4 * (n - 2)
+        cnt = (idx[:, None] * np.uint64(d) + np.arange(d, dtype=np.uint64)[None, :])
+        u[idx.astype(np.int64), :d] = _unit(raw64_at(seed, STREAM_UNIFORMS + 16 * n, cnt))
+        cnt = idx[:, None] * np.uint64(n) + np.arange(n, dtype=np.uint64)[None, :]
+        r = raw64_at(seed, STREAM_HELICITY + 16 * n, cnt) >> np.uint64(63)
+        hel[idx.astype(np.int64), :n] = (1 - 2 * r.astype(np.int64)).astype(np.int8)
+        if colours == "adjoint":
+            r = raw64_at(seed, STREAM_COLOUR + 16 * n, cnt) >> np.uint64(61)
+            col[idx.astype(np.int64), :n] = (1 + r.astype(np.int64)).astype(np.int8)
+        elif colours in ("flow", "balanced_flow"):
+            c2 = idx[:, None] * np.uint64(2 * n) + np.arange(2 * n, dtype=np.uint64)[None, :]
+            uu = _unit(raw64_at(seed, STREAM_COLOUR + 16 * n + 8, c2))
+            fl = (1 + np.minimum((uu * 3.0).astype(np.int64), 2)).astype(np.int8)
+            if colours == "balanced_flow":
+                rows = fl[:, 0::2].astype(np.int64)
+                keys = raw64_at(seed, STREAM_COLOUR + 16 * n + 12, cnt)
+                perm = np.argsort(keys, axis=1, kind="stable")
+                fl[:, 1::2] = np.take_along_axis(rows, perm, axis=1).astype(np.int8)
+            col[idx.astype(np.int64), :2 * n] = fl
+        else:
+            raise ValueError(f"unknown colour sampling {colours!r}")
+    return {"nev": nev, "u": u, "hel": hel, "colors": col}
