@@ -220,8 +220,9 @@ bg_status bg_cd_workspace_bytes(int n, bg_prec prec, int64_t* bytes) {
   if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_cd_workspace_bytes: invalid precision");
   const int sms = device_sms();
   if (sms <= 0) return fail(BG_ECUDA, "bg_cd_workspace_bytes: no device");
-  const size_t slab = (prec == BG_F32) ? cd_slab_bytes_f32(n) : cd_slab_bytes_f64(n);
-  *bytes = (int64_t)slab * cd_grid_ctas(sms);
+  const size_t ws = (prec == BG_F32) ? cd_workspace_bytes_f32(n, sms) : cd_workspace_bytes_f64(n, sms);
+  if (ws == 0) return fail(BG_ECUDA, "bg_cd_workspace_bytes: kernel configuration not supported on this device");
+  *bytes = (int64_t)ws;
   return BG_OK;
 }
 

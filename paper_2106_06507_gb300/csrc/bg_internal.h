@@ -63,12 +63,11 @@ struct ColourSumArgs {
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
 cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
 
-// Colour-dressed recursion (cd_f32.cu, cd_f64.cu): per-CTA workspace slab
-// bytes and launchers; CdParams is defined in cd_recursion.cuh.
+// Colour-dressed recursion (cd_f32.cu, cd_f64.cu): workspace bytes and
+// launchers; CdParams is defined in cd_recursion.cuh.
 struct CdParams;
-size_t cd_slab_bytes_f32(int n);
-size_t cd_slab_bytes_f64(int n);
-int cd_grid_ctas(int sms);
+size_t cd_workspace_bytes_f32(int n, int sms);  // 0 if the kernel cannot launch
+size_t cd_workspace_bytes_f64(int n, int sms);
 cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
 cudaError_t launch_cd_f64(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,

@@ -2,8 +2,7 @@
 #include "cd_recursion.cuh"
 
 namespace bg {
-int cd_grid_ctas(int sms) { return cd_grid(sms); }
-size_t cd_slab_bytes_f32(int n) { return cd_slab_bytes_t<float>(n); }
+size_t cd_workspace_bytes_f32(int n, int sms) { return cd_workspace_bytes_t<float>(n, sms); }
 cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
                           const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
   return launch_cd_t<float>(n, prm, p, hel, col, accept, me2, workspace, status, sms, s);

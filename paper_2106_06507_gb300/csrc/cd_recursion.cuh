@@ -13,70 +13,30 @@
 // with unit vertex factors (the couplings (1/sqrt2)^(n-2) are applied to A).
 // V3 uses current conservation: (X.Y)(P1 - P2) + 2(P.X)Y - 2(P.Y)X.
 //
-// Work decomposition: persistent CTAs, one event at a time per CTA.  The
-// subsets are processed level by level (by size); a task is (subset, colour
-// entry rc, chunk of its ordered partitions) and accumulates 4 + 6 values;
-// levels with few subsets split the partitions into chunks whose partial sums
-// are reduced in a fixed order (deterministic results).  The event's tables
-// (gluon and tensor currents, momenta, inverse propagators) live in a per-CTA
-// slab of global memory that stays resident in L1/L2; per-subset masks of
-// the non-zero colour entries skip products that vanish exactly (most of
-// them in the colour-flow basis).  In the colour-flow basis an event whose
-// flow is not balanced (some colour appears more often as a row than as a
-// column index) has amplitude zero and is skipped.
+// Work decomposition.  Persistent CTAs fetch events from a global counter
+// (dynamic scheduling: events rejected by the cut cost almost nothing, and
+// the CTAs stay balanced).  A CTA evaluates one event at a time, subsets
+// level by level (by size).  A task is (subset, chunk of its ordered
+// partitions, colour entry rc), with rc the fastest index, so that the nine
+// threads of one (subset, chunk) walk the same partitions and their loads of
+// the two sub-currents are broadcasts.  The colour products are computed
+// dense and branch-free (exact zeros contribute exact zeros); a partition is
+// skipped only when one of its sub-currents is zero in every entry.  Levels
+// with few subsets split the partitions into chunks whose partial sums are
+// reduced in a fixed order (deterministic results).
+//
+// Memory.  Each subset has one record (momentum, 9 gluon and 9 tensor
+// colour entries), stored by rank (subsets ordered by size): the records of
+// the first ranks -- the small subsets, which the partitions of every
+// larger subset read -- sit in shared memory, the rest in a per-CTA slab of
+// global memory that stays resident in L1/L2 (one or two CTAs per SM).  At
+// n <= 10 in FP32 the whole table fits in shared memory.
 #pragma once
 
 #include "bg_internal.h"
 #include "device_common.cuh"
 
 namespace bg {
-
-template <int N, typename T>
-struct CdShape {
-  static constexpr int NT = 256;
-  static constexpr int M = N - 1;
-  static constexpr int NS = 1 << M;
-  static constexpr int TARGET = 2 * NT;  // tasks wanted per level
-};
-
-__host__ __device__ constexpr int cd_binom(int n, int k) {
-  return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : cd_binom(n - 1, k - 1) + cd_binom(n - 1, k);
-}
-
-// Chunks of ordered partitions per (subset, colour entry) at level L.
-template <int N>
-__host__ __device__ constexpr int cd_chunks(int L) {
-  constexpr int M = N - 1;
-  const int tasks = 9 * cd_binom(M, L);
-  const int npart = (1 << L) - 2;
-  int c = (2 * 256 + tasks - 1) / tasks;
-  if (c < 1) c = 1;
-  if (c > npart) c = npart;
-  return c;
-}
-
-template <int N>
-__host__ __device__ constexpr int cd_max_partial_tasks() {
-  int mx = 0;
-  for (int L = 2; L < N - 1; ++L) {
-    const int c = cd_chunks<N>(L);
-    if (c > 1 && 9 * cd_binom(N - 1, L) * c > mx) mx = 9 * cd_binom(N - 1, L) * c;
-  }
-  return mx;
-}
-
-// Per-CTA workspace slab layout (bytes), for arithmetic type T.
-template <int N, typename T>
-struct CdSlab {
-  using S = CdShape<N, T>;
-  static constexpr size_t off_J = 0;                                          // T [NS][9][4]
-  static constexpr size_t off_T = off_J + sizeof(T) * S::NS * 36;             // T [NS][9][6]
-  static constexpr size_t off_P = off_T + sizeof(T) * S::NS * 54;             // T [NS][4]
-  static constexpr size_t off_inv = off_P + sizeof(T) * S::NS * 4;            // T [NS]
-  static constexpr size_t off_part = off_inv + sizeof(T) * S::NS;             // T [tasks][10]
-  static constexpr size_t bytes_raw = off_part + sizeof(T) * 10 * (cd_max_partial_tasks<N>() + 1);
-  static constexpr size_t bytes = (bytes_raw + 255) & ~size_t(255);
-};
 
 struct CdParams {
   int64_t B;              // capacity (row stride of p, hel, colours)
@@ -130,88 +90,201 @@ __device__ __forceinline__ int submask_at(int S, int j) {
   return r;
 }
 
-// Contribution of one ordered partition (S1 left, S2 right) to colour entry
-// (r, c), summed over the inner colour index l.
+
+__host__ __device__ constexpr int cd_binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  int c = 1;
+  for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+  return c;
+}
+
+template <int N, typename T>
+struct CdShape {
+  static constexpr int M = N - 1;
+  static constexpr int NS = 1 << M;
+  static constexpr int NT = (N <= 7) ? 128 : (N <= 9) ? 256 : 512;
+  static constexpr int TARGET = 2 * NT;  // tasks wanted per level
+  // subset record: P[4] | J[9][4] | T[9][6] | pad (16-byte multiple)
+  static constexpr int REC = 96;
+  static constexpr int OFF_J = 4, OFF_T = 40;
+  // static shared memory of the kernel (upper bound, bytes)
+  static constexpr size_t STATIC_SMEM = (size_t)NS * (2 + 2 + sizeof(T) + 1) + (size_t)N * 4 * 8 * 2 +
+                                        (size_t)N * 9 * 8 + (size_t)M * M * 8 + (N + 1) * 4 + (NT / 32) * 8 + 64;
+  static constexpr size_t SMEM_LIMIT = 232448;  // opt-in shared memory per block
+  static constexpr int NSM_FIT = (int)((SMEM_LIMIT - STATIC_SMEM - 1024) / (REC * sizeof(T)));
+  static constexpr int NSM = NS < NSM_FIT ? NS : NSM_FIT;  // records (by rank) in shared memory
+  static constexpr size_t DYN_SMEM = (size_t)NSM * REC * sizeof(T);
+};
+
+// Chunks of ordered partitions per (subset, colour entry) at level L.
+template <int N, typename T>
+__host__ __device__ constexpr int cd_chunks(int L) {
+  constexpr int M = N - 1;
+  const int tasks = 9 * cd_binom(M, L);
+  const int npart = (1 << L) - 2;
+  int c = (CdShape<N, T>::TARGET + tasks - 1) / tasks;
+  if (c < 1) c = 1;
+  if (c > npart) c = npart;
+  return c;
+}
+
+template <int N, typename T>
+__host__ __device__ constexpr int cd_max_partial_tasks() {
+  int mx = 0;
+  for (int L = 2; L < N - 1; ++L) {
+    const int c = cd_chunks<N, T>(L);
+    if (c > 1 && 9 * cd_binom(N - 1, L) * c > mx) mx = 9 * cd_binom(N - 1, L) * c;
+  }
+  return mx;
+}
+
+constexpr size_t kCdHeader = 256;  // workspace header: the event counter
+
+// Per-CTA slab of global memory (after the header): records of the ranks
+// that do not fit in shared memory, then the partial sums of chunked tasks.
+template <int N, typename T>
+struct CdSlab {
+  using S = CdShape<N, T>;
+  static constexpr size_t off_rec = 0;
+  static constexpr size_t off_part = off_rec + sizeof(T) * S::REC * (size_t)(S::NS - S::NSM);
+  static constexpr size_t bytes_raw = off_part + sizeof(T) * 10 * (size_t)(cd_max_partial_tasks<N, T>() + 1);
+  static constexpr size_t bytes = (bytes_raw + 255) & ~size_t(255);
+};
+
 template <typename T>
-__device__ __forceinline__ void cd_partition(const T* __restrict__ J, const T* __restrict__ Tt,
-                                             const T* __restrict__ Pt, const uint32_t* __restrict__ nz, int S1,
-                                             int S2, int r, int c, const T (&P2)[4], T (&br)[4], T (&tc)[6],
-                                             bool need_tensor) {
-  const uint32_t m1 = nz[S1], m2 = nz[S2];  // bits 0..8: gluon entries, 9..17: tensor entries
-  T dP[4];
-  const T* p1 = Pt + 4 * S1;
-  const T* p2 = Pt + 4 * S2;
+__device__ __forceinline__ void cd_ld4(const T* p, T (&x)[4]);
+template <>
+__device__ __forceinline__ void cd_ld4<float>(const float* p, float (&x)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void cd_ld4<double>(const double* p, double (&x)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void cd_ld6(const T* p, T (&x)[6]);
+template <>
+__device__ __forceinline__ void cd_ld6<float>(const float* p, float (&x)[6]) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+  const float2 a = q[0], b = q[1], c = q[2];
+  x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y, x[4] = c.x, x[5] = c.y;
+}
+template <>
+__device__ __forceinline__ void cd_ld6<double>(const double* p, double (&x)[6]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = q[0], b = q[1], c = q[2];
+  x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y, x[4] = c.x, x[5] = c.y;
+}
+
+// Contribution of one ordered partition (S1 left, record A; S2 right,
+// record B) to colour entry (r, c), summed over the inner colour index l.
+// Dense: zero entries contribute exact zeros.
+template <typename T, bool TENSOR>
+__device__ __forceinline__ void cd_partition(const T* __restrict__ A, const T* __restrict__ B, int r, int c,
+                                             const T (&P2)[4], T (&br)[4], T (&tc)[6]) {
+  T p1[4], p2[4], dP[4];
+  cd_ld4(A, p1);
+  cd_ld4(B, p2);
 #pragma unroll
   for (int i = 0; i < 4; ++i) dP[i] = p1[i] - p2[i];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     const int e1 = 3 * r + l, e2 = 3 * l + c;
-    const bool x = (m1 >> e1) & 1, y = (m2 >> e2) & 1;
-    const bool tx = (m1 >> (9 + e1)) & 1, ty = (m2 >> (9 + e2)) & 1;
-    if (!((x && (y || ty)) || (y && tx))) continue;
-    const T* X = J + (size_t)S1 * 36 + 4 * e1;
-    const T* Y = J + (size_t)S2 * 36 + 4 * e2;
-    if (x && y) {
-      const T xy = mdot(X, Y);
-      const T px = mdot(P2, X);
-      const T py = mdot(P2, Y);
+    T X[4], Y[4], T1[6], T2[6];
+    cd_ld4(A + 4 + 4 * e1, X);
+    cd_ld4(B + 4 + 4 * e2, Y);
+    cd_ld6(A + 40 + 6 * e1, T1);
+    cd_ld6(B + 40 + 6 * e2, T2);
+    const T xy = mdot(X, Y);
+    const T px = mdot(P2, X);
+    const T py = mdot(P2, Y);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) br[i] += xy * dP[i] + px * Y[i] - py * X[i];
-      if (need_tensor) {
-        tc[0] += X[0] * Y[1] - X[1] * Y[0];
-        tc[1] += X[0] * Y[2] - X[2] * Y[0];
-        tc[2] += X[0] * Y[3] - X[3] * Y[0];
-        tc[3] += X[1] * Y[2] - X[2] * Y[1];
-        tc[4] += X[1] * Y[3] - X[3] * Y[1];
-        tc[5] += X[2] * Y[3] - X[3] * Y[2];
-      }
+    for (int i = 0; i < 4; ++i) br[i] += xy * dP[i] + px * Y[i] - py * X[i];
+    if (TENSOR) {
+      tc[0] += X[0] * Y[1] - X[1] * Y[0];
+      tc[1] += X[0] * Y[2] - X[2] * Y[0];
+      tc[2] += X[0] * Y[3] - X[3] * Y[0];
+      tc[3] += X[1] * Y[2] - X[2] * Y[1];
+      tc[4] += X[1] * Y[3] - X[3] * Y[1];
+      tc[5] += X[2] * Y[3] - X[3] * Y[2];
     }
-    if (x && ty) ten_vec_acc(Tt + (size_t)S2 * 54 + 6 * e2, X, br);
-    if (y && tx) vec_ten_acc(Y, Tt + (size_t)S1 * 54 + 6 * e1, br);
+    ten_vec_acc(T2, X, br);
+    vec_ten_acc(Y, T1, br);
   }
 }
 
+// Rank of S among the subsets of its size in increasing order (colex):
+// sum over its set bits p_1 < p_2 < ... of C(p_j, j).
+__device__ __forceinline__ int cd_colex_rank(int S) {
+  int r = 0, j = 0;
+  for (int s = S; s; s &= s - 1) {
+    ++j;
+    r += cd_binom(__ffs(s) - 1, j);
+  }
+  return r;
+}
+
 template <int N, typename T>
-__global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __restrict__ p,
-                                                 const int8_t* __restrict__ hel, const int8_t* __restrict__ col,
-                                                 const uint8_t* __restrict__ accept, double* __restrict__ me2,
-                                                 unsigned char* __restrict__ workspace, int* __restrict__ status) {
+__device__ __forceinline__ T* cd_rec(T* sRec, T* gRec, int rk) {
+  constexpr int NSM = CdShape<N, T>::NSM, REC = CdShape<N, T>::REC;
+  return rk < NSM ? sRec + (size_t)rk * REC : gRec + (size_t)(rk - NSM) * REC;
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, const double* __restrict__ p,
+                                                                const int8_t* __restrict__ hel,
+                                                                const int8_t* __restrict__ col,
+                                                                const uint8_t* __restrict__ accept,
+                                                                double* __restrict__ me2,
+                                                                unsigned char* __restrict__ workspace,
+                                                                int* __restrict__ status) {
   using Sh = CdShape<N, T>;
   using L = CdSlab<N, T>;
   constexpr int M = Sh::M, NS = Sh::NS, NT = Sh::NT;
-  unsigned char* slab = workspace + (size_t)blockIdx.x * L::bytes;
-  T* J = reinterpret_cast<T*>(slab + L::off_J);
-  T* Tt = reinterpret_cast<T*>(slab + L::off_T);
-  T* Pt = reinterpret_cast<T*>(slab + L::off_P);
-  T* inv = reinterpret_cast<T*>(slab + L::off_inv);
-  T* part = reinterpret_cast<T*>(slab + L::off_part);
+  extern __shared__ __align__(16) unsigned char cd_smem[];
+  T* const sRec = reinterpret_cast<T*>(cd_smem);
+  unsigned long long* const counter = reinterpret_cast<unsigned long long*>(workspace);
+  unsigned char* const slab = workspace + kCdHeader + (size_t)blockIdx.x * L::bytes;
+  T* const gRec = reinterpret_cast<T*>(slab + L::off_rec);
+  T* const part = reinterpret_cast<T*>(slab + L::off_part);
 
-  __shared__ double s_k[N][4];       // scaled outgoing momenta (FP64)
-  __shared__ double s_e[N][4];       // polarisations (FP64)
-  __shared__ double s_E[N][3][3];    // external colour matrices
-  __shared__ double s_pair[M][M];    // pair invariants 2 k_a.k_b / s (FP64)
-  __shared__ uint32_t s_nz[NS];      // non-zero colour entries per subset
-  __shared__ uint16_t s_list[NS];    // subsets ordered by size
-  __shared__ int s_off[N + 1];
-  __shared__ int s_skip;
+  __shared__ uint16_t s_list[NS];  // rank -> subset
+  __shared__ uint16_t s_rank[NS];  // subset -> rank
+  __shared__ T s_inv[NS];          // inverse propagators, by rank
+  __shared__ uint8_t s_nz[NS];     // record has a non-zero entry, by rank
+  __shared__ int s_off[N + 1];     // first rank of each size
+  __shared__ double s_k[N][4];     // scaled outgoing momenta (FP64)
+  __shared__ double s_e[N][4];     // polarisations (FP64)
+  __shared__ double s_E[N][3][3];  // external colour matrices
+  __shared__ double s_pair[M][M];  // pair invariants 2 k_a.k_b / s (FP64)
   __shared__ double s_red[NT / 32];
+  __shared__ long long s_ev;
+  __shared__ int s_skip;
 
   const int tid = threadIdx.x;
   const int64_t S_ = prm.B;
   const int64_t Bn = prm.dB ? (*prm.dB < S_ ? *prm.dB : S_) : S_;
-  // subsets grouped by size (event independent)
-  if (tid == 0) {
-    int pos = 0;
-    for (int Lv = 0; Lv <= M; ++Lv) {
-      s_off[Lv] = pos;
-      for (int Sx = 0; Sx < NS; ++Sx)
-        if (__popc(Sx) == Lv) s_list[pos++] = (uint16_t)Sx;
-    }
-    s_off[M + 1] = pos;
+  // subsets ordered by size, then increasing (event independent)
+  if (tid <= M + 1) {
+    int o = 0;
+    for (int i = 0; i < tid; ++i) o += cd_binom(M, i);
+    s_off[tid] = o;
+  }
+  __syncthreads();
+  for (int Sx = tid; Sx < NS; Sx += NT) {
+    const int rk = s_off[__popc(Sx)] + cd_colex_rank(Sx);
+    s_list[rk] = (uint16_t)Sx;
+    s_rank[Sx] = (uint16_t)rk;
   }
   __syncthreads();
 
-  for (int64_t e = blockIdx.x; e < Bn; e += gridDim.x) {
+  for (;;) {
+    if (tid == 0) s_ev = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t e = s_ev;
+    if (e >= Bn) break;
     // ---- external states (FP64) ----
     if (tid < N) {
       const int g = tid;
@@ -274,7 +347,8 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
       continue;
     }
     // ---- subset momenta, inverse propagators (FP64 -> T), level 1 ----
-    for (int Sx = tid; Sx < NS; Sx += NT) {
+    for (int rk = tid; rk < NS; rk += NT) {
+      const int Sx = s_list[rk];
       double P[4] = {0.0, 0.0, 0.0, 0.0}, p2 = 0.0;
       for (int a = 0; a < M; ++a) {
         if (!((Sx >> a) & 1)) continue;
@@ -283,21 +357,22 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
         for (int b = a + 1; b < M; ++b)
           if ((Sx >> b) & 1) p2 += s_pair[a][b];
       }
+      T* R = cd_rec<N, T>(sRec, gRec, rk);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) Pt[4 * Sx + m] = T(P[m]);
-      inv[Sx] = (__popc(Sx) >= 2 && Sx != NS - 1) ? T(1) / T(p2) : T(0);
+      for (int m = 0; m < 4; ++m) R[m] = T(P[m]);
+      s_inv[rk] = (__popc(Sx) >= 2 && Sx != NS - 1) ? T(1.0 / p2) : T(0);
       if (__popc(Sx) == 1) {
         const int g = __ffs(Sx) - 1;
-        uint32_t mask = 0;
+        bool any = false;
         for (int rc = 0; rc < 9; ++rc) {
-          const double c = s_E[g][rc / 3][rc % 3];
-          if (c != 0.0) mask |= 1u << rc;
+          const double cf = s_E[g][rc / 3][rc % 3];
+          any = any || (cf != 0.0);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) J[(size_t)Sx * 36 + 4 * rc + m] = T(c * s_e[g][m]);
+          for (int m = 0; m < 4; ++m) R[Sh::OFF_J + 4 * rc + m] = T(cf * s_e[g][m]);
 #pragma unroll
-          for (int m = 0; m < 6; ++m) Tt[(size_t)Sx * 54 + 6 * rc + m] = T(0);
+          for (int m = 0; m < 6; ++m) R[Sh::OFF_T + 6 * rc + m] = T(0);
         }
-        s_nz[Sx] = mask;
+        s_nz[rk] = any ? 1 : 0;
       }
     }
     __syncthreads();
@@ -305,30 +380,34 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
     // ---- levels 2 .. M-1 ----
     for (int Lv = 2; Lv < M; ++Lv) {
       const int nsub = s_off[Lv + 1] - s_off[Lv];
-      const int nch = cd_chunks<N>(Lv);
+      const int nch = cd_chunks<N, T>(Lv);
       const int npart = (1 << Lv) - 2;
-      const int ntask = nsub * 9 * nch;
+      const int ntask = nsub * nch * 9;
       for (int t = tid; t < ntask; t += NT) {
-        const int ch = t % nch;
-        const int rc = (t / nch) % 9;
-        const int si = t / (nch * 9);
-        const int Sx = s_list[s_off[Lv] + si];
+        const int rc = t % 9;
+        const int u = t / 9;
+        const int ch = u % nch;
+        const int rkS = s_off[Lv] + u / nch;
+        const int Sx = s_list[rkS];
         const int r = rc / 3, c = rc % 3;
-        const int j0 = 1 + (int)((long)ch * npart / nch), j1 = 1 + (int)((long)(ch + 1) * npart / nch);
+        T* RS = cd_rec<N, T>(sRec, gRec, rkS);
         T P2[4], br[4] = {T(0), T(0), T(0), T(0)}, tc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
-        for (int m = 0; m < 4; ++m) P2[m] = T(2) * Pt[4 * Sx + m];
+        for (int m = 0; m < 4; ++m) P2[m] = T(2) * RS[m];
+        const int j0 = 1 + (int)((long)ch * npart / nch), j1 = 1 + (int)((long)(ch + 1) * npart / nch);
         int S1 = submask_at(Sx, j0);
         for (int j = j0; j < j1; ++j) {
-          cd_partition(J, Tt, Pt, s_nz, S1, Sx ^ S1, r, c, P2, br, tc, true);
+          const int r1 = s_rank[S1], r2 = s_rank[Sx ^ S1];
+          if (s_nz[r1] & s_nz[r2])
+            cd_partition<T, true>(cd_rec<N, T>(sRec, gRec, r1), cd_rec<N, T>(sRec, gRec, r2), r, c, P2, br, tc);
           S1 = ((S1 | ~Sx) + 1) & Sx;
         }
         if (nch == 1) {
-          const T ip = inv[Sx];
+          const T ip = s_inv[rkS];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) J[(size_t)Sx * 36 + 4 * rc + m] = br[m] * ip;
+          for (int m = 0; m < 4; ++m) RS[Sh::OFF_J + 4 * rc + m] = br[m] * ip;
 #pragma unroll
-          for (int m = 0; m < 6; ++m) Tt[(size_t)Sx * 54 + 6 * rc + m] = tc[m];
+          for (int m = 0; m < 6; ++m) RS[Sh::OFF_T + 6 * rc + m] = tc[m];
         } else {
 #pragma unroll
           for (int m = 0; m < 4; ++m) part[(size_t)t * 10 + m] = br[m];
@@ -338,37 +417,33 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
       }
       __syncthreads();
       if (nch > 1) {
-        for (int u = tid; u < nsub * 9; u += NT) {
-          const int rc = u % 9, si = u / 9;
-          const int Sx = s_list[s_off[Lv] + si];
+        for (int v = tid; v < nsub * 9; v += NT) {
+          const int rc = v % 9, si = v / 9;
+          const int rkS = s_off[Lv] + si;
           T acc[10];
 #pragma unroll
           for (int m = 0; m < 10; ++m) acc[m] = T(0);
-          for (int ch = 0; ch < nch; ++ch)
+          for (int ch = 0; ch < nch; ++ch) {
+            const size_t t = ((size_t)si * nch + ch) * 9 + rc;
 #pragma unroll
-            for (int m = 0; m < 10; ++m) acc[m] += part[((size_t)u * nch + ch) * 10 + m];
-          const T ip = inv[Sx];
+            for (int m = 0; m < 10; ++m) acc[m] += part[t * 10 + m];
+          }
+          T* RS = cd_rec<N, T>(sRec, gRec, rkS);
+          const T ip = s_inv[rkS];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) J[(size_t)Sx * 36 + 4 * rc + m] = acc[m] * ip;
+          for (int m = 0; m < 4; ++m) RS[Sh::OFF_J + 4 * rc + m] = acc[m] * ip;
 #pragma unroll
-          for (int m = 0; m < 6; ++m) Tt[(size_t)Sx * 54 + 6 * rc + m] = acc[4 + m];
+          for (int m = 0; m < 6; ++m) RS[Sh::OFF_T + 6 * rc + m] = acc[4 + m];
         }
         __syncthreads();
       }
-      // non-zero masks of this level
+      // non-zero flags of this level
       for (int si = tid; si < nsub; si += NT) {
-        const int Sx = s_list[s_off[Lv] + si];
-        uint32_t mask = 0;
-        for (int rc = 0; rc < 9; ++rc) {
-          bool zj = true, zt = true;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) zj = zj && (J[(size_t)Sx * 36 + 4 * rc + m] == T(0));
-#pragma unroll
-          for (int m = 0; m < 6; ++m) zt = zt && (Tt[(size_t)Sx * 54 + 6 * rc + m] == T(0));
-          if (!zj) mask |= 1u << rc;
-          if (!zt) mask |= 1u << (9 + rc);
-        }
-        s_nz[Sx] = mask;
+        const int rk = s_off[Lv] + si;
+        const T* R = cd_rec<N, T>(sRec, gRec, rk);
+        bool any = false;
+        for (int i = Sh::OFF_J; i < Sh::OFF_T + 54; ++i) any = any || (R[i] != T(0));
+        s_nz[rk] = any ? 1 : 0;
       }
       __syncthreads();
     }
@@ -378,15 +453,16 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
       constexpr int FULL = NS - 1;
       constexpr int npart = NS - 2;
       constexpr int nch = (2 * NT + 8) / 9 < npart ? (2 * NT + 8) / 9 : npart;
+      const T* RF = cd_rec<N, T>(sRec, gRec, NS - 1);
       T en[4], P2[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         en[m] = T(s_e[N - 1][m]);
-        P2[m] = T(2) * Pt[4 * FULL + m];
+        P2[m] = T(2) * RF[m];
       }
       double acc = 0.0;
       for (int t = tid; t < 9 * nch; t += NT) {
-        const int rc = t / nch, ch = t % nch;
+        const int rc = t % 9, ch = t / 9;
         const int r = rc / 3, c = rc % 3;
         const double w = s_E[N - 1][c][r];
         if (w == 0.0) continue;
@@ -394,7 +470,9 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
         T br[4] = {T(0), T(0), T(0), T(0)}, tc[6];
         int S1 = submask_at(FULL, j0);
         for (int j = j0; j < j1; ++j) {
-          cd_partition(J, Tt, Pt, s_nz, S1, FULL ^ S1, r, c, P2, br, tc, false);
+          const int r1 = s_rank[S1], r2 = s_rank[FULL ^ S1];
+          if (s_nz[r1] & s_nz[r2])
+            cd_partition<T, false>(cd_rec<N, T>(sRec, gRec, r1), cd_rec<N, T>(sRec, gRec, r2), r, c, P2, br, tc);
           S1 = ((S1 | ~FULL) + 1) & FULL;
         }
         acc += w * (double)mdot(en, br);
@@ -415,35 +493,51 @@ __global__ void __launch_bounds__(256) cd_kernel(CdParams prm, const double* __r
 }
 
 template <int N, typename T>
-size_t cd_slab_bytes() {
-  return CdSlab<N, T>::bytes;
+int cd_ctas_per_sm() {
+  using Sh = CdShape<N, T>;
+  if (cudaFuncSetAttribute(cd_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::DYN_SMEM) !=
+      cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cd_kernel<N, T>, Sh::NT, Sh::DYN_SMEM) != cudaSuccess)
+    return 0;
+  return nb;
 }
 
-// Persistent grid: 2 CTAs per SM.
-inline int cd_grid(int sms) { return 2 * sms; }
+template <int N, typename T>
+size_t cd_workspace_bytes_n(int sms) {
+  const int nb = cd_ctas_per_sm<N, T>();
+  if (nb <= 0) return 0;
+  return kCdHeader + (size_t)sms * nb * CdSlab<N, T>::bytes;
+}
 
 template <int N, typename T>
 cudaError_t launch_cd_n(const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
                         const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
-  int64_t grid = cd_grid(sms);
+  const int nb = cd_ctas_per_sm<N, T>();
+  if (nb <= 0) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)sms * nb;
   if (grid > prm.B) grid = prm.B;
-  cd_kernel<N, T><<<(unsigned)grid, CdShape<N, T>::NT, 0, s>>>(prm, p, hel, col, accept, me2,
-                                                                 static_cast<unsigned char*>(workspace), status);
+  // the event counter starts at zero for every launch
+  cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  cd_kernel<N, T><<<(unsigned)grid, CdShape<N, T>::NT, CdShape<N, T>::DYN_SMEM, s>>>(
+      prm, p, hel, col, accept, me2, static_cast<unsigned char*>(workspace), status);
   return cudaGetLastError();
 }
 
 template <typename T>
-size_t cd_slab_bytes_t(int n) {
+size_t cd_workspace_bytes_t(int n, int sms) {
   switch (n) {
-    case 4: return cd_slab_bytes<4, T>();
-    case 5: return cd_slab_bytes<5, T>();
-    case 6: return cd_slab_bytes<6, T>();
-    case 7: return cd_slab_bytes<7, T>();
-    case 8: return cd_slab_bytes<8, T>();
-    case 9: return cd_slab_bytes<9, T>();
-    case 10: return cd_slab_bytes<10, T>();
-    case 11: return cd_slab_bytes<11, T>();
-    case 12: return cd_slab_bytes<12, T>();
+    case 4: return cd_workspace_bytes_n<4, T>(sms);
+    case 5: return cd_workspace_bytes_n<5, T>(sms);
+    case 6: return cd_workspace_bytes_n<6, T>(sms);
+    case 7: return cd_workspace_bytes_n<7, T>(sms);
+    case 8: return cd_workspace_bytes_n<8, T>(sms);
+    case 9: return cd_workspace_bytes_n<9, T>(sms);
+    case 10: return cd_workspace_bytes_n<10, T>(sms);
+    case 11: return cd_workspace_bytes_n<11, T>(sms);
+    case 12: return cd_workspace_bytes_n<12, T>(sms);
     default: return 0;
   }
 }

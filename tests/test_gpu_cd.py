@@ -13,10 +13,13 @@ Tolerances (derived in the design notes):
   FP64: compared with the oracle in extended precision; as accurate as the
   plain FP64 oracle (median below max(1e-13, 8x the FP64 oracle's median), events above 1e-12 at most 2 + 1% + 4x
   the FP64 oracle's count, worst within max(5e-11, 8x the FP64 oracle's)).
-  FP32: median relative error < 1e-5, 99% of events < 1e-3.  The colour-
-  dressed amplitude of one colour sample is a sum of many colour-ordered
-  amplitudes with colour weights of both signs, so cancellations amplify
-  FP32 rounding more than in the colour-summed |M|^2.
+  FP32: median relative error < 1e-5; 99% of events within 1e-3 of
+  max(|M|^2, 1e-2 x the sample's median |M|^2).  The colour-dressed
+  amplitude of one colour sample is a sum of many colour-ordered amplitudes
+  with colour weights of both signs, so cancellations amplify FP32 rounding
+  more than in the colour-summed |M|^2; an event whose amplitude cancels to
+  a small fraction of the typical one keeps an absolute error of the size of
+  the cancelling terms.
 """
 import itertools
 
@@ -63,6 +66,14 @@ def split_zeros(got, ref, tol=1e-10):
     return ~zero
 
 
+def fp32_rel(got, ref):
+    """Error of FP32 results relative to max(|M|^2, 1e-2 x the sample's median
+    |M|^2): an event whose amplitude cancels to a small fraction of the
+    typical amplitude keeps an absolute FP32 error of the size of the terms
+    that cancel, so its own relative error is unbounded."""
+    return np.abs(got - ref) / np.maximum(ref, 1e-2 * np.median(ref))
+
+
 def assert_fp64_like(got, ext, f64):
     nz = split_zeros(got, ext)
     if not nz.any():
@@ -102,8 +113,8 @@ def test_cd_fp32_parity(bg, oracle, n, B, flow):
     ref = oracle.me2_cd(n, u, hel, cols, 1 if flow else 0, sqrt_s=SQRT_S, pt_min=-1.0)
     nz = split_zeros(got, ref, tol=1e-6)
     assert nz.sum() >= 2
-    rel = np.abs(got[nz] / ref[nz] - 1.0)
-    assert np.median(rel) < 1e-5
+    assert np.median(np.abs(got[nz] / ref[nz] - 1.0)) < 1e-5
+    rel = fp32_rel(got[nz], ref[nz])
     assert np.quantile(rel, 0.99) < 1e-3
 
 
