@@ -308,6 +308,8 @@ bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const
  *   cs_mode:  colour-sum arithmetic of the colour-ordered branches; the
  *             tensor-core mode applies to 6 <= n <= 9, smaller n use FP32
  *   color_mode: colour sampling of the colour-dressed branches
+ *   autotune: run bg_autotune for every branch's recursion before the graph
+ *             is recorded (the graph keeps the variants chosen then)
  * The paper has no single-launch counterpart: it runs one multiplicity at
  * a time.
  * ------------------------------------------------------------------------- */
@@ -323,6 +325,7 @@ typedef struct {
   bg_color_mode color_mode;
   int n_co_max;
   int64_t chunk_bytes;
+  int autotune;       /* 1: bg_autotune each branch's recursion at creation */
 } bg_mixed_desc;
 typedef struct bg_mixed bg_mixed;
 /* Errors: BG_EINVAL (desc), BG_ENOMEM, BG_ECUDA.  Synchronises the device. */
@@ -352,6 +355,36 @@ int64_t bg_mixed_workspace_bytes(const bg_mixed* plan);
 bg_status bg_mixed_run(bg_mixed* plan, int64_t B, void* stream);
 /* counts[13]: events of each n in the last run (synchronises the device). */
 bg_status bg_mixed_counts(bg_mixed* plan, int64_t* counts);
+
+/* ---------------------------------------------------------------------------
+ * Autotuning (no counterpart in the paper).  Each recursion has kernel
+ * variants that compute the same sums in the same order -- bitwise identical
+ * results -- and differ in how the work maps onto the GPU:
+ *   BG_ALGO_CO (sampled helicities, n >= 6): 0 = one thread per ordering,
+ *     1 = depth-first groups of six orderings sharing prefix currents
+ *     (default); helicity sums and n < 6 have one variant;
+ *   BG_ALGO_CD: threads per event (CTA size): n <= 9: 0 = 128, 1 = 256;
+ *     n >= 10: 0 = 256, 1 = 384, 2 = 512 (defaults 128 for n <= 8, 256 for
+ *     n = 9, 512 for n >= 10).
+ * bg_autotune times every variant of (algo, n, prec) on a synthetic probe
+ * batch of probe_batch events (<= 0: a size chosen by n) on `stream`, stores
+ * the fastest in a process-wide table for the current device and returns it
+ * in *best (ms[v], if not NULL, receives the time of variant v; give it
+ * bg_tune_num_variants entries).  It allocates and frees the probe buffers,
+ * synchronises `stream`, and must not run during stream capture.  Calls that
+ * launch a recursion (bg_currents_co, bg_currents_cd, bg_me2_batch, the
+ * mixed graph at creation) use the table's entry for the current device.
+ * bg_tune_set forces a variant (-1 restores the default); bg_tune_get reads
+ * it (-1 = default).  bg_tune_save / bg_tune_load write and read the table
+ * as text keyed by the device name (entries for other devices are ignored
+ * on load).  Errors: BG_EINVAL, BG_ENOMEM, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+int bg_tune_num_variants(bg_algo algo, int n);
+bg_status bg_autotune(bg_algo algo, int n, bg_prec prec, int64_t probe_batch, void* stream, int* best, float* ms);
+bg_status bg_tune_set(bg_algo algo, int n, bg_prec prec, int variant);
+bg_status bg_tune_get(bg_algo algo, int n, bg_prec prec, int* variant);
+bg_status bg_tune_save(const char* path);
+bg_status bg_tune_load(const char* path);
 
 /* Device status word of the current device: 0 if no kernel has seen an
  * invalid label since the last reset, else a BG_* code.  Synchronises the

@@ -42,7 +42,8 @@ class MixedDesc(ctypes.Structure):
     _fields_ = [("n_min", ctypes.c_int), ("n_max", ctypes.c_int), ("max_batch", ctypes.c_int64),
                 ("sqrt_s", ctypes.c_double), ("pt_min", ctypes.c_double), ("g_s", ctypes.c_double),
                 ("q", ctypes.c_double * 4), ("prec", ctypes.c_int), ("cs_mode", ctypes.c_int),
-                ("color_mode", ctypes.c_int), ("n_co_max", ctypes.c_int), ("chunk_bytes", ctypes.c_int64)]
+                ("color_mode", ctypes.c_int), ("n_co_max", ctypes.c_int), ("chunk_bytes", ctypes.c_int64),
+                ("autotune", ctypes.c_int)]
 
 
 class BGError(RuntimeError):
@@ -89,13 +90,21 @@ def lib() -> ctypes.CDLL:
         L.bg_mixed_workspace_bytes.restype = c_i64
         L.bg_mixed_run.argtypes = [vp, c_i64, vp]
         L.bg_mixed_counts.argtypes = [vp, ctypes.POINTER(c_i64)]
+        L.bg_tune_num_variants.argtypes = [c_int, c_int]
+        L.bg_tune_num_variants.restype = c_int
+        L.bg_autotune.argtypes = [c_int, c_int, c_int, c_i64, vp, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)]
+        L.bg_tune_set.argtypes = [c_int, c_int, c_int, c_int]
+        L.bg_tune_get.argtypes = [c_int, c_int, c_int, ctypes.POINTER(c_int)]
+        L.bg_tune_save.argtypes = [ctypes.c_char_p]
+        L.bg_tune_load.argtypes = [ctypes.c_char_p]
         L.bg_device_status.argtypes = [ctypes.POINTER(c_int)]
         L.bg_device_status_reset.argtypes = []
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_probe_fma", "bg_cd_workspace_bytes",
                      "bg_currents_cd", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
-                     "bg_mixed_counts"):
+                     "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
+                     "bg_tune_load"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -312,12 +321,14 @@ class Mixed:
 
     def __init__(self, n_min: int, n_max: int, max_batch: int, sqrt_s: float = 1000.0, pt_min: float = -1.0,
                  g_s: float = G_S_DEFAULT, q=DEFAULT_Q, prec: int = BG_F32, cs_mode: int = BG_CS_F32,
-                 color_mode: int = BG_COL_ADJOINT, n_co_max: int = 9, chunk_bytes: int = 0):
+                 color_mode: int = BG_COL_ADJOINT, n_co_max: int = 9, chunk_bytes: int = 0,
+                 autotune: bool = False):
         d = MixedDesc()
         d.n_min, d.n_max, d.max_batch, d.sqrt_s, d.pt_min, d.g_s = n_min, n_max, max_batch, sqrt_s, pt_min, g_s
         for i in range(4):
             d.q[i] = float(q[i])
         d.prec, d.cs_mode, d.color_mode, d.n_co_max, d.chunk_bytes = prec, cs_mode, color_mode, n_co_max, chunk_bytes
+        d.autotune = int(autotune)
         self.desc = d
         h = ctypes.c_void_p()
         _check(lib().bg_mixed_create(ctypes.byref(d), ctypes.byref(h)))
@@ -391,6 +402,38 @@ def probe_fma(prec: int, blocks: int, iters: int, stream=None) -> float:
     flops = ctypes.c_double(0.0)
     _check(lib().bg_probe_fma(prec, blocks, iters, ctypes.byref(flops), _stream(stream)))
     return flops.value
+
+
+def tune_num_variants(algo: int, n: int) -> int:
+    return int(lib().bg_tune_num_variants(algo, n))
+
+
+def autotune(algo: int, n: int, prec: int = BG_F32, probe_batch: int = 0, stream=None):
+    """Times every kernel variant of (algo, n, prec), records the fastest for
+    the current device; returns (best variant, [ms per variant])."""
+    nv = tune_num_variants(algo, n)
+    ms = (ctypes.c_float * max(nv, 1))()
+    best = ctypes.c_int(-1)
+    _check(lib().bg_autotune(algo, n, prec, probe_batch, _stream(stream), ctypes.byref(best), ms))
+    return best.value, [float(ms[i]) for i in range(nv)]
+
+
+def tune_set(algo: int, n: int, prec: int, variant: int) -> None:
+    _check(lib().bg_tune_set(algo, n, prec, variant))
+
+
+def tune_get(algo: int, n: int, prec: int) -> int:
+    v = ctypes.c_int(-1)
+    _check(lib().bg_tune_get(algo, n, prec, ctypes.byref(v)))
+    return v.value
+
+
+def tune_save(path: str) -> None:
+    _check(lib().bg_tune_save(path.encode()))
+
+
+def tune_load(path: str) -> None:
+    _check(lib().bg_tune_load(path.encode()))
 
 
 def device_status() -> int:

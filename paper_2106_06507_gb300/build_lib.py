@@ -35,6 +35,7 @@ SOURCES = [
     "co_grad.cu",
     "grad_rambo.cu",
     "mixed.cu",
+    "tune.cu",
 ]
 
 

@@ -50,6 +50,21 @@ static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintpt
 
 using namespace bg;
 
+namespace bg {
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
+}
+}  // namespace bg
+
 extern "C" {
 
 const char* bg_last_error(void) { return g_last_error.c_str(); }
@@ -207,12 +222,6 @@ bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps,
   return cuda_check(e, "bg_color_sum");
 }
 
-static int device_sms() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return sms;
-}
 
 bg_status bg_cd_workspace_bytes(int n, bg_prec prec, int64_t* bytes) {
   if (!bytes) return fail(BG_EINVAL, "bg_cd_workspace_bytes: NULL");

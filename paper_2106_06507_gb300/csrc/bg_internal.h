@@ -30,8 +30,10 @@ int64_t perm_rank(const int* perm, int m);
 // Dense matrix from the row: C[s][t] = row[rank(sigma_s^-1 o sigma_t)].
 void colour_dense(int n, const std::vector<double>& row, std::vector<double>& dense);
 
-// Device status word (api.cu).
+// Device status word and SM count of the current device (api.cu; 0 if
+// there is no device).
 int* device_status_ptr();
+int device_sms();
 
 // Kernel launchers (one per .cu file).
 // Kernels take a capacity B (row stride of event-indexed SoA arrays) and an
@@ -40,10 +42,18 @@ int* device_status_ptr();
 cudaError_t launch_rambo(int n, int64_t B, double sqrt_s, const double* u, double* p, double pt_min,
                          uint8_t* accept, cudaStream_t s, const int64_t* dB = nullptr);
 
+// variant < 0: the autotuner's choice for (n, precision) on the current
+// device, else the default (tune.cu).
 cudaError_t launch_co_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                          float* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr);
+                          float* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr, int variant = -1);
 cudaError_t launch_co_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                          double* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr);
+                          double* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr, int variant = -1);
+int co_variants(int n, bool helicity_sum);  // number of recursion variants
+
+// Autotuner table (tune.cu): the chosen variant of a kernel family for
+// (n, precision) on the current device, or -1 (default).
+enum TuneFamily { kTuneCO = 0, kTuneCD = 1 };
+int tune_variant(int family, int n, int prec);
 
 struct ColourSumArgs {
   int n;
@@ -69,9 +79,12 @@ struct CdParams;
 size_t cd_workspace_bytes_f32(int n, int sms);  // 0 if the kernel cannot launch
 size_t cd_workspace_bytes_f64(int n, int sms);
 cudaError_t launch_cd_f32(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                          const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
+                          const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s,
+                          int variant = -1);
 cudaError_t launch_cd_f64(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                          const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s);
+                          const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s,
+                          int variant = -1);
+int cd_variants(int n);  // number of kernel variants (threads per event)
 // (CdParams carries the capacity B and an optional device-side count dB.)
 
 // Gradient (co_grad.cu, grad_rambo.cu).

@@ -17,9 +17,11 @@
 // (dynamic scheduling: events rejected by the cut cost almost nothing, and
 // the CTAs stay balanced).  A CTA evaluates one event at a time, subsets
 // level by level (by size).  A task is (subset, chunk of its ordered
-// partitions, colour entry rc), with rc the fastest index, so that the nine
-// threads of one (subset, chunk) walk the same partitions and their loads of
-// the two sub-currents are broadcasts.  The colour products are computed
+// partitions, colour row r) and computes the three entries (r, c) of the
+// row: it reuses each left sub-current entry (r, l) for three products, and
+// the three threads of one (subset, chunk), r fastest, walk the same
+// partitions, so that their loads of the right sub-current (l, c) are
+// broadcasts.  The colour products are computed
 // dense and branch-free (exact zeros contribute exact zeros); a partition is
 // skipped only when one of its sub-currents is zero in every entry.  Levels
 // with few subsets split the partitions into chunks whose partial sums are
@@ -98,29 +100,42 @@ __host__ __device__ constexpr int cd_binom(int n, int k) {
   return c;
 }
 
+// Threads per CTA (one event per CTA) of the kernel variants, and the
+// default variant.  The task decomposition below depends on N only, so all
+// variants compute every sum in the same order: bitwise identical results.
+__host__ __device__ constexpr int cd_num_variants(int N) { return N <= 9 ? 2 : 3; }
+__host__ __device__ constexpr int cd_variant_threads(int N, int v) {
+  return N <= 9 ? (v == 0 ? 128 : 256) : (v == 0 ? 256 : v == 1 ? 384 : 512);
+}
+__host__ __device__ constexpr int cd_default_variant(int N) { return N <= 8 ? 0 : N == 9 ? 1 : 2; }
+
 template <int N, typename T>
 struct CdShape {
   static constexpr int M = N - 1;
   static constexpr int NS = 1 << M;
-  static constexpr int NT = (N <= 7) ? 128 : (N <= 9) ? 256 : 512;
-  static constexpr int TARGET = 2 * NT;  // tasks wanted per level
-  // subset record: P[4] | J[9][4] | T[9][6] | pad (16-byte multiple)
-  static constexpr int REC = 96;
-  static constexpr int OFF_J = 4, OFF_T = 40;
+  static constexpr int TARGET = (N <= 8) ? 256 : (N == 9) ? 512 : 1024;  // tasks wanted per level
+  // subset record: P[4] | J[9][4] | T[9][6] | 1/P^2 | pad.  100 elements:
+  // a multiple of 16 bytes whose word count is not a multiple of 32, so that
+  // records read by different threads spread over the shared-memory banks.
+  static constexpr int REC = 100;
+  static constexpr int OFF_J = 4, OFF_T = 40, OFF_INV = 94;
   // static shared memory of the kernel (upper bound, bytes)
-  static constexpr size_t STATIC_SMEM = (size_t)NS * (2 + 2 + sizeof(T) + 1) + (size_t)N * 4 * 8 * 2 +
-                                        (size_t)N * 9 * 8 + (size_t)M * M * 8 + (N + 1) * 4 + (NT / 32) * 8 + 64;
+  static constexpr size_t STATIC_SMEM = (size_t)NS * (2 + 2 + 1) + (size_t)N * 4 * 8 * 2 +
+                                        (size_t)N * 9 * 8 + (size_t)M * M * 8 + (N + 1) * 4 + 64;
   static constexpr size_t SMEM_LIMIT = 232448;  // opt-in shared memory per block
   static constexpr int NSM_FIT = (int)((SMEM_LIMIT - STATIC_SMEM - 1024) / (REC * sizeof(T)));
   static constexpr int NSM = NS < NSM_FIT ? NS : NSM_FIT;  // records (by rank) in shared memory
   static constexpr size_t DYN_SMEM = (size_t)NSM * REC * sizeof(T);
+  // top level: chunks of the partitions of the full set, per colour row
+  static constexpr int NPART_TOP = NS - 2;
+  static constexpr int NCH_TOP = (TARGET + 2) / 3 < NPART_TOP ? (TARGET + 2) / 3 : NPART_TOP;
 };
 
-// Chunks of ordered partitions per (subset, colour entry) at level L.
+// Chunks of ordered partitions per (subset, colour row) at level L.
 template <int N, typename T>
 __host__ __device__ constexpr int cd_chunks(int L) {
   constexpr int M = N - 1;
-  const int tasks = 9 * cd_binom(M, L);
+  const int tasks = 3 * cd_binom(M, L);
   const int npart = (1 << L) - 2;
   int c = (CdShape<N, T>::TARGET + tasks - 1) / tasks;
   if (c < 1) c = 1;
@@ -133,7 +148,7 @@ __host__ __device__ constexpr int cd_max_partial_tasks() {
   int mx = 0;
   for (int L = 2; L < N - 1; ++L) {
     const int c = cd_chunks<N, T>(L);
-    if (c > 1 && 9 * cd_binom(N - 1, L) * c > mx) mx = 9 * cd_binom(N - 1, L) * c;
+    if (c > 1 && 3 * cd_binom(N - 1, L) * c > mx) mx = 3 * cd_binom(N - 1, L) * c;
   }
   return mx;
 }
@@ -147,7 +162,8 @@ struct CdSlab {
   using S = CdShape<N, T>;
   static constexpr size_t off_rec = 0;
   static constexpr size_t off_part = off_rec + sizeof(T) * S::REC * (size_t)(S::NS - S::NSM);
-  static constexpr size_t bytes_raw = off_part + sizeof(T) * 10 * (size_t)(cd_max_partial_tasks<N, T>() + 1);
+  static constexpr size_t off_top = off_part + sizeof(T) * 30 * (size_t)(cd_max_partial_tasks<N, T>() + 1);
+  static constexpr size_t bytes_raw = off_top + sizeof(double) * 3 * (size_t)S::NCH_TOP;
   static constexpr size_t bytes = (bytes_raw + 255) & ~size_t(255);
 };
 
@@ -179,11 +195,11 @@ __device__ __forceinline__ void cd_ld6<double>(const double* p, double (&x)[6]) 
 }
 
 // Contribution of one ordered partition (S1 left, record A; S2 right,
-// record B) to colour entry (r, c), summed over the inner colour index l.
-// Dense: zero entries contribute exact zeros.
+// record B) to the colour entries (r, c), c = 0..2, of row r, summed over
+// the inner colour index l.  Dense: zero entries contribute exact zeros.
 template <typename T, bool TENSOR>
-__device__ __forceinline__ void cd_partition(const T* __restrict__ A, const T* __restrict__ B, int r, int c,
-                                             const T (&P2)[4], T (&br)[4], T (&tc)[6]) {
+__device__ __forceinline__ void cd_partition(const T* __restrict__ A, const T* __restrict__ B, int r,
+                                             const T (&P2)[4], T (&br)[3][4], T (&tc)[3][6]) {
   T p1[4], p2[4], dP[4];
   cd_ld4(A, p1);
   cd_ld4(B, p2);
@@ -191,27 +207,30 @@ __device__ __forceinline__ void cd_partition(const T* __restrict__ A, const T* _
   for (int i = 0; i < 4; ++i) dP[i] = p1[i] - p2[i];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const int e1 = 3 * r + l, e2 = 3 * l + c;
-    T X[4], Y[4], T1[6], T2[6];
-    cd_ld4(A + 4 + 4 * e1, X);
-    cd_ld4(B + 4 + 4 * e2, Y);
-    cd_ld6(A + 40 + 6 * e1, T1);
-    cd_ld6(B + 40 + 6 * e2, T2);
-    const T xy = mdot(X, Y);
+    T X[4], T1[6];
+    cd_ld4(A + 4 + 4 * (3 * r + l), X);
+    cd_ld6(A + 40 + 6 * (3 * r + l), T1);
     const T px = mdot(P2, X);
-    const T py = mdot(P2, Y);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) br[i] += xy * dP[i] + px * Y[i] - py * X[i];
-    if (TENSOR) {
-      tc[0] += X[0] * Y[1] - X[1] * Y[0];
-      tc[1] += X[0] * Y[2] - X[2] * Y[0];
-      tc[2] += X[0] * Y[3] - X[3] * Y[0];
-      tc[3] += X[1] * Y[2] - X[2] * Y[1];
-      tc[4] += X[1] * Y[3] - X[3] * Y[1];
-      tc[5] += X[2] * Y[3] - X[3] * Y[2];
+    for (int c = 0; c < 3; ++c) {
+      T Y[4], T2[6];
+      cd_ld4(B + 4 + 4 * (3 * l + c), Y);
+      cd_ld6(B + 40 + 6 * (3 * l + c), T2);
+      const T xy = mdot(X, Y);
+      const T py = mdot(P2, Y);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) br[c][i] += xy * dP[i] + px * Y[i] - py * X[i];
+      if (TENSOR) {
+        tc[c][0] += X[0] * Y[1] - X[1] * Y[0];
+        tc[c][1] += X[0] * Y[2] - X[2] * Y[0];
+        tc[c][2] += X[0] * Y[3] - X[3] * Y[0];
+        tc[c][3] += X[1] * Y[2] - X[2] * Y[1];
+        tc[c][4] += X[1] * Y[3] - X[3] * Y[1];
+        tc[c][5] += X[2] * Y[3] - X[3] * Y[2];
+      }
+      ten_vec_acc(T2, X, br[c]);
+      vec_ten_acc(Y, T1, br[c]);
     }
-    ten_vec_acc(T2, X, br);
-    vec_ten_acc(Y, T1, br);
   }
 }
 
@@ -232,8 +251,8 @@ __device__ __forceinline__ T* cd_rec(T* sRec, T* gRec, int rk) {
   return rk < NSM ? sRec + (size_t)rk * REC : gRec + (size_t)(rk - NSM) * REC;
 }
 
-template <int N, typename T>
-__global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, const double* __restrict__ p,
+template <int N, typename T, int NT>
+__global__ void __launch_bounds__(NT) cd_kernel(CdParams prm, const double* __restrict__ p,
                                                                 const int8_t* __restrict__ hel,
                                                                 const int8_t* __restrict__ col,
                                                                 const uint8_t* __restrict__ accept,
@@ -242,24 +261,23 @@ __global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, con
                                                                 int* __restrict__ status) {
   using Sh = CdShape<N, T>;
   using L = CdSlab<N, T>;
-  constexpr int M = Sh::M, NS = Sh::NS, NT = Sh::NT;
+  constexpr int M = Sh::M, NS = Sh::NS;
   extern __shared__ __align__(16) unsigned char cd_smem[];
   T* const sRec = reinterpret_cast<T*>(cd_smem);
   unsigned long long* const counter = reinterpret_cast<unsigned long long*>(workspace);
   unsigned char* const slab = workspace + kCdHeader + (size_t)blockIdx.x * L::bytes;
   T* const gRec = reinterpret_cast<T*>(slab + L::off_rec);
   T* const part = reinterpret_cast<T*>(slab + L::off_part);
+  double* const top = reinterpret_cast<double*>(slab + L::off_top);
 
   __shared__ uint16_t s_list[NS];  // rank -> subset
   __shared__ uint16_t s_rank[NS];  // subset -> rank
-  __shared__ T s_inv[NS];          // inverse propagators, by rank
   __shared__ uint8_t s_nz[NS];     // record has a non-zero entry, by rank
   __shared__ int s_off[N + 1];     // first rank of each size
   __shared__ double s_k[N][4];     // scaled outgoing momenta (FP64)
   __shared__ double s_e[N][4];     // polarisations (FP64)
   __shared__ double s_E[N][3][3];  // external colour matrices
   __shared__ double s_pair[M][M];  // pair invariants 2 k_a.k_b / s (FP64)
-  __shared__ double s_red[NT / 32];
   __shared__ long long s_ev;
   __shared__ int s_skip;
 
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, con
       T* R = cd_rec<N, T>(sRec, gRec, rk);
 #pragma unroll
       for (int m = 0; m < 4; ++m) R[m] = T(P[m]);
-      s_inv[rk] = (__popc(Sx) >= 2 && Sx != NS - 1) ? T(1.0 / p2) : T(0);
+      R[Sh::OFF_INV] = (__popc(Sx) >= 2 && Sx != NS - 1) ? T(1.0 / p2) : T(0);
       if (__popc(Sx) == 1) {
         const int g = __ffs(Sx) - 1;
         bool any = false;
@@ -382,54 +400,68 @@ __global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, con
       const int nsub = s_off[Lv + 1] - s_off[Lv];
       const int nch = cd_chunks<N, T>(Lv);
       const int npart = (1 << Lv) - 2;
-      const int ntask = nsub * nch * 9;
+      const int ntask = nsub * nch * 3;
       for (int t = tid; t < ntask; t += NT) {
-        const int rc = t % 9;
-        const int u = t / 9;
+        const int r = t % 3;
+        const int u = t / 3;
         const int ch = u % nch;
         const int rkS = s_off[Lv] + u / nch;
         const int Sx = s_list[rkS];
-        const int r = rc / 3, c = rc % 3;
         T* RS = cd_rec<N, T>(sRec, gRec, rkS);
-        T P2[4], br[4] = {T(0), T(0), T(0), T(0)}, tc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        T P2[4], br[3][4], tc[3][6];
 #pragma unroll
         for (int m = 0; m < 4; ++m) P2[m] = T(2) * RS[m];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+          for (int m = 0; m < 4; ++m) br[c][m] = T(0);
+#pragma unroll
+          for (int m = 0; m < 6; ++m) tc[c][m] = T(0);
+        }
         const int j0 = 1 + (int)((long)ch * npart / nch), j1 = 1 + (int)((long)(ch + 1) * npart / nch);
         int S1 = submask_at(Sx, j0);
         for (int j = j0; j < j1; ++j) {
           const int r1 = s_rank[S1], r2 = s_rank[Sx ^ S1];
           if (s_nz[r1] & s_nz[r2])
-            cd_partition<T, true>(cd_rec<N, T>(sRec, gRec, r1), cd_rec<N, T>(sRec, gRec, r2), r, c, P2, br, tc);
+            cd_partition<T, true>(cd_rec<N, T>(sRec, gRec, r1), cd_rec<N, T>(sRec, gRec, r2), r, P2, br, tc);
           S1 = ((S1 | ~Sx) + 1) & Sx;
         }
         if (nch == 1) {
-          const T ip = s_inv[rkS];
+          const T ip = RS[Sh::OFF_INV];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) RS[Sh::OFF_J + 4 * rc + m] = br[m] * ip;
+          for (int c = 0; c < 3; ++c) {
 #pragma unroll
-          for (int m = 0; m < 6; ++m) RS[Sh::OFF_T + 6 * rc + m] = tc[m];
+            for (int m = 0; m < 4; ++m) RS[Sh::OFF_J + 4 * (3 * r + c) + m] = br[c][m] * ip;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) RS[Sh::OFF_T + 6 * (3 * r + c) + m] = tc[c][m];
+          }
         } else {
+          T* q = part + (size_t)t * 30;
 #pragma unroll
-          for (int m = 0; m < 4; ++m) part[(size_t)t * 10 + m] = br[m];
+          for (int c = 0; c < 3; ++c) {
 #pragma unroll
-          for (int m = 0; m < 6; ++m) part[(size_t)t * 10 + 4 + m] = tc[m];
+            for (int m = 0; m < 4; ++m) q[10 * c + m] = br[c][m];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) q[10 * c + 4 + m] = tc[c][m];
+          }
         }
       }
       __syncthreads();
       if (nch > 1) {
         for (int v = tid; v < nsub * 9; v += NT) {
           const int rc = v % 9, si = v / 9;
+          const int r = rc / 3, c = rc % 3;
           const int rkS = s_off[Lv] + si;
           T acc[10];
 #pragma unroll
           for (int m = 0; m < 10; ++m) acc[m] = T(0);
           for (int ch = 0; ch < nch; ++ch) {
-            const size_t t = ((size_t)si * nch + ch) * 9 + rc;
+            const size_t t = ((size_t)si * nch + ch) * 3 + r;
 #pragma unroll
-            for (int m = 0; m < 10; ++m) acc[m] += part[t * 10 + m];
+            for (int m = 0; m < 10; ++m) acc[m] += part[t * 30 + 10 * c + m];
           }
           T* RS = cd_rec<N, T>(sRec, gRec, rkS);
-          const T ip = s_inv[rkS];
+          const T ip = RS[Sh::OFF_INV];
 #pragma unroll
           for (int m = 0; m < 4; ++m) RS[Sh::OFF_J + 4 * rc + m] = acc[m] * ip;
 #pragma unroll
@@ -452,7 +484,7 @@ __global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, con
     {
       constexpr int FULL = NS - 1;
       constexpr int npart = NS - 2;
-      constexpr int nch = (2 * NT + 8) / 9 < npart ? (2 * NT + 8) / 9 : npart;
+      constexpr int nch = Sh::NCH_TOP;
       const T* RF = cd_rec<N, T>(sRec, gRec, NS - 1);
       T en[4], P2[4];
 #pragma unroll
@@ -460,70 +492,109 @@ __global__ void __launch_bounds__(CdShape<N, T>::NT) cd_kernel(CdParams prm, con
         en[m] = T(s_e[N - 1][m]);
         P2[m] = T(2) * RF[m];
       }
-      double acc = 0.0;
-      for (int t = tid; t < 9 * nch; t += NT) {
-        const int rc = t % 9, ch = t / 9;
-        const int r = rc / 3, c = rc % 3;
-        const double w = s_E[N - 1][c][r];
-        if (w == 0.0) continue;
-        const int j0 = 1 + (int)((long)ch * npart / nch), j1 = 1 + (int)((long)(ch + 1) * npart / nch);
-        T br[4] = {T(0), T(0), T(0), T(0)}, tc[6];
-        int S1 = submask_at(FULL, j0);
-        for (int j = j0; j < j1; ++j) {
-          const int r1 = s_rank[S1], r2 = s_rank[FULL ^ S1];
-          if (s_nz[r1] & s_nz[r2])
-            cd_partition<T, false>(cd_rec<N, T>(sRec, gRec, r1), cd_rec<N, T>(sRec, gRec, r2), r, c, P2, br, tc);
-          S1 = ((S1 | ~FULL) + 1) & FULL;
-        }
-        acc += w * (double)mdot(en, br);
-      }
-      // block reduction (fixed order)
+      for (int t = tid; t < 3 * nch; t += NT) {
+        const int r = t % 3, ch = t / 3;
+        const double w0 = s_E[N - 1][0][r], w1 = s_E[N - 1][1][r], w2 = s_E[N - 1][2][r];
+        double v = 0.0;
+        if (w0 != 0.0 || w1 != 0.0 || w2 != 0.0) {
+          const int j0 = 1 + (int)((long)ch * npart / nch), j1 = 1 + (int)((long)(ch + 1) * npart / nch);
+          T br[3][4], tc[3][6];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((tid & 31) == 0) s_red[tid >> 5] = acc;
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) br[c][m] = T(0);
+          int S1 = submask_at(FULL, j0);
+          for (int j = j0; j < j1; ++j) {
+            const int r1 = s_rank[S1], r2 = s_rank[FULL ^ S1];
+            if (s_nz[r1] & s_nz[r2])
+              cd_partition<T, false>(cd_rec<N, T>(sRec, gRec, r1), cd_rec<N, T>(sRec, gRec, r2), r, P2, br, tc);
+            S1 = ((S1 | ~FULL) + 1) & FULL;
+          }
+          v = w0 * (double)mdot(en, br[0]) + w1 * (double)mdot(en, br[1]) + w2 * (double)mdot(en, br[2]);
+        }
+        top[t] = v;
+      }
       __syncthreads();
-      if (tid == 0) {
+      // reduction in a fixed order (independent of the CTA size)
+      if (tid < 32) {
         double a = 0.0;
-        for (int w = 0; w < NT / 32; ++w) a += s_red[w];
-        me2[e] = prm.scale * a * a;
+        for (int t = tid; t < 3 * nch; t += 32) a += top[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (tid == 0) me2[e] = prm.scale * a * a;
       }
       __syncthreads();
     }
   }
 }
 
-template <int N, typename T>
-int cd_ctas_per_sm() {
+template <int N, typename T, int NT>
+int cd_ctas_per_sm_nt() {
   using Sh = CdShape<N, T>;
-  if (cudaFuncSetAttribute(cd_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::DYN_SMEM) !=
+  if (cudaFuncSetAttribute(cd_kernel<N, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::DYN_SMEM) !=
       cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cd_kernel<N, T>, Sh::NT, Sh::DYN_SMEM) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cd_kernel<N, T, NT>, NT, Sh::DYN_SMEM) != cudaSuccess)
     return 0;
   return nb;
 }
 
 template <int N, typename T>
+int cd_ctas_per_sm(int v) {
+  switch (v) {
+    case 0: return cd_ctas_per_sm_nt<N, T, cd_variant_threads(N, 0)>();
+    case 1: return cd_ctas_per_sm_nt<N, T, cd_variant_threads(N, 1)>();
+    case 2:
+      if constexpr (N >= 10) return cd_ctas_per_sm_nt<N, T, cd_variant_threads(N, 2)>();
+      return 0;
+    default: return 0;
+  }
+}
+
+// Workspace for any variant: header + one slab per CTA of the largest grid.
+template <int N, typename T>
 size_t cd_workspace_bytes_n(int sms) {
-  const int nb = cd_ctas_per_sm<N, T>();
-  if (nb <= 0) return 0;
+  int nb = 0;
+  for (int v = 0; v < cd_num_variants(N); ++v) {
+    const int b = cd_ctas_per_sm<N, T>(v);
+    if (b <= 0) return 0;
+    nb = b > nb ? b : nb;
+  }
   return kCdHeader + (size_t)sms * nb * CdSlab<N, T>::bytes;
 }
 
-template <int N, typename T>
-cudaError_t launch_cd_n(const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                        const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
-  const int nb = cd_ctas_per_sm<N, T>();
+template <int N, typename T, int NT>
+cudaError_t launch_cd_nt(const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
+                         const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
+  const int nb = cd_ctas_per_sm_nt<N, T, NT>();
   if (nb <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)sms * nb;
   if (grid > prm.B) grid = prm.B;
   // the event counter starts at zero for every launch
   cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  cd_kernel<N, T><<<(unsigned)grid, CdShape<N, T>::NT, CdShape<N, T>::DYN_SMEM, s>>>(
+  cd_kernel<N, T, NT><<<(unsigned)grid, NT, CdShape<N, T>::DYN_SMEM, s>>>(
       prm, p, hel, col, accept, me2, static_cast<unsigned char*>(workspace), status);
   return cudaGetLastError();
+}
+
+template <int N, typename T>
+cudaError_t launch_cd_n(const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
+                        const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s,
+                        int variant) {
+  if (variant < 0 || variant >= cd_num_variants(N)) variant = cd_default_variant(N);
+  switch (variant) {
+    case 0:
+      return launch_cd_nt<N, T, cd_variant_threads(N, 0)>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    case 1:
+      return launch_cd_nt<N, T, cd_variant_threads(N, 1)>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    default:
+      if constexpr (N >= 10)
+        return launch_cd_nt<N, T, cd_variant_threads(N, 2)>(prm, p, hel, col, accept, me2, workspace, status, sms,
+                                                             s);
+      return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>
@@ -544,17 +615,18 @@ size_t cd_workspace_bytes_t(int n, int sms) {
 
 template <typename T>
 cudaError_t launch_cd_t(int n, const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                        const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
+                        const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s,
+                        int variant) {
   switch (n) {
-    case 4: return launch_cd_n<4, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 5: return launch_cd_n<5, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 6: return launch_cd_n<6, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 7: return launch_cd_n<7, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 8: return launch_cd_n<8, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 9: return launch_cd_n<9, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 10: return launch_cd_n<10, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 11: return launch_cd_n<11, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 12: return launch_cd_n<12, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    case 4: return launch_cd_n<4, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 5: return launch_cd_n<5, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 6: return launch_cd_n<6, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 7: return launch_cd_n<7, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 8: return launch_cd_n<8, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 9: return launch_cd_n<9, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 10: return launch_cd_n<10, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 11: return launch_cd_n<11, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
+    case 12: return launch_cd_n<12, T>(prm, p, hel, col, accept, me2, workspace, status, sms, s, variant);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -568,15 +568,21 @@ cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_
   return cudaGetLastError();
 }
 
+// Variants (sampled helicities, n >= 6): 0 = one thread per ordering,
+// 1 = depth-first groups of six orderings (default).  The helicity sum and
+// n < 6 have one variant.
+inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 2 : 1; }
+
 template <typename T>
 cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
-                        T* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr) {
+                        T* amps, int* status, cudaStream_t s, const int64_t* dB, int variant) {
   const bool sum = (hel == nullptr);
-#define BG_CO_CASE(NN)                                                                    \
-  case NN:                                                                                \
-    return sum ? launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB)     \
-               : (NN >= 6 ? launch_co_dfs<(NN >= 6 ? NN : 6), T>(B, sqrt_s, p, hel, q, amps, status, s, dB) \
-                          : launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB));
+  const bool dfs = !sum && n >= 6 && variant != 0;
+#define BG_CO_CASE(NN)                                                                                    \
+  case NN:                                                                                                \
+    return sum ? launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB)                     \
+               : (dfs ? launch_co_dfs<(NN >= 6 ? NN : 6), T>(B, sqrt_s, p, hel, q, amps, status, s, dB) \
+                      : launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB));
   switch (n) {
     BG_CO_CASE(4)
     BG_CO_CASE(5)

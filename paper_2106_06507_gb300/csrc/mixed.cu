@@ -344,6 +344,17 @@ bg_status bg_mixed_create(const bg_mixed_desc* d, bg_mixed** out) {
     }
   }
 #undef MX_ALLOC
+  if (d->autotune) {
+    for (int n = d->n_min; n <= d->n_max; ++n) {
+      const bg_algo algo = n <= d->n_co_max ? BG_ALGO_CO : BG_ALGO_CD;
+      if (bg_tune_num_variants(algo, n) < 2) continue;
+      st = bg_autotune(algo, n, d->prec, 0, nullptr, nullptr, nullptr);
+      if (st != BG_OK) {
+        bg_mixed_destroy(P);
+        return st;
+      }
+    }
+  }
   st = cuda_check(cudaMemcpy(P->dcap, P->cap, sizeof(P->cap), cudaMemcpyHostToDevice), "bg_mixed_create: upload");
   if (st != BG_OK) {
     bg_mixed_destroy(P);

@@ -83,3 +83,14 @@ def test_argument_errors_without_gpu(libbg):
     assert libbg.bg_momenta_rambo(5, 10, 1000.0, None, None, 0.0, None, None) == 1
     row = np.zeros(10)
     assert libbg.bg_colormat_row_host(10, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
+
+
+def test_tune_variant_counts_without_gpu(libbg):
+    # colour-ordered: sampled-helicity variants exist from n = 6; colour-
+    # dressed: two CTA sizes up to n = 9, three above; out of range: 0
+    CO, CD = 0, 1
+    assert [libbg.bg_tune_num_variants(CO, n) for n in range(4, 10)] == [1, 1, 2, 2, 2, 2]
+    assert [libbg.bg_tune_num_variants(CD, n) for n in range(4, 13)] == [2] * 6 + [3] * 3
+    assert libbg.bg_tune_num_variants(CO, 10) == 0
+    assert libbg.bg_tune_num_variants(CD, 3) == 0
+    assert libbg.bg_tune_num_variants(7, 6) == 0
