@@ -10,6 +10,18 @@ accumulation.  Metric: events/s (all generated events of all four
 multiplicities; per-n figures are in "per_n").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload co|cd|grad|mixed]
+
+The default workload (co) is the one above.  The others measure the other
+parts of the path with the same timing rules:
+  cd     colour-dressed recursion with sampled adjoint colours, n = 8, 10, 12,
+         2^20 events per n, FP32 currents, pT > 20 GeV;
+  grad   |M|^2 and d|M|^2/du (colour-ordered, FP32, full colour sum), n = 6
+         and 8, 2^18 events per n;
+  mixed  10^7 events with n uniform in 4..12 in one CUDA-graph launch: tensor-
+         core colour sum for n = 6..9 (FP32 CUDA cores for n = 4, 5),
+         colour-dressed recursion with sampled adjoint colours for n = 10..12,
+         FP32 currents, pT > 20 GeV, autotuned kernel variants.
 
 Prints ONE JSON line on rank 0.  N > 1 runs under torch.distributed.run, one
 process per GPU, each with its own events (weak scaling, no collective on the
@@ -48,11 +60,11 @@ WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqr
 # DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
 # n = 8, 2^20 events, scaled from a 2^16-event capture by the number of
 # events), valid only for the kernel sources it was taken from.
-NCU_TRAFFIC = {"sources_sha1": "c98db25cb47d095815fb005026892cd207c32c9e",
-               "bytes_per_launch": 16 * (17393408 + 127698432)}  # 2^16-event capture x 16
+NCU_TRAFFIC = {"sources_sha1": "31b7684facfe330d180fba98f64c843b05d7f7c4",
+               "bytes_per_launch": 16 * (17590784 + 127849216)}  # 2^16-event capture x 16
 # Executed FP32 operations per event of the dominant kernel at n = 8 (ncu sass
 # counts of the same capture: 2 x FFMA + FADD + FMUL), valid for the same sources.
-NCU_EXECUTED = {"sources_sha1": "c98db25cb47d095815fb005026892cd207c32c9e", "flops_per_event": 2524568}
+NCU_EXECUTED = {"sources_sha1": "31b7684facfe330d180fba98f64c843b05d7f7c4", "flops_per_event": 2524560}
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
 
@@ -397,7 +409,7 @@ def run_ours(args) -> None:
             "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS},
             "kernel_ms_per_step": {f"n{n}": [round(x / args.steps, 4) for x in kernel_ms[n]] for n in NS},
             "kernel_share": {k: round(v, 4) for k, v in shares.items()},
-            "roofline": {"kernel": f"co_kernel<{n_dom},float> (colour-ordered recursion)", "bound": "alu",
+            "roofline": {"kernel": f"co_kernel_dfs<{n_dom},float> (colour-ordered recursion)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "flops_per_launch": flops, "flops_model": "canonical (V3=65, V4=46, prop=12, final=7)",
@@ -419,9 +431,314 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def timed_steps(step, args, dev, stream) -> tuple[float, dict]:
+    """W untimed steps, then K steps between CUDA events on `stream` with a
+    barrier and a synchronisation on both sides; returns (seconds, max over
+    ranks) and the clock record of the timed region."""
+    import torch
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", "")) or str(dev.index)
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier()
+    return max_over_ranks(t0.elapsed_time(t1) * 1e-3, dev), clk
+
+
+def timed_host(step, args, dev) -> float:
+    """Wall-clock seconds of K steps that include host<->device copies."""
+    import torch
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    return max_over_ranks(time.perf_counter() - w0, dev)
+
+
+def cd_dense_flops(n: int) -> int:
+    """FLOPs per event of the colour-dressed recursion as implemented: every
+    ordered partition (S1, S2) of every subset takes the dense 3x3x3 colour
+    products; per (r, l, c) 56 FMA (X.Y, P.Y, the V3 update, the tensor
+    product and both tensor contractions), per (r, l) 4 FMA (P.X); the top
+    level skips the tensor product (44 FMA)."""
+    m = n - 1
+    inner = sum(math.comb(m, L) * (2 ** L - 2) for L in range(2, m))
+    top = 2 ** m - 2
+    return 2 * (inner * 9 * (4 + 3 * 56) + top * 9 * (4 + 3 * 44))
+
+
+def setup_gpu():
+    import torch
+    import torch.distributed as dist
+    world, rank, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2106_06507_gb300 import bg, build_lib
+    build_lib.build()
+    bg.lib()
+    return world, rank, dev, bg
+
+
+def finish_gpu(world):
+    import torch.distributed as dist
+    if world > 1 and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+CD_NS = (8, 10, 12)
+
+
+def run_cd(args) -> None:
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    first = rank * BATCH
+    U, HEL, COL, P, ACC, ME2 = {}, {}, {}, {}, {}, {}
+    host = {}
+    for n in CD_NS:
+        u = inputs.rambo_uniforms(n, BATCH, seed=SEED, first_event=first)
+        h = np.ascontiguousarray(inputs.helicities(n, BATCH, seed=SEED, first_event=first).T)
+        c = np.ascontiguousarray(inputs.adjoint_colours(n, BATCH, seed=SEED, first_event=first).T)
+        U[n], HEL[n], COL[n] = (torch.from_numpy(x).to(dev) for x in (u, h, c))
+        host[n] = tuple(torch.from_numpy(x).pin_memory() for x in (u, h, c))
+        P[n] = torch.empty((4, n, BATCH), dtype=torch.float64, device=dev)
+        ACC[n] = torch.empty((BATCH,), dtype=torch.uint8, device=dev)
+        ME2[n] = torch.empty((BATCH,), dtype=torch.float64, device=dev)
+    ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for n in CD_NS}
+    kernel_ms = {n: [0.0, 0.0] for n in CD_NS}
+
+    def step(record=False):
+        for n in CD_NS:
+            if record:
+                ev[n][0].record(stream)
+            bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            if record:
+                ev[n][1].record(stream)
+            bg.currents_cd(n, P[n], HEL[n], COL[n], prec=bg.BG_F32, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
+                           stream=stream)
+            if record:
+                ev[n][2].record(stream)
+
+    elapsed, clk = timed_steps(step, args, dev, stream)
+    value = world * len(CD_NS) * BATCH * args.steps / elapsed
+    for _ in range(args.steps):  # per-kernel times (separate pass)
+        step(True)
+        torch.cuda.synchronize(dev)
+        for n in CD_NS:
+            for j in range(2):
+                kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1]) / args.steps
+    ref = {n: ME2[n].cpu() for n in CD_NS}
+    out_h = {n: torch.empty((BATCH,), dtype=torch.float64).pin_memory() for n in CD_NS}
+    d_in = {n: tuple(torch.empty_like(x, device=dev) for x in host[n]) for n in CD_NS}
+
+    def e2e_step():
+        for n in CD_NS:
+            for dst, src in zip(d_in[n], host[n]):
+                dst.copy_(src, non_blocking=True)
+            bg.momenta_rambo(n, d_in[n][0], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            bg.currents_cd(n, P[n], d_in[n][1], d_in[n][2], prec=bg.BG_F32, sqrt_s=SQRT_S, accept=ACC[n],
+                           me2=ME2[n], stream=stream)
+            out_h[n].copy_(ME2[n], non_blocking=True)
+
+    e2e_s = timed_host(e2e_step, args, dev)
+    for n in CD_NS:
+        if not torch.equal(out_h[n], ref[n]):
+            raise RuntimeError(f"e2e colour-dressed |M|^2 differs from the device-resident run at n={n}")
+    h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in CD_NS)
+    n_dom = max(CD_NS, key=lambda n: kernel_ms[n][1])
+    accepted = int(ACC[n_dom].sum().item())  # events failing the cut are skipped by the kernel
+    flops = cd_dense_flops(n_dom) * accepted
+    achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("colour-dressed BG with sampled adjoint colours (1..8), n=8,10,12, 2^20 Rambo "
+                                    "points per n at sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, FP32 currents"),
+                       "n": list(CD_NS), "batch_per_n": BATCH, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2"},
+            "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) * 1e-3) for n in CD_NS},
+            "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in CD_NS},
+            "roofline": {"kernel": f"cd_kernel<{n_dom},float>", "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_model": "dense 3x3x3 colour products per ordered partition (56 FMA per "
+                                        "(r,l,c), 4 per (r,l)) x events passing the cut",
+                         "flops_per_event": cd_dense_flops(n_dom), "events_computed": accepted,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
+            "e2e": {"value": world * len(CD_NS) * BATCH * args.steps / e2e_s, "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(CD_NS) * BATCH * 8},
+            "gpu_launches": 2 * len(CD_NS) * args.steps, "clocks": clk}), flush=True)
+    finish_gpu(world)
+
+
+GRAD_NS = (6, 8)
+GRAD_BATCH = 1 << 18
+
+
+def run_grad(args) -> None:
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    first = rank * GRAD_BATCH
+    plans, U, HEL, G, M = {}, {}, {}, {}, {}
+    host = {}
+    for n in GRAD_NS:
+        u = inputs.rambo_uniforms(n, GRAD_BATCH, seed=SEED, first_event=first)
+        h = np.ascontiguousarray(inputs.helicities(n, GRAD_BATCH, seed=SEED, first_event=first).T)
+        U[n], HEL[n] = torch.from_numpy(u).to(dev), torch.from_numpy(h).to(dev)
+        host[n] = (torch.from_numpy(u).pin_memory(), torch.from_numpy(h).pin_memory())
+        G[n] = torch.empty_like(U[n])
+        M[n] = torch.empty((GRAD_BATCH,), dtype=torch.float64, device=dev)
+        plans[n] = bg.Plan(n, GRAD_BATCH, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_F32, hel_sampled=True,
+                           grad=True)
+
+    def step():
+        for n in GRAD_NS:
+            plans[n].grad(U[n], HEL[n], me2=M[n], out=G[n], stream=stream)
+
+    elapsed, clk = timed_steps(step, args, dev, stream)
+    value = world * len(GRAD_NS) * GRAD_BATCH * args.steps / elapsed
+    per_n = {}
+    for n in GRAD_NS:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plans[n].grad(U[n], HEL[n], me2=M[n], out=G[n], stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        per_n[str(n)] = GRAD_BATCH * world / (a.elapsed_time(b) * 1e-3)
+    ref = {n: G[n].cpu() for n in GRAD_NS}
+    d_in = {n: (torch.empty_like(U[n]), torch.empty_like(HEL[n])) for n in GRAD_NS}
+    out_h = {n: (torch.empty((GRAD_BATCH, 4 * (n - 2)), dtype=torch.float64).pin_memory(),
+                 torch.empty((GRAD_BATCH,), dtype=torch.float64).pin_memory()) for n in GRAD_NS}
+
+    def e2e_step():
+        for n in GRAD_NS:
+            d_in[n][0].copy_(host[n][0], non_blocking=True)
+            d_in[n][1].copy_(host[n][1], non_blocking=True)
+            plans[n].grad(d_in[n][0], d_in[n][1], me2=M[n], out=G[n], stream=stream)
+            out_h[n][0].copy_(G[n], non_blocking=True)
+            out_h[n][1].copy_(M[n], non_blocking=True)
+
+    e2e_s = timed_host(e2e_step, args, dev)
+    for n in GRAD_NS:
+        # |M|^2 is deterministic; the sums over orderings of the gradient use
+        # shared-memory atomics, so repeated calls agree to the FP32 rounding
+        # of the gradient (whose cancellations among (n-2)! orderings make it
+        # ~1e-4 relative in the median), not bit for bit
+        if not torch.equal(out_h[n][1], M[n].cpu()):
+            raise RuntimeError(f"e2e |M|^2 differs from the device-resident run at n={n}")
+        rel = (out_h[n][0] - ref[n]).norm(dim=1) / ref[n].norm(dim=1).clamp_min(1e-300)
+        if float(rel.median()) > 1e-4:
+            raise RuntimeError(f"e2e gradient differs from the device-resident run at n={n}")
+    h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in GRAD_NS)
+    d2h = sum(sum(x.numel() * x.element_size() for x in out_h[n]) for n in GRAD_NS)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("|M|^2 and d|M|^2/du (4(n-2) Rambo uniforms), colour-ordered FP32 with full "
+                                    "colour sum, n=6,8, 2^18 events per n, pT>20 GeV, sampled helicities"),
+                       "n": list(GRAD_NS), "batch_per_n": GRAD_BATCH, "parallelism": f"replicas x{world}"},
+            "per_n": per_n, "roofline": None,
+            "e2e": {"value": world * len(GRAD_NS) * GRAD_BATCH * args.steps / e2e_s, "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 5 * len(GRAD_NS) * args.steps, "clocks": clk}), flush=True)
+    for n in GRAD_NS:
+        plans[n].close()
+    finish_gpu(world)
+
+
+MIXED_EVENTS = 10_000_000
+
+
+def run_mixed(args) -> None:
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    B = MIXED_EVENTS
+    ev = inputs.mixed_events(B, 4, 12, seed=SEED + rank, colours="adjoint")
+    mx = bg.Mixed(4, 12, B, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_TC_BF16,
+                  color_mode=bg.BG_COL_ADJOINT, n_co_max=9, autotune=True)
+    host = (torch.from_numpy(ev["nev"]).pin_memory(), torch.from_numpy(ev["u"]).pin_memory(),
+            torch.from_numpy(np.ascontiguousarray(ev["hel"].T)).pin_memory(),
+            torch.from_numpy(np.ascontiguousarray(ev["colors"].T)).pin_memory())
+    dst = (mx.n_per_event, mx.u, mx.hel, mx.colors)
+    for d, h in zip(dst, host):
+        d.copy_(h)
+    torch.cuda.synchronize(dev)
+
+    def step():
+        mx.run(B, stream=stream)
+
+    elapsed, clk = timed_steps(step, args, dev, stream)
+    value = world * B * args.steps / elapsed
+    ref = mx.me2.cpu()
+    counts = mx.counts()
+    out_h = torch.empty((B,), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        for d, h in zip(dst, host):
+            d.copy_(h, non_blocking=True)
+        mx.run(B, stream=stream)
+        out_h.copy_(mx.me2, non_blocking=True)
+
+    e2e_s = timed_host(e2e_step, args, dev)
+    if not torch.equal(out_h, ref):
+        raise RuntimeError("e2e mixed |M|^2 differs from the device-resident run")
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    tuned = {str(n): bg.tune_get(bg.BG_ALGO_CO if n <= 9 else bg.BG_ALGO_CD, n, bg.BG_F32) for n in range(6, 13)}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("mixed batch, 10^7 events with n uniform in 4..12 in one CUDA-graph launch: "
+                                    "colour-ordered + tensor-core colour sum for n=6..9 (FP32 CUDA cores n=4,5), "
+                                    "colour-dressed with sampled adjoint colours for n=10..12, FP32 currents, "
+                                    "FP64 Rambo and accumulation, pT>20 GeV, autotuned kernel variants"),
+                       "events": B, "counts_per_n": counts[4:], "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2", "tuned_variants": tuned,
+                       "workspace_gb": mx.workspace_bytes / 1e9},
+            "roofline": None,
+            "e2e": {"value": world * B * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": B * 8},
+            "gpu_launches": None, "graph_launches": args.steps, "clocks": clk}), flush=True)
+    mx.close()
+    finish_gpu(world)
+
+
 def run_profile_case(args) -> None:
     """A small case of one multiplicity for ncu captures: `warmup` steps, then
-    one step (Rambo, recursion, colour sum), on cuda:0."""
+    one step (Rambo, recursion, colour sum; with --workload cd: Rambo once,
+    then the colour-dressed recursion), on cuda:0."""
     import numpy as np
     import torch
 
@@ -429,6 +746,17 @@ def run_profile_case(args) -> None:
     build_lib.build()
     n, B = args.profile_n, args.profile_batch
     dev = torch.device("cuda", 0)
+    if args.workload == "cd":
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
+        c = torch.from_numpy(np.ascontiguousarray(inputs.adjoint_colours(n, B, seed=SEED).T)).to(dev)
+        p, acc = bg.momenta_rambo(n, u, SQRT_S, PT_MIN)
+        for _ in range(args.warmup + 1):
+            me2 = bg.currents_cd(n, p, h, c, prec=bg.BG_F32, sqrt_s=SQRT_S, accept=acc)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_case": {"workload": "cd", "n": n, "batch": B,
+                                           "sum_me2": float(me2.sum().item())}}), flush=True)
+        return
     u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
     h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
     C = bg.ColourMatrix(n)
@@ -452,6 +780,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed"), default="co")
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling case: run only multiplicity n (warm-up steps, then one step)")
     ap.add_argument("--profile-batch", type=int, default=1 << 16)
@@ -460,6 +789,12 @@ def main(argv=None):
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cd":
+        run_cd(args)
+    elif args.workload == "grad":
+        run_grad(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 
