@@ -248,8 +248,8 @@ bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, d
  *   me2       [B] double DEVICE output, or NULL
  *   grad_u    [B][4(n-2)] double DEVICE output: upstream * d|M|^2/du
  * Events failing the cut get |M|^2 = 0 and a zero gradient (the cut is a
- * step function).  The sums over orderings use shared-memory atomics:
- * repeated calls agree to rounding of the recursion's type, not bit for bit.
+ * step function).  The sums over orderings are taken in a fixed order:
+ * repeated calls give bitwise identical results.
  * Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
  * ------------------------------------------------------------------------- */
 bg_status bg_me2_grad(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const double* upstream,
@@ -363,9 +363,10 @@ bg_status bg_mixed_counts(bg_mixed* plan, int64_t* counts);
  *   BG_ALGO_CO (sampled helicities, n >= 6): 0 = one thread per ordering,
  *     1 = depth-first groups of six orderings sharing prefix currents
  *     (default); helicity sums and n < 6 have one variant;
- *   BG_ALGO_CD: threads per event (CTA size): n <= 9: 0 = 128, 1 = 256;
- *     n >= 10: 0 = 256, 1 = 384, 2 = 512 (defaults 128 for n <= 8, 256 for
- *     n = 9, 512 for n >= 10).
+ *   BG_ALGO_CD: (threads per event, unrolling of the partition loop):
+ *     n <= 9: 0 = (128, 1), 1 = (256, 1), 2 = (128, 2), 3 = (256, 2);
+ *     n >= 10: 0 = (256, 1), 1 = (384, 1), 2 = (512, 1), 3 = (256, 2),
+ *     4 = (384, 2); defaults 0 for n <= 8, 1 for n = 9, 2 for n >= 10.
  * bg_autotune times every variant of (algo, n, prec) on a synthetic probe
  * batch of probe_batch events (<= 0: a size chosen by n) on `stream`, stores
  * the fastest in a process-wide table for the current device and returns it

@@ -100,14 +100,21 @@ __host__ __device__ constexpr int cd_binom(int n, int k) {
   return c;
 }
 
-// Threads per CTA (one event per CTA) of the kernel variants, and the
-// default variant.  The task decomposition below depends on N only, so all
-// variants compute every sum in the same order: bitwise identical results.
-__host__ __device__ constexpr int cd_num_variants(int N) { return N <= 9 ? 2 : 3; }
+// Kernel variants: threads per CTA (one event per CTA) and the unrolling of
+// the loop over partitions.  The task decomposition below depends on N only,
+// so all variants compute every sum in the same order: bitwise identical
+// results.
+//   N <= 9:  0 = (128, 1), 1 = (256, 1), 2 = (128, 2), 3 = (256, 2)
+//   N >= 10: 0 = (256, 1), 1 = (384, 1), 2 = (512, 1), 3 = (256, 2), 4 = (384, 2)
+__host__ __device__ constexpr int cd_num_variants(int N) { return N <= 9 ? 4 : 5; }
 __host__ __device__ constexpr int cd_variant_threads(int N, int v) {
-  return N <= 9 ? (v == 0 ? 128 : 256) : (v == 0 ? 256 : v == 1 ? 384 : 512);
+  return N <= 9 ? ((v & 1) ? 256 : 128) : ((v == 0 || v == 3) ? 256 : (v == 1 || v == 4) ? 384 : 512);
 }
+__host__ __device__ constexpr int cd_variant_unroll(int N, int v) { return (v >= (N <= 9 ? 2 : 3)) ? 2 : 1; }
 __host__ __device__ constexpr int cd_default_variant(int N) { return N <= 8 ? 0 : N == 9 ? 1 : 2; }
+// Resident CTAs per SM the register allocation aims at: one for n >= 10
+// (shared memory admits one), several for the small tables of n <= 9.
+__host__ __device__ constexpr int cd_min_blocks(int N, int NT) { return N >= 10 ? 1 : 0 * NT; }
 
 template <int N, typename T>
 struct CdShape {
@@ -251,8 +258,8 @@ __device__ __forceinline__ T* cd_rec(T* sRec, T* gRec, int rk) {
   return rk < NSM ? sRec + (size_t)rk * REC : gRec + (size_t)(rk - NSM) * REC;
 }
 
-template <int N, typename T, int NT>
-__global__ void __launch_bounds__(NT) cd_kernel(CdParams prm, const double* __restrict__ p,
+template <int N, typename T, int NT, int UR>
+__global__ void __launch_bounds__(NT, cd_min_blocks(N, NT)) cd_kernel(CdParams prm, const double* __restrict__ p,
                                                                 const int8_t* __restrict__ hel,
                                                                 const int8_t* __restrict__ col,
                                                                 const uint8_t* __restrict__ accept,
@@ -420,6 +427,7 @@ __global__ void __launch_bounds__(NT) cd_kernel(CdParams prm, const double* __re
         }
         const int j0 = 1 + (int)((long)ch * npart / nch), j1 = 1 + (int)((long)(ch + 1) * npart / nch);
         int S1 = submask_at(Sx, j0);
+#pragma unroll UR
         for (int j = j0; j < j1; ++j) {
           const int r1 = s_rank[S1], r2 = s_rank[Sx ^ S1];
           if (s_nz[r1] & s_nz[r2])
@@ -504,6 +512,7 @@ __global__ void __launch_bounds__(NT) cd_kernel(CdParams prm, const double* __re
 #pragma unroll
             for (int m = 0; m < 4; ++m) br[c][m] = T(0);
           int S1 = submask_at(FULL, j0);
+#pragma unroll UR
           for (int j = j0; j < j1; ++j) {
             const int r1 = s_rank[S1], r2 = s_rank[FULL ^ S1];
             if (s_nz[r1] & s_nz[r2])
@@ -528,14 +537,15 @@ __global__ void __launch_bounds__(NT) cd_kernel(CdParams prm, const double* __re
   }
 }
 
-template <int N, typename T, int NT>
-int cd_ctas_per_sm_nt() {
+template <int N, typename T, int V>
+int cd_ctas_per_sm_v() {
   using Sh = CdShape<N, T>;
-  if (cudaFuncSetAttribute(cd_kernel<N, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::DYN_SMEM) !=
-      cudaSuccess)
+  constexpr int NT = cd_variant_threads(N, V), UR = cd_variant_unroll(N, V);
+  if (cudaFuncSetAttribute(cd_kernel<N, T, NT, UR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Sh::DYN_SMEM) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cd_kernel<N, T, NT>, NT, Sh::DYN_SMEM) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cd_kernel<N, T, NT, UR>, NT, Sh::DYN_SMEM) != cudaSuccess)
     return 0;
   return nb;
 }
@@ -543,10 +553,12 @@ int cd_ctas_per_sm_nt() {
 template <int N, typename T>
 int cd_ctas_per_sm(int v) {
   switch (v) {
-    case 0: return cd_ctas_per_sm_nt<N, T, cd_variant_threads(N, 0)>();
-    case 1: return cd_ctas_per_sm_nt<N, T, cd_variant_threads(N, 1)>();
-    case 2:
-      if constexpr (N >= 10) return cd_ctas_per_sm_nt<N, T, cd_variant_threads(N, 2)>();
+    case 0: return cd_ctas_per_sm_v<N, T, 0>();
+    case 1: return cd_ctas_per_sm_v<N, T, 1>();
+    case 2: return cd_ctas_per_sm_v<N, T, 2>();
+    case 3: return cd_ctas_per_sm_v<N, T, 3>();
+    case 4:
+      if constexpr (cd_num_variants(N) > 4) return cd_ctas_per_sm_v<N, T, 4>();
       return 0;
     default: return 0;
   }
@@ -564,17 +576,18 @@ size_t cd_workspace_bytes_n(int sms) {
   return kCdHeader + (size_t)sms * nb * CdSlab<N, T>::bytes;
 }
 
-template <int N, typename T, int NT>
-cudaError_t launch_cd_nt(const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                         const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
-  const int nb = cd_ctas_per_sm_nt<N, T, NT>();
+template <int N, typename T, int V>
+cudaError_t launch_cd_v(const CdParams& prm, const double* p, const int8_t* hel, const int8_t* col,
+                        const uint8_t* accept, double* me2, void* workspace, int* status, int sms, cudaStream_t s) {
+  constexpr int NT = cd_variant_threads(N, V), UR = cd_variant_unroll(N, V);
+  const int nb = cd_ctas_per_sm_v<N, T, V>();
   if (nb <= 0) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)sms * nb;
   if (grid > prm.B) grid = prm.B;
   // the event counter starts at zero for every launch
   cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  cd_kernel<N, T, NT><<<(unsigned)grid, NT, CdShape<N, T>::DYN_SMEM, s>>>(
+  cd_kernel<N, T, NT, UR><<<(unsigned)grid, NT, CdShape<N, T>::DYN_SMEM, s>>>(
       prm, p, hel, col, accept, me2, static_cast<unsigned char*>(workspace), status);
   return cudaGetLastError();
 }
@@ -585,14 +598,13 @@ cudaError_t launch_cd_n(const CdParams& prm, const double* p, const int8_t* hel,
                         int variant) {
   if (variant < 0 || variant >= cd_num_variants(N)) variant = cd_default_variant(N);
   switch (variant) {
-    case 0:
-      return launch_cd_nt<N, T, cd_variant_threads(N, 0)>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
-    case 1:
-      return launch_cd_nt<N, T, cd_variant_threads(N, 1)>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    case 0: return launch_cd_v<N, T, 0>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    case 1: return launch_cd_v<N, T, 1>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    case 2: return launch_cd_v<N, T, 2>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
+    case 3: return launch_cd_v<N, T, 3>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
     default:
-      if constexpr (N >= 10)
-        return launch_cd_nt<N, T, cd_variant_threads(N, 2)>(prm, p, hel, col, accept, me2, workspace, status, sms,
-                                                             s);
+      if constexpr (cd_num_variants(N) > 4)
+        return launch_cd_v<N, T, 4>(prm, p, hel, col, accept, me2, workspace, status, sms, s);
       return cudaErrorInvalidValue;
   }
 }

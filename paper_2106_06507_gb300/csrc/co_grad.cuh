@@ -2,19 +2,24 @@
 // the gradient of |M|^2 = scale * A^T C A (Eq. 2.16) with respect to the
 // momenta and polarisation vectors of the gluons.
 //
-// One thread per (event, ordering).  Each thread owns slots in shared
-// memory (thread index fastest, so accesses are bank-conflict free) for the
-// currents J(i..j) of its ordering, their adjoints, the prefix sums S_p of
-// the ordered momenta and their adjoints.  The forward sweep recomputes the
-// currents (same arithmetic as co_recursion.cuh); the reverse sweep walks the
-// segments from the longest to the shortest.  The adjoint of the amplitude
-// with unit vertex factors is dA = 2 vfac (C A)_sigma, vfac = (1/sqrt2)^(n-2).
-// For every segment the adjoint of its bracket is pushed to the sub-currents
-// it was built from (V3 and V4 terms), to the prefix sums (V3 momentum terms
-// and the propagator 1/P^2), and, for single-gluon segments, to the
-// polarisation vectors.  The per-event adjoints of the momenta and
-// polarisations are summed over the orderings (warp reductions and shared
-// atomics) and written in FP64 as [B][n][4].
+// One thread per (event, ordering).  As in the forward kernel the whole
+// recursion is unrolled at compile time for each n and lives in registers:
+// the forward sweep computes the currents J(i..j) (same arithmetic as
+// co_recursion.cuh), the reverse sweep walks the segments from the longest
+// to the shortest with the adjoints Jbar(i..j) of the currents and Sbar_p of
+// the prefix sums of the ordered momenta, also in registers.  The adjoint of
+// the amplitude with unit vertex factors is dA = 2 vfac (C A)_sigma,
+// vfac = (1/sqrt2)^(n-2).  For every segment the adjoint of its bracket is
+// pushed to the sub-currents it was built from (V3 and V4 terms), to the
+// prefix sums (V3 momentum terms and the propagator 1/P^2), and, for
+// single-gluon segments, to the polarisation vectors.
+//
+// Sums over the orderings of an event, in a fixed order (deterministic):
+// the tasks of an event are padded to whole warps; each thread stores its
+// per-gluon adjoints in shared memory (thread index fastest) at the slot of
+// the gluon it holds at each position, each warp reduces them with shuffles,
+// and the warp partials are added in warp order at the end.  Output: FP64
+// [B][n][4] adjoints of the scaled momenta and of the polarisation vectors.
 #pragma once
 
 #include "co_recursion.cuh"
@@ -23,257 +28,185 @@ namespace bg {
 
 template <int N, typename T>
 struct GradShape {
-  static constexpr int NT = sizeof(T) == 4 ? 128 : 64;
+  static constexpr int NT = 128;
   static constexpr int M = N - 1;
   static constexpr int K = ct_fact(N - 2);
-  static constexpr int EB0 = NT / ct_gcd(NT, K);
-  static constexpr int EB = EB0 > 64 ? 64 : EB0;
-  static constexpr int NSEG = M * (M + 1) / 2;
+  static constexpr int KP = (K + 31) / 32 * 32;   // tasks per event, whole warps
+  static constexpr int WPE = KP / 32;             // warps per event
+  static constexpr int EB = NT / ct_gcd(NT, KP);  // events per block: EB * KP % NT == 0
   static constexpr int NMASK = 1 << M;
   static constexpr int NPAIR = M * (M - 1) / 2;
-  // per-thread slots: J, Jbar (NSEG x 4), S, Sbar (N x 4), scratch (5 x M)
-  static constexpr int SLOTS = 2 * NSEG * 4 + 2 * N * 4 + 5 * M;
+  static constexpr int NVAL = 2 * N * 4;          // adjoint values per ordering
 };
 
 template <int N, typename T>
 struct GradSmem {
   using S = GradShape<N, T>;
-  static constexpr size_t off_pair = 0;                                              // double [EB][NPAIR]
-  static constexpr size_t off_inv = off_pair + sizeof(double) * S::EB * S::NPAIR;    // T [EB][NMASK]
-  static constexpr size_t off_k = off_inv + sizeof(T) * S::EB * S::NMASK;            // T [EB][N][4]
-  static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                 // T [EB][N][4]
-  static constexpr size_t off_acc = off_e + sizeof(T) * S::EB * N * 4;               // T [EB][2][N][4]
-  static constexpr size_t off_slot = off_acc + sizeof(T) * S::EB * 2 * N * 4;        // T [SLOTS][NT]
-  static constexpr size_t off_ord = off_slot + sizeof(T) * S::SLOTS * S::NT;         // int [K]
+  static constexpr size_t off_pair = 0;                                               // double [EB][NPAIR]
+  static constexpr size_t off_inv = off_pair + sizeof(double) * S::EB * S::NPAIR;     // T [EB][NMASK]
+  static constexpr size_t off_k = off_inv + sizeof(T) * S::EB * S::NMASK;             // T [EB][N][4]
+  static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                  // T [EB][N][4]
+  static constexpr size_t off_part = off_e + sizeof(T) * S::EB * N * 4;               // T [EB][WPE][NVAL]
+  static constexpr size_t off_scr = off_part + sizeof(T) * S::EB * S::WPE * S::NVAL;  // T [NVAL][NT]
+  static constexpr size_t off_ord = off_scr + sizeof(T) * S::NVAL * S::NT;            // int [K]
   static constexpr size_t bytes = off_ord + sizeof(int) * S::K;
 };
 
-// Per-thread view of the slots.
+// Forward sweep: all currents of one ordering in registers (J[i][i] hold the
+// polarisations); returns the top bracket (the amplitude is en . brtop).
 template <int N, typename T>
-struct GradSlots {
-  using S = GradShape<N, T>;
-  T* base;
-  int tid;
-  __device__ __forceinline__ int seg(int i, int j) const { return i * S::M - i * (i - 1) / 2 + (j - i); }
-  __device__ __forceinline__ T& J(int i, int j, int m) const { return base[((seg(i, j)) * 4 + m) * S::NT + tid]; }
-  __device__ __forceinline__ T& Jb(int i, int j, int m) const {
-    return base[((S::NSEG + seg(i, j)) * 4 + m) * S::NT + tid];
-  }
-  __device__ __forceinline__ T& Sp(int p, int m) const { return base[((2 * S::NSEG + p) * 4 + m) * S::NT + tid]; }
-  __device__ __forceinline__ T& Sb(int p, int m) const {
-    return base[((2 * S::NSEG + N + p) * 4 + m) * S::NT + tid];
-  }
-  // scratch arrays 0..4 of length M
-  __device__ __forceinline__ T& X(int a, int s) const {
-    return base[(8 * S::NSEG + 8 * N + a * S::M + s) * S::NT + tid];
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ T dot4(const T* a, const T* b) {
-  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
-}
-
-template <int N, typename T>
-__device__ __forceinline__ void loadJ(const GradSlots<N, T>& sl, int i, int j, T (&v)[4]) {
-#pragma unroll
-  for (int m = 0; m < 4; ++m) v[m] = sl.J(i, j, m);
-}
-
-// Forward sweep in the slots; returns the amplitude with unit vertex factors.
-template <int N, typename T>
-__device__ T grad_forward(const GradSlots<N, T>& sl, const int* msk, const T* __restrict__ inv, const T (&en)[4],
-                          T (&brtop)[4]) {
+__device__ __forceinline__ void grad_forward(T (&J)[N - 1][N - 1][4], const T (&Sp)[N][4], const int (&msk)[N],
+                                             const T* __restrict__ inv, T (&brtop)[4]) {
   constexpr int M = N - 1;
-  T amp = T(0);
+#pragma unroll
   for (int len = 2; len <= M; ++len) {
+#pragma unroll
     for (int i = 0; i + len - 1 < M; ++i) {
       const int j = i + len - 1;
-      T P2[4], br[4], by[4], W[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        P2[m] = T(2) * (sl.Sp(j + 1, m) - sl.Sp(i, m));
-        br[m] = T(0);
-        by[m] = T(0);
-        W[m] = T(0);
-      }
-      T sxy = T(0);
-      for (int s = i; s < j; ++s) {
-        T X[4], Y[4];
-        loadJ(sl, i, s, X);
-        loadJ(sl, s + 1, j, Y);
-        const T xy = dot4(X, Y);
-        sxy += xy;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) W[m] = fma(xy, sl.Sp(s + 1, m), W[m]);
-        sl.X(0, s) = -dot4(P2, Y);  // cX
-        sl.X(1, s) = dot4(P2, X);   // cR
-      }
-      for (int s = i; s < j; ++s)
-        for (int t = s + 1; t < j; ++t) {
-          T X[4], Y[4], Z[4];
-          loadJ(sl, i, s, X);
-          loadJ(sl, s + 1, t, Y);
-          loadJ(sl, t + 1, j, Z);
-          sl.X(0, s) -= dot4(Y, Z);
-          sl.X(1, t) -= dot4(X, Y);
-          const T xz = dot4(X, Z);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) by[m] = fma(xz, Y[m], by[m]);
-        }
-      for (int s = i; s < j; ++s) {
-        const T cx = sl.X(0, s), cr = sl.X(1, s);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) br[m] = fma(cx, sl.J(i, s, m), fma(cr, sl.J(s + 1, j, m), br[m]));
-      }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) br[m] += T(2) * (W[m] + by[m]) - sxy * (sl.Sp(i, m) + sl.Sp(j + 1, m));
+      T br[4];
+      co_bracket<N, T>(J, Sp, i, j, br);
       if (len < M) {
         const T ip = inv[msk[j + 1] ^ msk[i]];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) sl.J(i, j, m) = br[m] * ip;
+        for (int m = 0; m < 4; ++m) J[i][j][m] = br[m] * ip;
       } else {
-        amp = dot4(en, br);
 #pragma unroll
         for (int m = 0; m < 4; ++m) brtop[m] = br[m];
       }
     }
   }
-  return amp;
 }
 
-// Reverse sweep: adjoints of all currents (slots Jb), of the prefix sums
-// (slots Sb) and of the last gluon's polarisation (enb).
+// Reverse sweep: adjoints of all currents (Jb), of the prefix sums (Sb) and
+// of the last gluon's polarisation (enb), for the amplitude adjoint abar.
 template <int N, typename T>
-__device__ void grad_reverse(const GradSlots<N, T>& sl, const int* msk, const T* __restrict__ inv, const T (&en)[4],
-                             const T (&brtop)[4], T abar, T (&enb)[4]) {
+__device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], const T (&Sp)[N][4],
+                                             const int (&msk)[N], const T* __restrict__ inv, const T (&en)[4],
+                                             const T (&brtop)[4], T abar, T (&Jb)[N - 1][N - 1][4],
+                                             T (&Sb)[N][4], T (&enb)[4]) {
   constexpr int M = N - 1;
   const T gm[4] = {T(1), T(-1), T(-1), T(-1)};
+#pragma unroll
   for (int p = 0; p < N; ++p)
 #pragma unroll
-    for (int m = 0; m < 4; ++m) sl.Sb(p, m) = T(0);
+    for (int m = 0; m < 4; ++m) Sb[p][m] = T(0);
+#pragma unroll
   for (int i = 0; i < M; ++i)
+#pragma unroll
     for (int j = i; j < M; ++j)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) sl.Jb(i, j, m) = T(0);
+      for (int m = 0; m < 4; ++m) Jb[i][j][m] = T(0);
 #pragma unroll
   for (int m = 0; m < 4; ++m) enb[m] = abar * gm[m] * brtop[m];
 
+#pragma unroll
   for (int len = M; len >= 2; --len) {
+#pragma unroll
     for (int i = 0; i + len - 1 < M; ++i) {
       const int j = i + len - 1;
       T P2[4], bb[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) P2[m] = T(2) * (sl.Sp(j + 1, m) - sl.Sp(i, m));
+      for (int m = 0; m < 4; ++m) P2[m] = T(2) * (Sp[j + 1][m] - Sp[i][m]);
       if (len == M) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) bb[m] = abar * gm[m] * en[m];
       } else {
+        // J = br / P^2: bracket adjoint Jbar / P^2; d(1/P^2)/dP^mu = -2 g_mu P^mu / P^4
         const T ip = inv[msk[j + 1] ^ msk[i]];
         T jbj = T(0);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          const T v = sl.Jb(i, j, m);
-          bb[m] = v * ip;
-          jbj = fma(v, sl.J(i, j, m), jbj);
+          bb[m] = Jb[i][j][m] * ip;
+          jbj = fma(Jb[i][j][m], J[i][j][m], jbj);
         }
-        // J = br / P^2: d(1/P^2)/dP^mu = -2 g_mu P^mu / P^4, inv_bar = (Jbar . J) / inv
         const T c = T(-2) * jbj * ip;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          const T pl = gm[m] * (sl.Sp(j + 1, m) - sl.Sp(i, m));
-          sl.Sb(j + 1, m) = fma(c, pl, sl.Sb(j + 1, m));
-          sl.Sb(i, m) = fma(-c, pl, sl.Sb(i, m));
+          const T pl = gm[m] * (Sp[j + 1][m] - Sp[i][m]);
+          Sb[j + 1][m] = fma(c, pl, Sb[j + 1][m]);
+          Sb[i][m] = fma(-c, pl, Sb[i][m]);
         }
       }
-      // recompute cX, cR (scratch 0, 1) and xy (scratch 2); sxy
+      // forward coefficients of the bracket: xy_s, cX_s = -P2.Y_s - sum Y.Z,
+      // cR_t = P2.X_t - sum X.Y
+      T xy[M], cX[M], cR[M], cXb[M], cRb[M];
       T sxy = T(0);
+#pragma unroll
       for (int s = i; s < j; ++s) {
-        T X[4], Y[4];
-        loadJ(sl, i, s, X);
-        loadJ(sl, s + 1, j, Y);
-        const T xy = dot4(X, Y);
-        sl.X(2, s) = xy;
-        sxy += xy;
-        sl.X(0, s) = -dot4(P2, Y);
-        sl.X(1, s) = dot4(P2, X);
+        xy[s] = mdot(J[i][s], J[s + 1][j]);
+        sxy += xy[s];
+        cX[s] = -mdot(P2, J[s + 1][j]);
+        cR[s] = mdot(P2, J[i][s]);
       }
+#pragma unroll
       for (int s = i; s < j; ++s)
+#pragma unroll
         for (int t = s + 1; t < j; ++t) {
-          T X[4], Y[4], Z[4];
-          loadJ(sl, i, s, X);
-          loadJ(sl, s + 1, t, Y);
-          loadJ(sl, t + 1, j, Z);
-          sl.X(0, s) -= dot4(Y, Z);
-          sl.X(1, t) -= dot4(X, Y);
+          cX[s] -= mdot(J[s + 1][t], J[t + 1][j]);
+          cR[t] -= mdot(J[i][s], J[s + 1][t]);
         }
-      // bracket = sum_s (cX X_s + cR Y_s) + 2 W + 2 by - sxy (S_i + S_{j+1})
+      // bracket = sum_s (cX_s X_s + cR_s Y_s) + 2 W + 2 by - sxy (S_i + S_{j+1})
+#pragma unroll
       for (int s = i; s < j; ++s) {
         T a = T(0), b = T(0);
-        const T cx = sl.X(0, s), cr = sl.X(1, s);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          a = fma(bb[m], sl.J(i, s, m), a);
-          b = fma(bb[m], sl.J(s + 1, j, m), b);
-          sl.Jb(i, s, m) = fma(cx, bb[m], sl.Jb(i, s, m));
-          sl.Jb(s + 1, j, m) = fma(cr, bb[m], sl.Jb(s + 1, j, m));
+          a = fma(bb[m], J[i][s][m], a);
+          b = fma(bb[m], J[s + 1][j][m], b);
+          Jb[i][s][m] = fma(cX[s], bb[m], Jb[i][s][m]);
+          Jb[s + 1][j][m] = fma(cR[s], bb[m], Jb[s + 1][j][m]);
         }
-        sl.X(3, s) = a;  // cX bar
-        sl.X(4, s) = b;  // cR bar
+        cXb[s] = a;
+        cRb[s] = b;
       }
       T sxyb = T(0);
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        sxyb = fma(-bb[m], sl.Sp(i, m) + sl.Sp(j + 1, m), sxyb);
-        sl.Sb(i, m) = fma(-sxy, bb[m], sl.Sb(i, m));
-        sl.Sb(j + 1, m) = fma(-sxy, bb[m], sl.Sb(j + 1, m));
+        sxyb = fma(-bb[m], Sp[i][m] + Sp[j + 1][m], sxyb);
+        Sb[i][m] = fma(-sxy, bb[m], Sb[i][m]);
+        Sb[j + 1][m] = fma(-sxy, bb[m], Sb[j + 1][m]);
       }
-      // V4: cX[s] -= Y.Z, cR[t] -= X.Y, by += (X.Z) Y with by_bar = 2 bb
+      // V4: cX_s -= Y.Z, cR_t -= X.Y, by += (X.Z) Y with by_bar = 2 bb
+#pragma unroll
       for (int s = i; s < j; ++s)
+#pragma unroll
         for (int t = s + 1; t < j; ++t) {
-          T X[4], Y[4], Z[4];
-          loadJ(sl, i, s, X);
-          loadJ(sl, s + 1, t, Y);
-          loadJ(sl, t + 1, j, Z);
-          const T xz = dot4(X, Z);
-          const T yzb = -sl.X(3, s);
-          const T xyb = -sl.X(4, t);
+          const T xz = mdot(J[i][s], J[t + 1][j]);
+          const T yzb = -cXb[s];
+          const T xyb = -cRb[t];
           T xzb = T(0);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) xzb = fma(T(2) * bb[m], Y[m], xzb);
+          for (int m = 0; m < 4; ++m) xzb = fma(T(2) * bb[m], J[s + 1][t][m], xzb);
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
-            sl.Jb(i, s, m) += gm[m] * (xzb * Z[m] + xyb * Y[m]);
-            sl.Jb(t + 1, j, m) += gm[m] * (xzb * X[m] + yzb * Y[m]);
-            sl.Jb(s + 1, t, m) += T(2) * xz * bb[m] + gm[m] * (xyb * X[m] + yzb * Z[m]);
+            Jb[i][s][m] += gm[m] * (xzb * J[t + 1][j][m] + xyb * J[s + 1][t][m]);
+            Jb[t + 1][j][m] += gm[m] * (xzb * J[i][s][m] + yzb * J[s + 1][t][m]);
+            Jb[s + 1][t][m] += T(2) * xz * bb[m] + gm[m] * (xyb * J[i][s][m] + yzb * J[t + 1][j][m]);
           }
         }
-      // V3: xy = X.Y (sxy, W), cR = P2.X, cX = -P2.Y
+      // V3: xy_s enters sxy and W = sum_s xy_s S_{s+1}; cR_s = P2.X_s, cX_s = -P2.Y_s
       T P2b[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
       for (int s = i; s < j; ++s) {
-        T X[4], Y[4];
-        loadJ(sl, i, s, X);
-        loadJ(sl, s + 1, j, Y);
         T xyb = sxyb;
-        const T xy = sl.X(2, s);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          xyb = fma(T(2) * bb[m], sl.Sp(s + 1, m), xyb);
-          sl.Sb(s + 1, m) = fma(xy, T(2) * bb[m], sl.Sb(s + 1, m));
+          xyb = fma(T(2) * bb[m], Sp[s + 1][m], xyb);
+          Sb[s + 1][m] = fma(xy[s], T(2) * bb[m], Sb[s + 1][m]);
         }
-        const T pxb = sl.X(4, s);
-        const T pyb = -sl.X(3, s);
+        const T pxb = cRb[s];
+        const T pyb = -cXb[s];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          sl.Jb(i, s, m) += gm[m] * (xyb * Y[m] + pxb * P2[m]);
-          sl.Jb(s + 1, j, m) += gm[m] * (xyb * X[m] + pyb * P2[m]);
-          P2b[m] += gm[m] * (pxb * X[m] + pyb * Y[m]);
+          Jb[i][s][m] += gm[m] * (xyb * J[s + 1][j][m] + pxb * P2[m]);
+          Jb[s + 1][j][m] += gm[m] * (xyb * J[i][s][m] + pyb * P2[m]);
+          P2b[m] += gm[m] * (pxb * J[i][s][m] + pyb * J[s + 1][j][m]);
         }
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        sl.Sb(j + 1, m) = fma(T(2), P2b[m], sl.Sb(j + 1, m));
-        sl.Sb(i, m) = fma(T(-2), P2b[m], sl.Sb(i, m));
+        Sb[j + 1][m] = fma(T(2), P2b[m], Sb[j + 1][m]);
+        Sb[i][m] = fma(T(-2), P2b[m], Sb[i][m]);
       }
     }
   }
@@ -289,14 +222,14 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
                                                                       int* __restrict__ status) {
   using S = GradShape<N, T>;
   using L = GradSmem<N, T>;
-  constexpr int M = S::M, K = S::K, EB = S::EB, NT = S::NT;
+  constexpr int M = S::M, K = S::K, KP = S::KP, EB = S::EB, NT = S::NT, NVAL = S::NVAL;
   extern __shared__ __align__(16) unsigned char smem[];
   double* s_pair = reinterpret_cast<double*>(smem + L::off_pair);
   T* s_inv = reinterpret_cast<T*>(smem + L::off_inv);
   T* s_k = reinterpret_cast<T*>(smem + L::off_k);
   T* s_e = reinterpret_cast<T*>(smem + L::off_e);
-  T* s_acc = reinterpret_cast<T*>(smem + L::off_acc);
-  T* s_slot = reinterpret_cast<T*>(smem + L::off_slot);
+  T* s_part = reinterpret_cast<T*>(smem + L::off_part);
+  T* s_scr = reinterpret_cast<T*>(smem + L::off_scr);
   int* s_ord = reinterpret_cast<int*>(smem + L::off_ord);
 
   const int64_t e0 = (int64_t)blockIdx.x * EB;
@@ -321,7 +254,6 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
     }
     s_ord[r] = packed;
   }
-  for (int it = tid; it < EB * 2 * N * 4; it += NT) s_acc[it] = T(0);
   for (int it = tid; it < EB * N; it += NT) {
     const int el = it / N, g = it % N;
     const int64_t e = e0 + el;
@@ -376,33 +308,35 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
   }
   __syncthreads();
 
-  // ---- one ordering per thread: forward, reverse, accumulate ----
-  const GradSlots<N, T> sl{s_slot, tid};
-  constexpr int TOTAL = EB * K;
+  // ---- one ordering per thread: forward, reverse, per-warp sums ----
   const T vfac = T(1.0 / double(1 << ((N - 2) / 2)) * (((N - 2) & 1) ? 0.70710678118654752440 : 1.0));
-  for (int t = tid; t < TOTAL; t += NT) {
-    const int el = t / K;
-    const int r = t - el * K;
+  const int lane = tid & 31;
+  for (int t = tid; t < EB * KP; t += NT) {  // EB * KP is a multiple of NT: uniform rounds
+    const int el = t / KP;
+    const int r = t - el * KP;
     const int64_t e = e0 + el;
-    const bool live = e < B;
-    int gl[N];
-    int msk[N];
+    const bool live = (e < B) && (r < K);
     if (live) {
       const int packed = s_ord[r];
+      int gl[N];
       gl[0] = 0;
+#pragma unroll
       for (int pos = 1; pos < N - 1; ++pos) gl[pos] = (packed >> (4 * (pos - 1))) & 15;
       gl[N - 1] = N - 1;
       const T* ke = s_k + el * N * 4;
       const T* ee = s_e + el * N * 4;
+      T J[M][M][4], Jb[M][M][4], Sp[N][4], Sb[N][4];
+      int msk[N];
       msk[0] = 0;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) sl.Sp(0, m) = T(0);
+      for (int m = 0; m < 4; ++m) Sp[0][m] = T(0);
+#pragma unroll
       for (int pos = 0; pos < M; ++pos) {
         const int g = gl[pos];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          sl.J(pos, pos, m) = ee[g * 4 + m];
-          sl.Sp(pos + 1, m) = sl.Sp(pos, m) + ke[g * 4 + m];
+          J[pos][pos][m] = ee[g * 4 + m];
+          Sp[pos + 1][m] = Sp[pos][m] + ke[g * 4 + m];
         }
         msk[pos + 1] = msk[pos] | (1 << g);
       }
@@ -410,67 +344,53 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
 #pragma unroll
       for (int m = 0; m < 4; ++m) en[m] = ee[(N - 1) * 4 + m];
       const T* inv = s_inv + el * S::NMASK;
-      grad_forward<N, T>(sl, msk, inv, en, brtop);
+      grad_forward<N, T>(J, Sp, msk, inv, brtop);
       const T abar = T(2) * vfac * Y[e * (int64_t)K + r];
-      grad_reverse<N, T>(sl, msk, inv, en, brtop, abar, enb);
-      // momentum adjoint of the gluon at position q: sum of Sbar_p for p > q.
-      // In place, shifted by one slot: afterwards Sb(q + 1) holds that sum.
+      grad_reverse<N, T>(J, Sp, msk, inv, en, brtop, abar, Jb, Sb, enb);
+      // momentum adjoint of the gluon at position q: the sum of Sbar_p over
+      // p > q (S_p holds the momenta of positions < p); polarisation adjoints
+      // Jbar(q..q), and enb for the last gluon, whose momentum enters only
+      // through its polarisation.  Stored at the gluon's slot.
       T run[4] = {T(0), T(0), T(0), T(0)};
-      for (int pos = M - 1; pos >= 0; --pos)
+#pragma unroll
+      for (int pos = M - 1; pos >= 0; --pos) {
+        const int g = gl[pos];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          run[m] += sl.Sb(pos + 1, m);
-          sl.Sb(pos + 1, m) = run[m];
+          run[m] += Sb[pos + 1][m];
+          s_scr[((0 * N + g) * 4 + m) * NT + tid] = run[m];
+          s_scr[((1 * N + g) * 4 + m) * NT + tid] = Jb[pos][pos][m];
         }
-      // the last gluon's polarisation adjoint goes to a dead scratch slot
-#pragma unroll
-      for (int m = 0; m < 4; ++m) sl.X(0, m) = enb[m];
-    }
-    // sum over the orderings of each event, gluon by gluon
-    const int el0 = __shfl_sync(0xffffffffu, el, 0);
-    const bool uniform = __all_sync(0xffffffffu, el == el0);
-    for (int g = 0; g < N; ++g) {
-      // position of gluon g in this ordering
-      int pos_g = -1;
-      if (live) {
-        for (int pos = 0; pos < N; ++pos)
-          if (gl[pos] == g) pos_g = pos;
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        T a = T(0), b = T(0);
-        if (live) {
-          if (pos_g < M) {
-            a = sl.Sb(pos_g + 1, m);
-            b = sl.Jb(pos_g, pos_g, m);
-          } else {
-            b = sl.X(0, m);
-          }
-        }
-        if (uniform) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
-          }
-          if ((tid & 31) == 0 && live) {
-            atomicAdd(&s_acc[((el * 2 + 0) * N + g) * 4 + m], a);
-            atomicAdd(&s_acc[((el * 2 + 1) * N + g) * 4 + m], b);
-          }
-        } else if (live) {
-          atomicAdd(&s_acc[((el * 2 + 0) * N + g) * 4 + m], a);
-          atomicAdd(&s_acc[((el * 2 + 1) * N + g) * 4 + m], b);
-        }
+        s_scr[((0 * N + N - 1) * 4 + m) * NT + tid] = T(0);
+        s_scr[((1 * N + N - 1) * 4 + m) * NT + tid] = enb[m];
       }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NVAL; ++v) s_scr[v * NT + tid] = T(0);
+    }
+    // warp sums in a fixed order; a warp holds orderings of one event
+    const int wglob = t >> 5;  // warp index among the block's tasks
+    const int wel = wglob / S::WPE, wr = wglob % S::WPE;
+#pragma unroll 4
+    for (int v = 0; v < NVAL; ++v) {
+      T a = s_scr[v * NT + tid];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      if (lane == 0) s_part[(wel * S::WPE + wr) * NVAL + v] = a;
     }
   }
   __syncthreads();
-  for (int it = tid; it < EB * N * 4; it += NT) {
-    const int el = it / (N * 4), rem = it % (N * 4);
+  for (int it = tid; it < EB * NVAL; it += NT) {
+    const int el = it / NVAL, v = it % NVAL;
     const int64_t e = e0 + el;
     if (e >= B) continue;
-    kbar_out[e * N * 4 + rem] = (double)s_acc[(el * 2 + 0) * N * 4 + rem];
-    ebar_out[e * N * 4 + rem] = (double)s_acc[(el * 2 + 1) * N * 4 + rem];
+    T a = T(0);
+    for (int w = 0; w < S::WPE; ++w) a += s_part[(el * S::WPE + w) * NVAL + v];
+    const int which = v / (N * 4), rem = v % (N * 4);
+    (which == 0 ? kbar_out : ebar_out)[e * N * 4 + rem] = (double)a;
   }
 }
 

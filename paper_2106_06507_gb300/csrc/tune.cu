@@ -4,8 +4,8 @@
 // results) and differ only in how the work maps onto the GPU:
 //   colour-ordered recursion, sampled helicities, n >= 6:
 //     0 = one thread per ordering, 1 = depth-first groups of six orderings;
-//   colour-dressed recursion: threads per event (CTA size), see
-//     cd_variant_threads() in cd_recursion.cuh.
+//   colour-dressed recursion: threads per event (CTA size) and unrolling of
+//     the partition loop, see cd_variant_threads() in cd_recursion.cuh.
 // bg_autotune times every variant on a synthetic probe batch (Rambo points
 // from a hash of the event index, no cut) and records the fastest in a
 // process-wide table keyed by (device, algorithm, n, precision); launches

@@ -43,7 +43,7 @@ def cd_all_variants(bg, n, B, prec, flow):
                                            (12, 40, 1, True), (8, 100, 0, False), (11, 24, 0, True)])
 def test_cd_variants_bitwise_identical(bg, n, B, prec, flow):
     outs = cd_all_variants(bg, n, B, prec, flow)
-    assert len(outs) == (2 if n <= 9 else 3)
+    assert len(outs) == (4 if n <= 9 else 5)
     assert np.count_nonzero(outs[0]) > 0
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
@@ -68,7 +68,7 @@ def test_co_variants_bitwise_identical(bg, n, prec):
 
 def test_autotune_table_and_cache(bg, tmp_path):
     best_cd, ms_cd = bg.autotune(bg.BG_ALGO_CD, 10, bg.BG_F32, probe_batch=2048)
-    assert 0 <= best_cd < 3 and len(ms_cd) == 3 and min(ms_cd) > 0
+    assert 0 <= best_cd < 5 and len(ms_cd) == 5 and min(ms_cd) > 0
     assert ms_cd[best_cd] == min(ms_cd)
     assert bg.tune_get(bg.BG_ALGO_CD, 10, bg.BG_F32) == best_cd
     best_co, ms_co = bg.autotune(bg.BG_ALGO_CO, 7, bg.BG_F32)
@@ -87,7 +87,7 @@ def test_autotune_table_and_cache(bg, tmp_path):
     assert bg.autotune(bg.BG_ALGO_CO, 5, bg.BG_F32)[0] == 0
     bg.tune_set(bg.BG_ALGO_CO, 5, bg.BG_F32, -1)
     with pytest.raises(bg.BGError):
-        bg.tune_set(bg.BG_ALGO_CD, 10, bg.BG_F32, 3)
+        bg.tune_set(bg.BG_ALGO_CD, 10, bg.BG_F32, 5)
     with pytest.raises(bg.BGError):
         bg.autotune(bg.BG_ALGO_CO, 10, bg.BG_F32)
     bad = tmp_path / "bad.txt"

@@ -87,10 +87,11 @@ def test_argument_errors_without_gpu(libbg):
 
 def test_tune_variant_counts_without_gpu(libbg):
     # colour-ordered: sampled-helicity variants exist from n = 6; colour-
-    # dressed: two CTA sizes up to n = 9, three above; out of range: 0
+    # dressed: four (CTA size, unrolling) pairs up to n = 9, five above;
+    # out of range: 0
     CO, CD = 0, 1
     assert [libbg.bg_tune_num_variants(CO, n) for n in range(4, 10)] == [1, 1, 2, 2, 2, 2]
-    assert [libbg.bg_tune_num_variants(CD, n) for n in range(4, 13)] == [2] * 6 + [3] * 3
+    assert [libbg.bg_tune_num_variants(CD, n) for n in range(4, 13)] == [4] * 6 + [5] * 3
     assert libbg.bg_tune_num_variants(CO, 10) == 0
     assert libbg.bg_tune_num_variants(CD, 3) == 0
     assert libbg.bg_tune_num_variants(7, 6) == 0
