@@ -2,66 +2,91 @@
 // Rambo uniforms: from the adjoints of the scaled momenta and polarisation
 // vectors (co_grad.cuh) through the light-cone polarisations (Eq. 2.7) and
 // through Rambo (Sec. 3) to the 4(n-2) uniforms of each event.  One thread
-// per event, FP64.  The Rambo Jacobian is applied in forward mode, one
-// uniform at a time (4(n-2) tangent sweeps of the momentum construction);
-// the incoming momenta do not depend on the uniforms.
+// per event, FP64, one reverse sweep through the Rambo construction; the
+// incoming momenta do not depend on the uniforms.
 #include "bg_internal.h"
 #include "device_common.cuh"
 
 namespace bg {
 namespace {
 
-// value + derivative along one direction
-struct D1 {
-  double v, d;
-};
-__device__ __forceinline__ D1 mk(double v, double d = 0.0) { return D1{v, d}; }
-__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return D1{a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return D1{a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return D1{a.v * b.v, a.d * b.v + a.v * b.d}; }
-__device__ __forceinline__ D1 operator/(D1 a, D1 b) {
-  const double iv = 1.0 / b.v;
-  return D1{a.v * iv, (a.d - a.v * iv * b.d) * iv};
-}
-__device__ __forceinline__ D1 dsqrt(D1 a) {
-  const double s = sqrt(a.v);
-  return D1{s, a.d * 0.5 / s};
-}
-__device__ __forceinline__ D1 dlog(D1 a) { return D1{log(a.v), a.d / a.v}; }
-
-// Rambo final-state momenta and their derivative along uniform `dir`.
+// Reverse mode through Rambo: given the adjoints pbar of the final-state lab
+// momenta, accumulate the adjoints of the 4(n-2) uniforms.  Forward:
+//   q_i = q0_i (1, st_i cos phi_i, st_i sin phi_i, c_i),  c_i = 2u1 - 1,
+//   phi_i = 2 pi u2, q0_i = -log(u3 u4), st_i = sqrt(1 - c_i^2);
+//   Q = sum_i q_i, M = sqrt(Q^2), b = -Q_vec/M, x = sqrt_s/M, gamma = Q0/M,
+//   a = 1/(1 + gamma);  p_i = x y_i with y0 = gamma q0 + b.q, y_vec = q_vec
+//   + b q0 + a (b.q) b.
 template <int N>
-__device__ void rambo_tangent(const double* u, double sqrt_s, int dir, D1 (&p)[N - 2][4]) {
+__device__ void rambo_reverse(const double* u, double sqrt_s, const double (&pbar)[N - 2][4], double* ubar) {
   constexpr int NOUT = N - 2;
-  D1 q[NOUT][4];
-  D1 Q[4] = {mk(0), mk(0), mk(0), mk(0)};
+  double q[NOUT][4], st[NOUT], cphi[NOUT], sphi[NOUT];
+  double Q[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = 0; i < NOUT; ++i) {
-    const D1 u1 = mk(u[4 * i + 0], dir == 4 * i + 0 ? 1.0 : 0.0);
-    const D1 u2 = mk(u[4 * i + 1], dir == 4 * i + 1 ? 1.0 : 0.0);
-    const D1 u3 = mk(u[4 * i + 2], dir == 4 * i + 2 ? 1.0 : 0.0);
-    const D1 u4 = mk(u[4 * i + 3], dir == 4 * i + 3 ? 1.0 : 0.0);
-    const D1 c = mk(2.0) * u1 - mk(1.0);
-    double sphi, cphi;
-    sincospi(2.0 * u2.v, &sphi, &cphi);
-    const double tp = 6.283185307179586477;
-    const D1 sp = mk(sphi, tp * cphi * u2.d), cp = mk(cphi, -tp * sphi * u2.d);
-    const D1 q0 = mk(0.0) - dlog(u3 * u4);
-    const D1 st = dsqrt(mk(1.0) - c * c);
+    const double c = 2.0 * u[4 * i + 0] - 1.0;
+    sincospi(2.0 * u[4 * i + 1], &sphi[i], &cphi[i]);
+    const double q0 = -log(u[4 * i + 2] * u[4 * i + 3]);
+    st[i] = sqrt(1.0 - c * c);
     q[i][0] = q0;
-    q[i][1] = q0 * st * cp;
-    q[i][2] = q0 * st * sp;
+    q[i][1] = q0 * st[i] * cphi[i];
+    q[i][2] = q0 * st[i] * sphi[i];
     q[i][3] = q0 * c;
-    for (int m = 0; m < 4; ++m) Q[m] = Q[m] + q[i][m];
+    for (int m = 0; m < 4; ++m) Q[m] += q[i][m];
   }
-  const D1 M = dsqrt(Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3]);
-  const D1 b[3] = {mk(0.0) - Q[1] / M, mk(0.0) - Q[2] / M, mk(0.0) - Q[3] / M};
-  const D1 x = mk(sqrt_s) / M;
-  const D1 gamma = Q[0] / M;
-  const D1 a = mk(1.0) / (mk(1.0) + gamma);
+  const double M = sqrt(Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3]);
+  const double b[3] = {-Q[1] / M, -Q[2] / M, -Q[3] / M};
+  const double x = sqrt_s / M;
+  const double gamma = Q[0] / M;
+  const double a = 1.0 / (1.0 + gamma);
+  // adjoints of x, gamma, a, b and of the q_i (direct terms)
+  double xbar = 0.0, gbar = 0.0, abar = 0.0, bbar[3] = {0.0, 0.0, 0.0};
+  double qbar[NOUT][4];
   for (int i = 0; i < NOUT; ++i) {
-    const D1 bq = b[0] * q[i][1] + b[1] * q[i][2] + b[2] * q[i][3];
-    p[i][0] = x * (gamma * q[i][0] + bq);
-    for (int j = 0; j < 3; ++j) p[i][1 + j] = x * (q[i][1 + j] + b[j] * q[i][0] + a * bq * b[j]);
+    const double bq = b[0] * q[i][1] + b[1] * q[i][2] + b[2] * q[i][3];
+    const double y0 = gamma * q[i][0] + bq;
+    double yb[4];
+    for (int m = 0; m < 4; ++m) yb[m] = x * pbar[i][m];
+    xbar += pbar[i][0] * y0;
+    double ybb = 0.0;  // sum_k ybar_k b_k
+    for (int k = 0; k < 3; ++k) {
+      const double yk = q[i][1 + k] + b[k] * q[i][0] + a * bq * b[k];
+      xbar += pbar[i][1 + k] * yk;
+      ybb += yb[1 + k] * b[k];
+    }
+    gbar += yb[0] * q[i][0];
+    abar += bq * ybb;
+    const double bqbar = yb[0] + a * ybb;
+    qbar[i][0] = yb[0] * gamma + ybb;
+    for (int k = 0; k < 3; ++k) {
+      bbar[k] += yb[1 + k] * (q[i][0] + a * bq) + bqbar * q[i][1 + k];
+      qbar[i][1 + k] = yb[1 + k] + bqbar * b[k];
+    }
+  }
+  // a = 1/(1+gamma), x = sqrt_s/M, gamma = Q0/M, b = -Q_vec/M, M = sqrt(Q^2)
+  gbar += -a * a * abar;
+  double Mbar = -xbar * x / M - gbar * gamma / M;
+  double Qbar[4] = {gbar / M, 0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k) {
+    Qbar[1 + k] = -bbar[k] / M;
+    Mbar += -bbar[k] * b[k] / M;
+  }
+  Qbar[0] += Mbar * Q[0] / M;
+  for (int k = 0; k < 3; ++k) Qbar[1 + k] += -Mbar * Q[1 + k] / M;
+  // Q = sum q_i; then q_i(u)
+  const double twopi = 6.283185307179586477;
+  for (int i = 0; i < NOUT; ++i) {
+    double qb[4];
+    for (int m = 0; m < 4; ++m) qb[m] = qbar[i][m] + Qbar[m];
+    const double q0 = q[i][0];
+    const double c = 2.0 * u[4 * i + 0] - 1.0;
+    const double q0bar = qb[0] + qb[1] * st[i] * cphi[i] + qb[2] * st[i] * sphi[i] + qb[3] * c;
+    const double stbar = q0 * (qb[1] * cphi[i] + qb[2] * sphi[i]);
+    const double cbar = q0 * qb[3] - stbar * c / st[i];
+    const double phibar = q0 * st[i] * (-qb[1] * sphi[i] + qb[2] * cphi[i]);
+    ubar[4 * i + 0] = 2.0 * cbar;
+    ubar[4 * i + 1] = twopi * phibar;
+    ubar[4 * i + 2] = -q0bar / u[4 * i + 2];
+    ubar[4 * i + 3] = -q0bar / u[4 * i + 3];
   }
 }
 
@@ -130,15 +155,9 @@ __global__ void __launch_bounds__(128) rambo_grad_kernel(int64_t B, double sqrt_
       pbar[i][m] = kb[m] * inv_s;
     }
   }
-  const double* ue = u + e * DIM;
-  for (int dir = 0; dir < DIM; ++dir) {
-    D1 pt[NOUT][4];
-    rambo_tangent<N>(ue, sqrt_s, dir, pt);
-    double s = 0.0;
-    for (int i = 0; i < NOUT; ++i)
-      for (int m = 0; m < 4; ++m) s += pbar[i][m] * pt[i][m].d;
-    gout[dir] = w * s;
-  }
+  double ub[DIM];
+  rambo_reverse<N>(u + e * DIM, sqrt_s, pbar, ub);
+  for (int j = 0; j < DIM; ++j) gout[j] = w * ub[j];
 }
 
 template <int N>
