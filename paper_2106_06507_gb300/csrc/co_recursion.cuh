@@ -60,8 +60,43 @@ struct CoSmem {
   static constexpr size_t off_k = off_inv + sizeof(T) * S::EB * S::NMASK;                  // T [EB][N][4]
   static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                       // T [EB][NPOL][N][4]
   static constexpr size_t off_ord = off_e + sizeof(T) * S::EB * S::NPOL * N * 4;           // int [K]
-  static constexpr size_t bytes = off_ord + sizeof(int) * S::K;
+  static constexpr size_t off_p2 = (off_ord + sizeof(int) * S::K + 7) & ~size_t(7);       // double [EB][NMASK]
+  static constexpr size_t bytes = off_p2 + sizeof(double) * S::EB * S::NMASK;
 };
+
+// Inverse propagators 1/P(S)^2 for every subset S of the first M gluons of
+// each of the block's EB events, from the FP64 pair invariants 2 k_a.k_b
+// (s_pair [EB][M(M-1)/2], a < b lexicographic).  P(S)^2 is built by the
+// highest member h of S: P(S)^2 = P(S - h)^2 + sum_{a in S-h} 2 k_a.k_h, in M
+// rounds separated by barriers (s_p2 [EB][2^M] FP64).  The full set and the
+// single gluons get 0.  Called by all threads of the block.
+template <int M, int EB, int NT, typename T>
+__device__ __forceinline__ void co_inverse_table(const double* __restrict__ s_pair, double* __restrict__ s_p2,
+                                                 T* __restrict__ s_inv, int64_t e0, int64_t B) {
+  constexpr int NMASK = 1 << M, NPAIR = M * (M - 1) / 2;
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int h = 0; h < M; ++h) {
+    for (int it = tid; it < (EB << h); it += NT) {
+      const int el = it >> h, low = it & ((1 << h) - 1);
+      if (e0 + el >= B) continue;
+      double v = low ? s_p2[el * NMASK + low] : 0.0;
+      for (int r = low; r; r &= r - 1) {
+        const int a = __ffs(r) - 1;
+        v += s_pair[el * NPAIR + a * M - a * (a + 1) / 2 + (h - a - 1)];
+      }
+      s_p2[el * NMASK + (low | (1 << h))] = v;
+    }
+    __syncthreads();
+  }
+  for (int it = tid; it < EB * NMASK; it += NT) {
+    const int el = it / NMASK, mask = it % NMASK;
+    if (e0 + el >= B) continue;
+    s_inv[el * NMASK + mask] =
+        (__popc(mask) >= 2 && mask != NMASK - 1) ? T(1) / T(s_p2[el * NMASK + mask]) : T(0);
+  }
+  __syncthreads();
+}
 
 // Bracket of segment (i..j) of one ordering (the V3 and V4 sums before the
 // propagator); i and j are compile-time after unrolling.  J[a][b] hold the
@@ -142,8 +177,8 @@ __device__ __forceinline__ T co_recursion(T (&J)[N - 1][N - 1][4], const T (&Sp)
 
 template <int N, typename T, bool SUMHEL>
 __global__ void __launch_bounds__(256) co_kernel(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
-                                                 const double* __restrict__ p, const int8_t* __restrict__ hel, Q4 q,
-                                                 T* __restrict__ amps, int* __restrict__ status) {
+                                                 const double* __restrict__ p, const int8_t* __restrict__ hel,
+                                                 PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
   // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
   const int64_t B = dB ? (*dB < S_ ? *dB : S_) : S_;
   using S = CoShape<N, SUMHEL>;
@@ -192,22 +227,24 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t S_, const int64_t* __re
 #pragma unroll
       for (int m = 0; m < 4; ++m) k[m] = -k[m];
     }
-    double e1[4], e2[4];
-    lc_polarisations(k, q.v, e1, e2);
 #pragma unroll
     for (int m = 0; m < 4; ++m) s_k[(el * N + g) * 4 + m] = T(k[m]);
     if (SUMHEL) {
+      T e1[4], e2[4];
+      lc_polarisation_frame<T>(k, F, true, e1);
+      lc_polarisation_frame<T>(k, F, false, e2);
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        s_e[((el * 2 + 0) * N + g) * 4 + m] = T(e1[m]);
-        s_e[((el * 2 + 1) * N + g) * 4 + m] = T(e2[m]);
+        s_e[((el * 2 + 0) * N + g) * 4 + m] = e1[m];
+        s_e[((el * 2 + 1) * N + g) * 4 + m] = e2[m];
       }
     } else {
       const int h = hel[(int64_t)g * S_ + e];
       if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
-      const double* ev = (h < 0) ? e2 : e1;
+      T ev[4];
+      lc_polarisation_frame<T>(k, F, h >= 0, ev);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) s_e[(el * N + g) * 4 + m] = T(ev[m]);
+      for (int m = 0; m < 4; ++m) s_e[(el * N + g) * 4 + m] = ev[m];
     }
   }
   // pair invariants 2 k_a.k_b (FP64) among the first M gluons
@@ -232,22 +269,7 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t S_, const int64_t* __re
   }
   __syncthreads();
   // ---- phase 1b: inverse propagators for every subset of the first M gluons
-  for (int it = tid; it < EB * S::NMASK; it += S::NT) {
-    const int el = it / S::NMASK, mask = it % S::NMASK;
-    if (e0 + el >= B) continue;
-    double p2 = 0.0;
-    int idx = 0;
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-#pragma unroll
-      for (int b = a + 1; b < M; ++b) {
-        if (((mask >> a) & 1) && ((mask >> b) & 1)) p2 += s_pair[el * S::NPAIR + idx];
-        ++idx;
-      }
-    }
-    s_inv[el * S::NMASK + mask] = (__popc(mask) >= 2 && mask != S::NMASK - 1) ? T(1) / T(p2) : T(0);
-  }
-  __syncthreads();
+  co_inverse_table<M, EB, S::NT, T>(s_pair, reinterpret_cast<double*>(smem + L::off_p2), s_inv, e0, B);
 
   // ---- phase 2: one ordering (and polarisation configuration) per thread
   constexpr int TOTAL = EB * S::TPE;
@@ -304,10 +326,9 @@ cudaError_t launch_co_n(int64_t B, double sqrt_s, const double* p, const int8_t*
   auto kern = co_kernel<N, T, SUMHEL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (err != cudaSuccess) return err;
-  Q4 qq;
-  for (int m = 0; m < 4; ++m) qq.v[m] = q[m];
+  const PolFrame F = make_pol_frame(q);
   const int64_t blocks = (B + S::EB - 1) / S::EB;
-  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, dB, 1.0 / sqrt_s, p, hel, qq, amps, status);
+  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, dB, 1.0 / sqrt_s, p, hel, F, amps, status);
   return cudaGetLastError();
 }
 
@@ -339,13 +360,14 @@ struct CoDfsSmem {
   static constexpr size_t off_k = off_inv + sizeof(T) * S::EB * S::NMASK;              // T [EB][N][4]
   static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                   // T [EB][N][4]
   static constexpr size_t off_ord = off_e + sizeof(T) * S::EB * N * 4;                 // int [G]
-  static constexpr size_t bytes = off_ord + sizeof(int) * S::G;
+  static constexpr size_t off_p2 = (off_ord + sizeof(int) * S::G + 7) & ~size_t(7);     // double [EB][NMASK]
+  static constexpr size_t bytes = off_p2 + sizeof(double) * S::EB * S::NMASK;
 };
 
 template <int N, typename T>
 __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
                                                      const double* __restrict__ p, const int8_t* __restrict__ hel,
-                                                     Q4 q, T* __restrict__ amps, int* __restrict__ status) {
+                                                     PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
   // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
   const int64_t B = dB ? (*dB < S_ ? *dB : S_) : S_;
   using S = CoDfsShape<N>;
@@ -395,15 +417,14 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t S_, const int64_t* 
 #pragma unroll
       for (int m = 0; m < 4; ++m) k[m] = -k[m];
     }
-    double e1[4], e2[4];
-    lc_polarisations(k, q.v, e1, e2);
     const int h = hel[(int64_t)g * S_ + e];
     if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
-    const double* ev = (h < 0) ? e2 : e1;
+    T ev[4];
+    lc_polarisation_frame<T>(k, F, h >= 0, ev);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       s_k[(el * N + g) * 4 + m] = T(k[m]);
-      s_e[(el * N + g) * 4 + m] = T(ev[m]);
+      s_e[(el * N + g) * 4 + m] = ev[m];
     }
   }
   for (int it = tid; it < EB * S::NPAIR; it += NT) {
@@ -425,22 +446,7 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t S_, const int64_t* 
         sgn * 2.0 * (ka[0] * kb[0] - ka[1] * kb[1] - ka[2] * kb[2] - ka[3] * kb[3]) * inv_sqrt_s * inv_sqrt_s;
   }
   __syncthreads();
-  for (int it = tid; it < EB * S::NMASK; it += NT) {
-    const int el = it / S::NMASK, mask = it % S::NMASK;
-    if (e0 + el >= B) continue;
-    double p2 = 0.0;
-    int idx = 0;
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-#pragma unroll
-      for (int b = a + 1; b < M; ++b) {
-        if (((mask >> a) & 1) && ((mask >> b) & 1)) p2 += s_pair[el * S::NPAIR + idx];
-        ++idx;
-      }
-    }
-    s_inv[el * S::NMASK + mask] = (__popc(mask) >= 2 && mask != S::NMASK - 1) ? T(1) / T(p2) : T(0);
-  }
-  __syncthreads();
+  co_inverse_table<M, EB, NT, T>(s_pair, reinterpret_cast<double*>(smem + L::off_p2), s_inv, e0, B);
 
   // ---- phase 2: one group of six orderings per thread
   constexpr int TOTAL = EB * G;
@@ -561,10 +567,9 @@ cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_
   auto kern = co_kernel_dfs<N, T>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (err != cudaSuccess) return err;
-  Q4 qq;
-  for (int m = 0; m < 4; ++m) qq.v[m] = q[m];
+  const PolFrame F = make_pol_frame(q);
   const int64_t blocks = (B + S::EB - 1) / S::EB;
-  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, dB, 1.0 / sqrt_s, p, hel, qq, amps, status);
+  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(B, dB, 1.0 / sqrt_s, p, hel, F, amps, status);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <stdint.h>
 
 namespace bg {
@@ -72,6 +74,59 @@ __device__ __forceinline__ void lc_polarisations(const double k[4], const double
   e2[1] = b1 - cb * q[1];
   e2[2] = b2 - cb * q[2];
   e2[3] = b3 - cb * q[3];
+}
+
+// The gauge frame of lc_polarisations depends only on q: PolFrame holds it,
+// computed once on the host, for q (index 0) and for its tie-break partner
+// (q0, -q_vec) (index 1), so that each gluon needs two dot products and one
+// division.  Same construction as lc_polarisations.
+struct PolFrame {
+  double q[2][4];
+  double a[2][3];
+  double b[2][3];
+};
+
+inline PolFrame make_pol_frame(const double* qin) {
+  PolFrame F;
+  for (int f = 0; f < 2; ++f) {
+    const double sg = f ? -1.0 : 1.0;
+    const double q[4] = {qin[0], sg * qin[1], sg * qin[2], sg * qin[3]};
+    for (int m = 0; m < 4; ++m) F.q[f][m] = q[m];
+    const double inv_qn = 1.0 / std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double nx = q[1] * inv_qn, ny = q[2] * inv_qn, nz = q[3] * inv_qn, sb = 1.0;
+    if (nz < 0.0) {
+      nx = -nx;
+      ny = -ny;
+      nz = -nz;
+      sb = -1.0;
+    }
+    const double h = 1.0 / (1.0 + nz);
+    F.a[f][0] = 1.0 - nx * nx * h;
+    F.a[f][1] = -nx * ny * h;
+    F.a[f][2] = -nx;
+    F.b[f][0] = sb * (-nx * ny * h);
+    F.b[f][1] = sb * (1.0 - ny * ny * h);
+    F.b[f][2] = sb * (-ny);
+  }
+  return F;
+}
+
+// e = A - (A.k / q.k) q for A = (0, a) (label +1) or (0, b) (label -1); the
+// ratio in the arithmetic of T (the vector is rounded to T anyway).
+template <typename T>
+__device__ __forceinline__ void lc_polarisation_frame(const double k[4], const PolFrame& F, bool plus, T (&e)[4]) {
+  int f = 0;
+  double kq = k[0] * F.q[0][0] - k[1] * F.q[0][1] - k[2] * F.q[0][2] - k[3] * F.q[0][3];
+  if (fabs(kq) <= 1e-9 * fabs(k[0]) * F.q[0][0]) {
+    f = 1;
+    kq = k[0] * F.q[1][0] - k[1] * F.q[1][1] - k[2] * F.q[1][2] - k[3] * F.q[1][3];
+  }
+  const double* A = plus ? F.a[f] : F.b[f];
+  const double Ak = -(A[0] * k[1] + A[1] * k[2] + A[2] * k[3]);
+  const T c = T(Ak) / T(kq);
+  e[0] = -c * T(F.q[f][0]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) e[1 + i] = T(A[i]) - c * T(F.q[f][1 + i]);
 }
 
 }  // namespace bg
