@@ -361,8 +361,10 @@ bg_status bg_mixed_counts(bg_mixed* plan, int64_t* counts);
  * variants that compute the same sums in the same order -- bitwise identical
  * results -- and differ in how the work maps onto the GPU:
  *   BG_ALGO_CO (sampled helicities, n >= 6): 0 = one thread per ordering,
- *     1 = depth-first groups of six orderings sharing prefix currents
- *     (default); helicity sums and n < 6 have one variant;
+ *     1 = depth-first groups of six orderings sharing prefix currents in
+ *     blocks of 256 threads, 2 = the same in blocks of 128 (defaults: 2 for
+ *     n = 6, 7; 1 for n = 8, 9);
+ *     helicity sums and n < 6 have one variant;
  *   BG_ALGO_CD: (threads per event, unrolling of the partition loop):
  *     n <= 9: 0 = (128, 1), 1 = (256, 1), 2 = (128, 2), 3 = (256, 2);
  *     n >= 10: 0 = (256, 1), 1 = (384, 1), 2 = (512, 1), 3 = (256, 2),

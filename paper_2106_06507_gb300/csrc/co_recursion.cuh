@@ -340,9 +340,9 @@ cudaError_t launch_co_n(int64_t B, double sqrt_s, const double* p, const int8_t*
 // position once per choice of its gluon (3), and the last two columns once per
 // ordering (6).  At n = 8 this removes ~21 % of the arithmetic.
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, int NT_ = 256>
 struct CoDfsShape {
-  static constexpr int NT = 256;
+  static constexpr int NT = NT_;
   static constexpr int M = N - 1;
   static constexpr int K = ct_fact(N - 2);
   static constexpr int G = K / 6;                  // groups of six orderings
@@ -352,9 +352,9 @@ struct CoDfsShape {
   static constexpr int NPAIR = M * (M - 1) / 2;
 };
 
-template <int N, typename T>
+template <int N, typename T, int NT_ = 256>
 struct CoDfsSmem {
-  using S = CoDfsShape<N>;
+  using S = CoDfsShape<N, NT_>;
   static constexpr size_t off_pair = 0;                                                // double [EB][NPAIR]
   static constexpr size_t off_inv = off_pair + sizeof(double) * S::EB * S::NPAIR;      // T [EB][NMASK]
   static constexpr size_t off_k = off_inv + sizeof(T) * S::EB * S::NMASK;              // T [EB][N][4]
@@ -364,14 +364,14 @@ struct CoDfsSmem {
   static constexpr size_t bytes = off_p2 + sizeof(double) * S::EB * S::NMASK;
 };
 
-template <int N, typename T>
-__global__ void __launch_bounds__(256) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
+template <int N, typename T, int NT_>
+__global__ void __launch_bounds__(NT_) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
                                                      const double* __restrict__ p, const int8_t* __restrict__ hel,
                                                      PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
   // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
   const int64_t B = dB ? (*dB < S_ ? *dB : S_) : S_;
-  using S = CoDfsShape<N>;
-  using L = CoDfsSmem<N, T>;
+  using S = CoDfsShape<N, NT_>;
+  using L = CoDfsSmem<N, T, NT_>;
   constexpr int M = S::M, K = S::K, G = S::G, EB = S::EB, NT = S::NT;
   extern __shared__ __align__(16) unsigned char smem[];
   double* s_pair = reinterpret_cast<double*>(smem + L::off_pair);
@@ -559,12 +559,12 @@ __global__ void __launch_bounds__(256) co_kernel_dfs(int64_t S_, const int64_t* 
   }
 }
 
-template <int N, typename T>
+template <int N, typename T, int NT>
 cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
                           int* status, cudaStream_t s, const int64_t* dB) {
-  using S = CoDfsShape<N>;
-  using L = CoDfsSmem<N, T>;
-  auto kern = co_kernel_dfs<N, T>;
+  using S = CoDfsShape<N, NT>;
+  using L = CoDfsSmem<N, T, NT>;
+  auto kern = co_kernel_dfs<N, T, NT>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (err != cudaSuccess) return err;
   const PolFrame F = make_pol_frame(q);
@@ -574,20 +574,24 @@ cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_
 }
 
 // Variants (sampled helicities, n >= 6): 0 = one thread per ordering,
-// 1 = depth-first groups of six orderings (default).  The helicity sum and
-// n < 6 have one variant.
-inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 2 : 1; }
+// 1 = depth-first groups of six orderings in blocks of 256 threads, 2 = the
+// same in blocks of 128 threads (more resident blocks: the FP64 prologue of
+// one block overlaps the recursion of another).  Defaults (GB300 timings):
+// 2 for n = 6, 7; 1 for n = 8, 9.  The helicity sum and n < 6 have one
+// variant.
+inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 3 : 1; }
 
 template <typename T>
 cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
                         T* amps, int* status, cudaStream_t s, const int64_t* dB, int variant) {
   const bool sum = (hel == nullptr);
-  const bool dfs = !sum && n >= 6 && variant != 0;
-#define BG_CO_CASE(NN)                                                                                    \
-  case NN:                                                                                                \
-    return sum ? launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB)                     \
-               : (dfs ? launch_co_dfs<(NN >= 6 ? NN : 6), T>(B, sqrt_s, p, hel, q, amps, status, s, dB) \
-                      : launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB));
+  const int v = (sum || n < 6) ? 0 : (variant < 0 || variant > 2 ? (n <= 7 ? 2 : 1) : variant);
+#define BG_CO_CASE(NN)                                                                                   \
+  case NN:                                                                                               \
+    if (sum) return launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB);                \
+    if (v == 1) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 256>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
+    if (v == 2) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 128>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
+    return launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB);
   switch (n) {
     BG_CO_CASE(4)
     BG_CO_CASE(5)
