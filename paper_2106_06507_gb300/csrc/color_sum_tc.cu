@@ -144,6 +144,38 @@ __host__ __device__ constexpr uint32_t tile_off(int r, int k) {
   return (uint32_t)(((r >> 3) * (TC_KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// 16 amplitudes of one row from column m0 (zeros beyond k or for rows past
+// the batch).
+template <typename TIn>
+__device__ __forceinline__ void tc_load16(const TIn* row, bool live, int m0, int k, float (&x)[16]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = 0.0f;
+  if (!live || m0 >= k) return;
+  if (sizeof(TIn) == 4 && m0 + 16 <= k && (k & 3) == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float4 f = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(row) + m0 + 4 * v);
+      x[4 * v] = f.x, x[4 * v + 1] = f.y, x[4 * v + 2] = f.z, x[4 * v + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (m0 + j < k) x[j] = (float)row[m0 + j];
+  }
+}
+
+// The TC_KC amplitudes of K chunk kc of one row.
+template <typename TIn>
+__device__ __forceinline__ void tc_load_chunk(const TIn* row, bool live, int kc, int k, float (&x)[TC_KC]) {
+#pragma unroll
+  for (int g = 0; g < TC_KC / 16; ++g) {
+    float v[16];
+    tc_load16<TIn>(row, live, kc * TC_KC + g * 16, k, v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[g * 16 + j] = v[j];
+  }
+}
+
 struct TcParams {
   int64_t B;             // capacity
   const int64_t* dB;     // optional device-side event count
@@ -154,6 +186,41 @@ struct TcParams {
   double scale; // includes the gcd of C
   float g;      // gcd of C (Y = g D)
 };
+
+// Converter step `it` for row r: wait for stage it % 2 to be free, split the
+// FP32 amplitudes x into hi / mid / lo BF16 planes in the stage's canonical
+// layout, signal full_a.  Returns false if a wait gave up.
+__device__ __forceinline__ bool tc_convert_chunk(const float (&x)[TC_KC], int it, int r, unsigned char* stage_base,
+                                                 uint32_t stage_bytes, uint32_t a_plane_bytes, uint64_t* empty,
+                                                 uint64_t* full_a, int* status, volatile int* abort_flag) {
+  const int s = it & 1;
+  const uint32_t use = (uint32_t)(it >> 1);
+  if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) return false;
+  unsigned char* st = stage_base + s * stage_bytes;
+#pragma unroll
+  for (int g = 0; g < TC_KC / 8; ++g) {
+    uint32_t hi[4], mid[4], lo[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const float x0 = x[g * 8 + j], x1 = x[g * 8 + j + 1];
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      const float r0 = x0 - __bfloat162float(h0), r1 = x1 - __bfloat162float(h1);
+      const __nv_bfloat16 m0 = __float2bfloat16_rn(r0), m1 = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(r0 - __bfloat162float(m0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(r1 - __bfloat162float(m1));
+      hi[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      mid[j / 2] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+      lo[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    const uint32_t off = tile_off(r, g * 8);
+    *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(st + a_plane_bytes + off) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
+    *reinterpret_cast<uint4*>(st + 2 * a_plane_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+  fence_proxy_async();
+  mbar_arrive(&full_a[s]);
+  return true;
+}
 
 template <typename TIn, int CPL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -268,52 +335,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp < 6) {
     // ---------------- converters: FP32 -> hi/mid/lo BF16 planes ----------------
+    // The amplitudes of the next K chunk are loaded into registers before the
+    // current chunk is converted (and before waiting for a free stage), so
+    // the loads' latency overlaps the conversion and the MMAs.
     const int r = threadIdx.x - 64;  // row (event) of the tile, 0..127
     const int64_t e = e0 + r;
-    for (int it = 0; it < total; ++it) {
-      const int s = it & 1;
-      const uint32_t use = (uint32_t)(it >> 1);
-      if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) break;
-      const int kc = it % P.kchunks;
-      unsigned char* st = stage_base + s * stage_bytes;
-      const TIn* row = A + e * (int64_t)P.k;
-#pragma unroll 2
-      for (int g = 0; g < TC_KC / 8; ++g) {
-        const int kk = kc * TC_KC + g * 8;
-        float x[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = 0.0f;
-        if (e < P.B && kk < P.k) {
-          if (sizeof(TIn) == 4 && kk + 8 <= P.k) {
-            const float4 v0 = *reinterpret_cast<const float4*>(row + kk);
-            const float4 v1 = *reinterpret_cast<const float4*>(row + kk + 4);
-            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-            x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (kk + j < P.k) x[j] = (float)row[kk + j];
-          }
-        }
-        uint32_t hi[4], mid[4], lo[4];
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          const __nv_bfloat16 h0 = __float2bfloat16_rn(x[j]), h1 = __float2bfloat16_rn(x[j + 1]);
-          const float r0 = x[j] - __bfloat162float(h0), r1 = x[j + 1] - __bfloat162float(h1);
-          const __nv_bfloat16 m0 = __float2bfloat16_rn(r0), m1 = __float2bfloat16_rn(r1);
-          const __nv_bfloat16 l0 = __float2bfloat16_rn(r0 - __bfloat162float(m0));
-          const __nv_bfloat16 l1 = __float2bfloat16_rn(r1 - __bfloat162float(m1));
-          hi[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-          mid[j / 2] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
-          lo[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-        }
-        const uint32_t off = tile_off(r, g * 8);
-        *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(st + a_plane_bytes + off) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
-        *reinterpret_cast<uint4*>(st + 2 * a_plane_bytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
-      fence_proxy_async();
-      mbar_arrive(&full_a[s]);
+    const TIn* row = A + e * (int64_t)P.k;
+    float xa[TC_KC], xb[TC_KC];
+    tc_load_chunk<TIn>(row, e < P.B, 0, P.k, xa);
+    for (int it = 0; it < total; it += 2) {
+      if (it + 1 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 1) % P.kchunks, P.k, xb);
+      if (!tc_convert_chunk(xa, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag))
+        break;
+      if (it + 1 >= total) break;
+      if (it + 2 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 2) % P.kchunks, P.k, xa);
+      if (!tc_convert_chunk(xb, it + 1, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status,
+                            abort_flag))
+        break;
     }
   } else {
     // ---------------- epilogue: one event per thread ----------------
@@ -330,17 +368,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!__all_sync(0xffffffffu, ready)) break;
       tc_fence_after();
       float part = 0.0f;
+      float an[16];
+      tc_load16<TIn>(row, e < P.B, ntile * P.nt, P.k, an);
       for (int c0 = 0; c0 < P.nt; c0 += 16) {
+        float ac[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) ac[j] = an[j];
+        if (c0 + 16 < P.nt) tc_load16<TIn>(row, e < P.B, ntile * P.nt + c0 + 16, P.k, an);
         float d[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.nt + c0), d);
         const int m0 = ntile * P.nt + c0;
-        if (e < P.B) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) part = fmaf(ac[j], d[j], part);  // ac is 0 beyond k and B
+        if (Y && e < P.B) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (m0 + j < P.k) {
-              part = fmaf((float)row[m0 + j], d[j], part);
-              if (Y) Y[e * (int64_t)P.k + m0 + j] = (TIn)(P.g * d[j]);
-            }
+            if (m0 + j < P.k) Y[e * (int64_t)P.k + m0 + j] = (TIn)(P.g * d[j]);
         }
       }
       acc += (double)part;
