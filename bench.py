@@ -272,6 +272,12 @@ def run_ours(args) -> None:
     bg.lib()
 
     stream = torch.cuda.current_stream(dev)
+    f64 = args.precision == "f64"
+    prec = bg.BG_F64 if f64 else bg.BG_F32
+
+    def csm(n):
+        return bg.BG_CS_F64 if f64 else cs_mode_for(bg, n)
+
     # inputs: resident in HBM before the timed region; each rank its own events
     first = rank * BATCH
     U, HEL, P, ACC, AMPS, ME2, CM = {}, {}, {}, {}, {}, {}, {}
@@ -283,7 +289,8 @@ def run_ours(args) -> None:
         HEL[n] = torch.from_numpy(h).to(dev)
         P[n] = torch.empty((4, n, BATCH), dtype=torch.float64, device=dev)
         ACC[n] = torch.empty((BATCH,), dtype=torch.uint8, device=dev)
-        AMPS[n] = torch.empty((BATCH, 1, math.factorial(n - 2)), dtype=torch.float32, device=dev)
+        AMPS[n] = torch.empty((BATCH, 1, math.factorial(n - 2)), dtype=torch.float64 if f64 else torch.float32,
+                              device=dev)
         ME2[n] = torch.empty((BATCH,), dtype=torch.float64, device=dev)
         CM[n] = bg.ColourMatrix(n)
         h2d += u.nbytes + h.nbytes
@@ -299,10 +306,10 @@ def run_ours(args) -> None:
             bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
             if record:
                 ev[n][1].record(stream)
-            bg.currents_co(n, P[n], HEL[n], prec=bg.BG_F32, sqrt_s=SQRT_S, amps=AMPS[n], stream=stream)
+            bg.currents_co(n, P[n], HEL[n], prec=prec, sqrt_s=SQRT_S, amps=AMPS[n], stream=stream)
             if record:
                 ev[n][2].record(stream)
-            bg.color_sum(CM[n], AMPS[n], True, mode=cs_mode_for(bg, n), sqrt_s=SQRT_S, accept=ACC[n],
+            bg.color_sum(CM[n], AMPS[n], True, mode=csm(n), sqrt_s=SQRT_S, accept=ACC[n],
                          me2=ME2[n], stream=stream)
             if record:
                 ev[n][3].record(stream)
@@ -352,7 +359,7 @@ def run_ours(args) -> None:
     value = events / elapsed
 
     # e2e: the public plan API with HOST buffers, copies inside the timed region
-    plans = {n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=cs_mode_for(bg, n), hel_sampled=True)
+    plans = {n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=prec, cs_mode=csm(n), hel_sampled=True)
              for n in NS}
     host_u = {n: U[n].cpu().pin_memory() for n in NS}
     host_h = {n: HEL[n].cpu().pin_memory() for n in NS}
@@ -381,11 +388,13 @@ def run_ours(args) -> None:
     flops = canonical_recursion_flops(n_dom) * BATCH
     achieved = flops / dom_s / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    if f64:  # FP64 pipe: no unit count to quote; the FMA probe's measured rate
+        peak = probe_f64
     traffic = None
     executed = None
-    if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8:
+    if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
-    if NCU_EXECUTED["sources_sha1"] == sources_sha1() and n_dom == 8:
+    if NCU_EXECUTED["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64:
         ex = NCU_EXECUTED["flops_per_event"] * BATCH / dom_s / 1e12
         executed = {"achieved": ex, "frac": ex / (NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
                     "flops_per_event": NCU_EXECUTED["flops_per_event"],
@@ -398,10 +407,11 @@ def run_ours(args) -> None:
         line = {
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S,
                        "pt_min_gev": PT_MIN, "helicities": "sampled, weight 2^n",
-                       "precision": ("FP32 currents; colour sum on tcgen05 tensor cores (BF16x3 amplitude split, "
+                       "precision": ("FP64 currents and FP64 colour sum (CUDA cores)" if f64 else
+                                     "FP32 currents; colour sum on tcgen05 tensor cores (BF16x3 amplitude split, "
                                      "FP32 accumulate) for n=6..8, FP32 CUDA cores for n=5; "
                                      "FP64 Rambo/polarisations/per-event accumulation"),
                        "parallelism": f"replicas x{world}",
@@ -409,12 +419,14 @@ def run_ours(args) -> None:
             "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS},
             "kernel_ms_per_step": {f"n{n}": [round(x / args.steps, 4) for x in kernel_ms[n]] for n in NS},
             "kernel_share": {k: round(v, 4) for k, v in shares.items()},
-            "roofline": {"kernel": f"co_kernel_dfs<{n_dom},float> (colour-ordered recursion)", "bound": "alu",
+            "roofline": {"kernel": f"co_kernel_dfs<{n_dom},{'double' if f64 else 'float'}> (colour-ordered recursion)",
+                         "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "flops_per_launch": flops, "flops_model": "canonical (V3=65, V4=46, prop=12, final=7)",
                          "executed": executed,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts, max clock)",
+                         "peak_source": ("FP64 FMA probe (measured)" if f64 else
+                                         "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts, max clock)"),
                          "probe_fp32_tflops": probe_f32, "probe_fp64_tflops": probe_f64},
             "cpu_baseline": None,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -472,6 +484,18 @@ def timed_host(step, args, dev) -> float:
     return max_over_ranks(time.perf_counter() - w0, dev)
 
 
+def fma_probe_tflops(bg, prec, stream, dev, iters: int) -> float:
+    """Measured FMA-pipe rate (TFLOP/s) of the library's probe kernel."""
+    import torch
+    bg.probe_fma(prec, NUM_SMS * 8, 64, stream=stream)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    fl = bg.probe_fma(prec, NUM_SMS * 8, iters, stream=stream)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    return fl / (s0.elapsed_time(s1) * 1e-3) / 1e12
+
+
 def cd_dense_flops(n: int) -> int:
     """FLOPs per event of the colour-dressed recursion as implemented: every
     ordered partition (S1, S2) of every subset takes the dense 3x3x3 colour
@@ -513,18 +537,20 @@ def run_cd(args) -> None:
     from paper_2106_06507_gb300 import inputs
     world, rank, dev, bg = setup_gpu()
     stream = torch.cuda.current_stream(dev)
-    first = rank * BATCH
+    cd_prec = bg.BG_F64 if args.precision == "f64" else bg.BG_F32
+    batch = BATCH if args.precision == "f32" else BATCH >> 4  # FP64 on GB300 is ~1/64 of FP32
+    first = rank * batch
     U, HEL, COL, P, ACC, ME2 = {}, {}, {}, {}, {}, {}
     host = {}
     for n in CD_NS:
-        u = inputs.rambo_uniforms(n, BATCH, seed=SEED, first_event=first)
-        h = np.ascontiguousarray(inputs.helicities(n, BATCH, seed=SEED, first_event=first).T)
-        c = np.ascontiguousarray(inputs.adjoint_colours(n, BATCH, seed=SEED, first_event=first).T)
+        u = inputs.rambo_uniforms(n, batch, seed=SEED, first_event=first)
+        h = np.ascontiguousarray(inputs.helicities(n, batch, seed=SEED, first_event=first).T)
+        c = np.ascontiguousarray(inputs.adjoint_colours(n, batch, seed=SEED, first_event=first).T)
         U[n], HEL[n], COL[n] = (torch.from_numpy(x).to(dev) for x in (u, h, c))
         host[n] = tuple(torch.from_numpy(x).pin_memory() for x in (u, h, c))
-        P[n] = torch.empty((4, n, BATCH), dtype=torch.float64, device=dev)
-        ACC[n] = torch.empty((BATCH,), dtype=torch.uint8, device=dev)
-        ME2[n] = torch.empty((BATCH,), dtype=torch.float64, device=dev)
+        P[n] = torch.empty((4, n, batch), dtype=torch.float64, device=dev)
+        ACC[n] = torch.empty((batch,), dtype=torch.uint8, device=dev)
+        ME2[n] = torch.empty((batch,), dtype=torch.float64, device=dev)
     ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for n in CD_NS}
     kernel_ms = {n: [0.0, 0.0] for n in CD_NS}
 
@@ -535,13 +561,13 @@ def run_cd(args) -> None:
             bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
             if record:
                 ev[n][1].record(stream)
-            bg.currents_cd(n, P[n], HEL[n], COL[n], prec=bg.BG_F32, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
+            bg.currents_cd(n, P[n], HEL[n], COL[n], prec=cd_prec, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
                            stream=stream)
             if record:
                 ev[n][2].record(stream)
 
     elapsed, clk = timed_steps(step, args, dev, stream)
-    value = world * len(CD_NS) * BATCH * args.steps / elapsed
+    value = world * len(CD_NS) * batch * args.steps / elapsed
     for _ in range(args.steps):  # per-kernel times (separate pass)
         step(True)
         torch.cuda.synchronize(dev)
@@ -549,7 +575,7 @@ def run_cd(args) -> None:
             for j in range(2):
                 kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1]) / args.steps
     ref = {n: ME2[n].cpu() for n in CD_NS}
-    out_h = {n: torch.empty((BATCH,), dtype=torch.float64).pin_memory() for n in CD_NS}
+    out_h = {n: torch.empty((batch,), dtype=torch.float64).pin_memory() for n in CD_NS}
     d_in = {n: tuple(torch.empty_like(x, device=dev) for x in host[n]) for n in CD_NS}
 
     def e2e_step():
@@ -557,7 +583,7 @@ def run_cd(args) -> None:
             for dst, src in zip(d_in[n], host[n]):
                 dst.copy_(src, non_blocking=True)
             bg.momenta_rambo(n, d_in[n][0], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
-            bg.currents_cd(n, P[n], d_in[n][1], d_in[n][2], prec=bg.BG_F32, sqrt_s=SQRT_S, accept=ACC[n],
+            bg.currents_cd(n, P[n], d_in[n][1], d_in[n][2], prec=cd_prec, sqrt_s=SQRT_S, accept=ACC[n],
                            me2=ME2[n], stream=stream)
             out_h[n].copy_(ME2[n], non_blocking=True)
 
@@ -571,25 +597,30 @@ def run_cd(args) -> None:
     flops = cd_dense_flops(n_dom) * accepted
     achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    if cd_prec == bg.BG_F64:
+        peak, peak_source = fma_probe_tflops(bg, bg.BG_F64, stream, dev, 500), "FP64 FMA probe (measured)"
     if rank == 0:
         print(json.dumps({
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": ("colour-dressed BG with sampled adjoint colours (1..8), n=8,10,12, 2^20 Rambo "
-                                    "points per n at sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, FP32 currents"),
-                       "n": list(CD_NS), "batch_per_n": BATCH, "parallelism": f"replicas x{world}",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": ("colour-dressed BG with sampled adjoint colours (1..8), n=8,10,12, "
+                                    f"{batch} Rambo points per n at sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, "
+                                    f"{args.precision.upper()} currents"),
+                       "n": list(CD_NS), "batch_per_n": batch, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2"},
-            "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) * 1e-3) for n in CD_NS},
+            "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in CD_NS},
             "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in CD_NS},
-            "roofline": {"kernel": f"cd_kernel<{n_dom},float>", "bound": "alu", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": f"cd_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
+                         "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "flops_model": "dense 3x3x3 colour products per ordered partition (56 FMA per "
                                         "(r,l,c), 4 per (r,l)) x events passing the cut",
                          "flops_per_event": cd_dense_flops(n_dom), "events_computed": accepted,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
-            "e2e": {"value": world * len(CD_NS) * BATCH * args.steps / e2e_s, "unit": "events/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(CD_NS) * BATCH * 8},
+                         "peak_source": peak_source},
+            "e2e": {"value": world * len(CD_NS) * batch * args.steps / e2e_s, "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(CD_NS) * batch * 8},
             "gpu_launches": 2 * len(CD_NS) * args.steps, "clocks": clk}), flush=True)
     finish_gpu(world)
 
@@ -774,6 +805,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed"), default="co")
+    ap.add_argument("--precision", choices=("f32", "f64"), default="f32",
+                    help="recursion arithmetic of the co and cd workloads (f64: the plain FP64 GPU form)")
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling case: run only multiplicity n (warm-up steps, then one step)")
     ap.add_argument("--profile-batch", type=int, default=1 << 16)
