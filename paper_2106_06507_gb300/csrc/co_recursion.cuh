@@ -364,8 +364,8 @@ struct CoDfsSmem {
   static constexpr size_t bytes = off_p2 + sizeof(double) * S::EB * S::NMASK;
 };
 
-template <int N, typename T, int NT_>
-__global__ void __launch_bounds__(NT_) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
+template <int N, typename T, int NT_, int MINB_ = 1>
+__global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
                                                      const double* __restrict__ p, const int8_t* __restrict__ hel,
                                                      PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
   // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
@@ -559,12 +559,12 @@ __global__ void __launch_bounds__(NT_) co_kernel_dfs(int64_t S_, const int64_t* 
   }
 }
 
-template <int N, typename T, int NT>
+template <int N, typename T, int NT, int MINB = 1>
 cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
                           int* status, cudaStream_t s, const int64_t* dB) {
   using S = CoDfsShape<N, NT>;
   using L = CoDfsSmem<N, T, NT>;
-  auto kern = co_kernel_dfs<N, T, NT>;
+  auto kern = co_kernel_dfs<N, T, NT, MINB>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (err != cudaSuccess) return err;
   const PolFrame F = make_pol_frame(q);
@@ -576,21 +576,23 @@ cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_
 // Variants (sampled helicities, n >= 6): 0 = one thread per ordering,
 // 1 = depth-first groups of six orderings in blocks of 256 threads, 2 = the
 // same in blocks of 128 threads (more resident blocks: the FP64 prologue of
-// one block overlaps the recursion of another).  Defaults (GB300 timings):
-// 2 for n = 6, 7; 1 for n = 8, 9.  The helicity sum and n < 6 have one
-// variant.
-inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 3 : 1; }
+// one block overlaps the recursion of another), 3 = 128-thread blocks with
+// registers capped for three resident blocks per SM.  Defaults (GB300
+// timings): 2 for n = 6, 7; 1 for n = 8, 9.  The helicity sum and n < 6 have
+// one variant.
+inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 4 : 1; }
 
 template <typename T>
 cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
                         T* amps, int* status, cudaStream_t s, const int64_t* dB, int variant) {
   const bool sum = (hel == nullptr);
-  const int v = (sum || n < 6) ? 0 : (variant < 0 || variant > 2 ? (n <= 7 ? 2 : 1) : variant);
+  const int v = (sum || n < 6) ? 0 : (variant < 0 || variant > 3 ? (n <= 7 ? 2 : 1) : variant);
 #define BG_CO_CASE(NN)                                                                                   \
   case NN:                                                                                               \
     if (sum) return launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB);                \
     if (v == 1) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 256>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
     if (v == 2) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 128>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
+    if (v == 3) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 128, 3>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
     return launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB);
   switch (n) {
     BG_CO_CASE(4)

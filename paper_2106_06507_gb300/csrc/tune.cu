@@ -3,8 +3,9 @@
 // Variants compute the same sums in the same order (bitwise identical
 // results) and differ only in how the work maps onto the GPU:
 //   colour-ordered recursion, sampled helicities, n >= 6:
-//     0 = one thread per ordering, 1 / 2 = depth-first groups of six
-//     orderings in blocks of 256 / 128 threads;
+//     0 = one thread per ordering, 1 / 2 / 3 = depth-first groups of six
+//     orderings in blocks of 256 / 128 / 128 threads (3: registers capped
+//     for three resident blocks);
 //   colour-dressed recursion: threads per event (CTA size) and unrolling of
 //     the partition loop, see cd_variant_threads() in cd_recursion.cuh.
 // bg_autotune times every variant on a synthetic probe batch (Rambo points
