@@ -343,6 +343,10 @@ def run_ours(args) -> None:
 
     probe_f32 = probe(bg.BG_F32, 20000)
     probe_f64 = probe(bg.BG_F64, 500)
+    # kernel variants of the recursion chosen by the library's autotuner on
+    # this GPU (they give bitwise identical results)
+    probe_batch = (1 << 14) if f64 else (1 << 18)
+    tuned = {n: bg.autotune(bg.BG_ALGO_CO, n, prec, probe_batch=probe_batch, stream=stream)[0] for n in NS if n >= 6}
 
     for _ in range(args.warmup):
         step_overlap()
@@ -414,9 +418,10 @@ def run_ours(args) -> None:
         peak = probe_f64
     traffic = None
     executed = None
-    if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64:
+    dfs = tuned.get(n_dom, 0) != 0  # the ncu figures are for the depth-first kernel
+    if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64 and dfs:
         traffic = NCU_TRAFFIC["bytes_per_launch"]
-    if NCU_EXECUTED["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64:
+    if NCU_EXECUTED["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64 and dfs:
         ex = NCU_EXECUTED["flops_per_event"] * BATCH / dom_s / 1e12
         executed = {"achieved": ex, "frac": ex / (NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
                     "flops_per_event": NCU_EXECUTED["flops_per_event"],
@@ -437,13 +442,15 @@ def run_ours(args) -> None:
                                      "FP32 accumulate) for n=6..8, FP32 CUDA cores for n=5; "
                                      "FP64 Rambo/polarisations/per-event accumulation"),
                        "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB of uniforms per step"},
+                       "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB of uniforms per step",
+                       "tuned_variants": {str(n): v for n, v in tuned.items()}},
             "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS},
             "kernel_ms_per_step": {f"n{n}": [round(x / args.steps, 4) for x in kernel_ms[n]] for n in NS},
             "schedule": ("Rambo for all n on a side stream ahead of the recursions and colour sums (FP64 and FP32 "
                          "pipes overlap); kernel_ms_per_step and kernel_share from the same step serialised"),
             "kernel_share": {k: round(v, 4) for k, v in shares.items()},
-            "roofline": {"kernel": f"co_kernel_dfs<{n_dom},{'double' if f64 else 'float'}> (colour-ordered recursion)",
+            "roofline": {"kernel": (f"{'co_kernel_dfs' if dfs else 'co_kernel'}<{n_dom},{'double' if f64 else 'float'}> "
+                                    f"(colour-ordered recursion, tuned variant {tuned.get(n_dom, 0)})"),
                          "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": traffic,
