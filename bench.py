@@ -60,11 +60,11 @@ WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqr
 # DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
 # n = 8, 2^20 events, scaled from a 2^16-event capture by the number of
 # events), valid only for the kernel sources it was taken from.
-NCU_TRAFFIC = {"sources_sha1": "26948e27eb69d07443bf1c523ff3895a48247928",
-               "bytes_per_launch": 16 * (17387520 + 127755520)}  # 2^16-event capture x 16
+NCU_TRAFFIC = {"sources_sha1": "7ba9df895bf416125976c8bd21337f52a2f68f02",
+               "bytes_per_launch": 16 * (17532160 + 127553280)}  # 2^16-event capture x 16
 # Executed FP32 operations per event of the dominant kernel at n = 8 (ncu sass
 # counts of the same capture: 2 x FFMA + FADD + FMUL), valid for the same sources.
-NCU_EXECUTED = {"sources_sha1": "26948e27eb69d07443bf1c523ff3895a48247928", "flops_per_event": 2524693}
+NCU_EXECUTED = {"sources_sha1": "7ba9df895bf416125976c8bd21337f52a2f68f02", "flops_per_event": 2524693}
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
 
