@@ -199,6 +199,17 @@ int64_t bg_plan_workspace_bytes(const bg_plan* plan);
 bg_status bg_me2_batch(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const int8_t* colors,
                        double* me2, void* stream);
 
+/* bg_me2_batch_async -- as bg_me2_batch, but it never waits: every copy and
+ * kernel is enqueued on `stream` and the call returns.  With PINNED host
+ * buffers the copies are asynchronous, so that calls of several plans on
+ * several streams overlap their host<->device transfers with each other's
+ * kernels; |M|^2 in a host `me2` is valid once `stream` has completed (for
+ * example after cudaStreamSynchronize).  Host buffers must stay unchanged
+ * and alive until then.  (Pageable host buffers work too, but their copies
+ * are synchronous with the host.)  Errors: as bg_me2_batch. */
+bg_status bg_me2_batch_async(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, double* me2,
+                             void* stream);
+
 /* ---------------------------------------------------------------------------
  * bg_me2_batch_noalloc -- the same pipeline as bg_me2_batch (Rambo -> cut ->
  * polarisations -> colour-ordered recursion -> colour sum) for callers that

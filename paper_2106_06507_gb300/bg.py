@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         L.bg_plan_workspace_bytes.argtypes = [vp]
         L.bg_plan_workspace_bytes.restype = c_i64
         L.bg_me2_batch.argtypes = [vp, c_i64, vp, vp, vp, vp, vp]
+        L.bg_me2_batch_async.argtypes = [vp, c_i64, vp, vp, vp, vp]
         L.bg_me2_grad.argtypes = [vp, c_i64, vp, vp, vp, vp, vp, vp]
         L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
@@ -101,7 +102,7 @@ def lib() -> ctypes.CDLL:
         L.bg_device_status_reset.argtypes = []
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
-                     "bg_plan_create", "bg_me2_batch", "bg_probe_fma", "bg_cd_workspace_bytes",
+                     "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_probe_fma", "bg_cd_workspace_bytes",
                      "bg_currents_cd", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
                      "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
                      "bg_tune_load"):
@@ -270,14 +271,18 @@ class Plan:
     def workspace_bytes(self) -> int:
         return int(lib().bg_plan_workspace_bytes(self._h))
 
-    def me2(self, u, hel=None, colors=None, out=None, stream=None):
+    def me2(self, u, hel=None, colors=None, out=None, stream=None, wait=True):
         """u [B, 4(n-2)] float64, hel [n, B] int8 (device or host tensors or
         numpy arrays) -> me2 [B] float64 (on the device of `out`, or a new
-        CUDA tensor if out is None)."""
+        CUDA tensor if out is None).  wait=False: bg_me2_batch_async (a host
+        `out` is valid after the stream completes; use pinned buffers)."""
         B = u.shape[0]
         if out is None:
             out = torch.empty((B,), dtype=torch.float64, device="cuda")
-        _check(lib().bg_me2_batch(self._h, B, _vptr(u), _vptr(hel), _vptr(colors), _vptr(out), _stream(stream)))
+        if wait:
+            _check(lib().bg_me2_batch(self._h, B, _vptr(u), _vptr(hel), _vptr(colors), _vptr(out), _stream(stream)))
+        else:
+            _check(lib().bg_me2_batch_async(self._h, B, _vptr(u), _vptr(hel), _vptr(out), _stream(stream)))
         return out
 
     def grad(self, u: torch.Tensor, hel: torch.Tensor, upstream: torch.Tensor | None = None,

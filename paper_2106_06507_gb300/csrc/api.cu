@@ -364,9 +364,10 @@ bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
   return BG_OK;
 }
 
-bg_status bg_me2_batch(bg_plan* P, int64_t B, const double* u, const int8_t* hel, const int8_t* colors,
-                       double* me2, void* stream) {
-  (void)colors;
+// The whole path for one plan; `sync`: wait for a host output before
+// returning (bg_me2_batch) or not (bg_me2_batch_async).
+static bg_status me2_batch_impl(bg_plan* P, int64_t B, const double* u, const int8_t* hel, double* me2,
+                                void* stream, bool sync) {
   if (!P) return fail(BG_EINVAL, "bg_me2_batch: plan is NULL");
   if (B < 0 || B > P->d.max_batch) return fail(BG_EINVAL, "bg_me2_batch: B outside 0..max_batch");
   if (B == 0) return BG_OK;
@@ -403,9 +404,19 @@ bg_status bg_me2_batch(bg_plan* P, int64_t B, const double* u, const int8_t* hel
     st = cuda_check(cudaMemcpyAsync(me2, md, (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, s),
                     "bg_me2_batch: copy me2");
     if (st != BG_OK) return st;
-    st = cuda_check(cudaStreamSynchronize(s), "bg_me2_batch: synchronise");
+    if (sync) st = cuda_check(cudaStreamSynchronize(s), "bg_me2_batch: synchronise");
   }
   return st;
+}
+
+bg_status bg_me2_batch(bg_plan* P, int64_t B, const double* u, const int8_t* hel, const int8_t* colors,
+                       double* me2, void* stream) {
+  (void)colors;
+  return me2_batch_impl(P, B, u, hel, me2, stream, true);
+}
+
+bg_status bg_me2_batch_async(bg_plan* P, int64_t B, const double* u, const int8_t* hel, double* me2, void* stream) {
+  return me2_batch_impl(P, B, u, hel, me2, stream, false);
 }
 
 bg_status bg_me2_grad(bg_plan* P, int64_t B, const double* u, const int8_t* hel, const double* upstream,

@@ -86,3 +86,29 @@ def test_plan_errors(bg):
     assert ei.value.code == bg.BG_EINVAL
     assert plan.workspace_bytes > 0
     plan.close()
+
+
+def test_plan_async_host_buffers_on_streams(bg):
+    # bg_me2_batch_async with pinned host buffers on several streams gives
+    # the same |M|^2 as the synchronous call
+    import torch
+    res = []
+    plans, hosts, outs, streams = [], [], [], []
+    for n in (6, 7):
+        B = 2000
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=60 + n)).pin_memory()
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=60 + n).T)).pin_memory()
+        plan = bg.Plan(n, B, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_TC_BF16, hel_sampled=True)
+        ref = plan.me2(u, h, out=torch.empty(B, dtype=torch.float64).pin_memory())
+        res.append(ref.clone())
+        plans.append(plan)
+        hosts.append((u, h))
+        outs.append(torch.full((B,), -1.0, dtype=torch.float64).pin_memory())
+        streams.append(torch.cuda.Stream())
+    for plan, (u, h), out, st in zip(plans, hosts, outs, streams):
+        plan.me2(u, h, out=out, stream=st, wait=False)
+    for st in streams:
+        st.synchronize()
+    for ref, out, plan in zip(res, outs, plans):
+        assert torch.equal(ref, out)
+        plan.close()
