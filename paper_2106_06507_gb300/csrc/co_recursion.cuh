@@ -98,6 +98,27 @@ __device__ __forceinline__ void co_inverse_table(const double* __restrict__ s_pa
   __syncthreads();
 }
 
+// y[m] = fma(a, x[m], y[m]) for the four components; in FP32 as two packed
+// f32x2 FMAs (same per-component arithmetic, half the instructions).
+template <typename T>
+__device__ __forceinline__ void axpy4(T a, const T (&x)[4], T (&y)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) y[m] = fma(a, x[m], y[m]);
+}
+template <>
+__device__ __forceinline__ void axpy4<float>(float a, const float (&x)[4], float (&y)[4]) {
+  unsigned long long aa, x01, x23, y01, y23;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(aa) : "f"(a));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x01) : "f"(x[0]), "f"(x[1]));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x23) : "f"(x[2]), "f"(x[3]));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y01) : "f"(y[0]), "f"(y[1]));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y23) : "f"(y[2]), "f"(y[3]));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(y01) : "l"(aa), "l"(x01));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(y23) : "l"(aa), "l"(x23));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(y[0]), "=f"(y[1]) : "l"(y01));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(y[2]), "=f"(y[3]) : "l"(y23));
+}
+
 // Bracket of segment (i..j) of one ordering (the V3 and V4 sums before the
 // propagator); i and j are compile-time after unrolling.  J[a][b] hold the
 // currents of the shorter segments, Sp[p] the prefix sums of the ordered
@@ -120,8 +141,7 @@ __device__ __forceinline__ void co_bracket(const T (&J)[N - 1][N - 1][4], const 
     const T px = mdot(P2, J[i][s]);
     const T py = mdot(P2, J[s + 1][j]);
     sxy += xy;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) W[m] = fma(xy, Sp[s + 1][m], W[m]);
+    axpy4(xy, Sp[s + 1], W);
     cX[s] = -py;
     cR[s] = px;
   }
@@ -134,14 +154,13 @@ __device__ __forceinline__ void co_bracket(const T (&J)[N - 1][N - 1][4], const 
       const T yz = mdot(J[s + 1][t], J[t + 1][j]);
       cX[s] -= yz;
       cR[t] -= xy;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) by[m] = fma(xz, J[s + 1][t][m], by[m]);
+      axpy4(xz, J[s + 1][t], by);
     }
   }
 #pragma unroll
   for (int s = i; s < j; ++s) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) br[m] = fma(cX[s], J[i][s][m], fma(cR[s], J[s + 1][j][m], br[m]));
+    axpy4(cR[s], J[s + 1][j], br);
+    axpy4(cX[s], J[i][s], br);
   }
 #pragma unroll
   for (int m = 0; m < 4; ++m) br[m] += T(2) * (W[m] + by[m]) - sxy * (Sp[i][m] + Sp[j + 1][m]);
