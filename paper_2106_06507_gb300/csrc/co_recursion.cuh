@@ -119,6 +119,56 @@ __device__ __forceinline__ void axpy4<float>(float a, const float (&x)[4], float
   asm("mov.b64 {%0, %1}, %2;" : "=f"(y[2]), "=f"(y[3]) : "l"(y23));
 }
 
+// Component-wise helpers of the same shape: z = x + y, z = x - y, z = a x.
+template <typename T>
+__device__ __forceinline__ void add4(const T (&x)[4], const T (&y)[4], T (&z)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) z[m] = x[m] + y[m];
+}
+template <typename T>
+__device__ __forceinline__ void sub4(const T (&x)[4], const T (&y)[4], T (&z)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) z[m] = x[m] - y[m];
+}
+template <typename T>
+__device__ __forceinline__ void scale4(T a, const T (&x)[4], T (&z)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) z[m] = a * x[m];
+}
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+template <>
+__device__ __forceinline__ void add4<float>(const float (&x)[4], const float (&y)[4], float (&z)[4]) {
+  unsigned long long a = pk2(x[0], x[1]), b = pk2(x[2], x[3]);
+  asm("add.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(pk2(y[0], y[1])));
+  asm("add.rn.f32x2 %0, %0, %1;" : "+l"(b) : "l"(pk2(y[2], y[3])));
+  upk2(a, z[0], z[1]);
+  upk2(b, z[2], z[3]);
+}
+template <>
+__device__ __forceinline__ void sub4<float>(const float (&x)[4], const float (&y)[4], float (&z)[4]) {
+  unsigned long long a = pk2(x[0], x[1]), b = pk2(x[2], x[3]);
+  asm("sub.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(pk2(y[0], y[1])));
+  asm("sub.rn.f32x2 %0, %0, %1;" : "+l"(b) : "l"(pk2(y[2], y[3])));
+  upk2(a, z[0], z[1]);
+  upk2(b, z[2], z[3]);
+}
+template <>
+__device__ __forceinline__ void scale4<float>(float s, const float (&x)[4], float (&z)[4]) {
+  unsigned long long a = pk2(x[0], x[1]), b = pk2(x[2], x[3]);
+  const unsigned long long ss = pk2(s, s);
+  asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(a) : "l"(ss));
+  asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(b) : "l"(ss));
+  upk2(a, z[0], z[1]);
+  upk2(b, z[2], z[3]);
+}
+
 // Bracket of segment (i..j) of one ordering (the V3 and V4 sums before the
 // propagator); i and j are compile-time after unrolling.  J[a][b] hold the
 // currents of the shorter segments, Sp[p] the prefix sums of the ordered
@@ -128,8 +178,8 @@ __device__ __forceinline__ void co_bracket(const T (&J)[N - 1][N - 1][4], const 
                                            const int j, T (&br)[4]) {
   constexpr int M = N - 1;
   T P2[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) P2[m] = T(2) * (Sp[j + 1][m] - Sp[i][m]);
+  sub4(Sp[j + 1], Sp[i], P2);
+  scale4(T(2), P2, P2);
   T by[4], W[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) { br[m] = T(0); by[m] = T(0); W[m] = T(0); }
@@ -162,8 +212,13 @@ __device__ __forceinline__ void co_bracket(const T (&J)[N - 1][N - 1][4], const 
     axpy4(cR[s], J[s + 1][j], br);
     axpy4(cX[s], J[i][s], br);
   }
-#pragma unroll
-  for (int m = 0; m < 4; ++m) br[m] += T(2) * (W[m] + by[m]) - sxy * (Sp[i][m] + Sp[j + 1][m]);
+  // br += 2 (W + by) - sxy (S_i + S_{j+1})
+  T t[4], u[4];
+  add4(W, by, t);
+  add4(Sp[i], Sp[j + 1], u);
+  add4(t, t, t);
+  axpy4(-sxy, u, t);
+  add4(br, t, br);
 }
 
 // Recursion for one ordering; J[i][i] hold the external currents in colour
@@ -184,8 +239,7 @@ __device__ __forceinline__ T co_recursion(T (&J)[N - 1][N - 1][4], const T (&Sp)
       co_bracket<N, T>(J, Sp, i, j, br);
       if (len < M) {
         const T ip = inv[msk[j + 1] ^ msk[i]];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) J[i][j][m] = br[m] * ip;
+        scale4(ip, br, J[i][j]);
       } else {
         amp = mdot(en, br);
       }
@@ -510,8 +564,7 @@ __global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const in
         T br[4];
         co_bracket<N, T>(J, Sp, i, j, br);
         const T ip = inv[msk[j + 1] ^ msk[i]];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) J[i][j][m] = br[m] * ip;
+        scale4(ip, br, J[i][j]);
       }
     }
     T* out = amps + (e * (int64_t)K + 6 * gi);
@@ -533,8 +586,7 @@ __global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const in
           T br[4];
           co_bracket<N, T>(J, Sp, i, P, br);
           const T ip = inv[msk[P + 1] ^ msk[i]];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) J[i][P][m] = br[m] * ip;
+          scale4(ip, br, J[i][P]);
         }
       }
 #pragma unroll 1
@@ -556,8 +608,7 @@ __global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const in
           T br[4];
           co_bracket<N, T>(J, Sp, i, P, br);
           const T ip = inv[msk[P + 1] ^ msk[i]];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) J[i][P][m] = br[m] * ip;
+          scale4(ip, br, J[i][P]);
         }
         T amp = T(0);
 #pragma unroll
@@ -566,8 +617,7 @@ __global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const in
           co_bracket<N, T>(J, Sp, i, P + 1, br);
           if (i > 0) {
             const T ip = inv[msk[P + 2] ^ msk[i]];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) J[i][P + 1][m] = br[m] * ip;
+            scale4(ip, br, J[i][P + 1]);
           } else {
             amp = mdot(en, br);
           }
