@@ -52,6 +52,30 @@ struct GradSmem {
   static constexpr size_t bytes = off_ord + sizeof(int) * S::K;
 };
 
+// acc += g o (a x + b z), g = (1, -1, -1, -1) component-wise (the metric
+// applied to a gradient), as packed operations in FP32.
+template <typename T>
+__device__ __forceinline__ void gaxpby4(T a, const T (&x)[4], T b, const T (&z)[4], T (&acc)[4]) {
+  T t[4];
+  scale4(b, z, t);
+  axpy4(a, x, t);
+  const T gm[4] = {T(1), T(-1), T(-1), T(-1)};
+#pragma unroll
+  for (int m = 0; m < 4; ++m) acc[m] = fma(gm[m], t[m], acc[m]);
+}
+template <>
+__device__ __forceinline__ void gaxpby4<float>(float a, const float (&x)[4], float b, const float (&z)[4],
+                                               float (&acc)[4]) {
+  float t[4];
+  scale4(b, z, t);
+  axpy4(a, x, t);
+  unsigned long long a01 = pk2(acc[0], acc[1]), a23 = pk2(acc[2], acc[3]);
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a01) : "l"(pk2(1.0f, -1.0f)), "l"(pk2(t[0], t[1])));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a23) : "l"(pk2(-1.0f, -1.0f)), "l"(pk2(t[2], t[3])));
+  upk2(a01, acc[0], acc[1]);
+  upk2(a23, acc[2], acc[3]);
+}
+
 // Forward sweep: all currents of one ordering in registers (J[i][i] hold the
 // polarisations); returns the top bracket (the amplitude is en . brtop).
 template <int N, typename T>
@@ -153,19 +177,19 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
         for (int m = 0; m < 4; ++m) {
           a = fma(bb[m], J[i][s][m], a);
           b = fma(bb[m], J[s + 1][j][m], b);
-          Jb[i][s][m] = fma(cX[s], bb[m], Jb[i][s][m]);
-          Jb[s + 1][j][m] = fma(cR[s], bb[m], Jb[s + 1][j][m]);
         }
+        axpy4(cX[s], bb, Jb[i][s]);
+        axpy4(cR[s], bb, Jb[s + 1][j]);
         cXb[s] = a;
         cRb[s] = b;
       }
       T sxyb = T(0);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        sxyb = fma(-bb[m], Sp[i][m] + Sp[j + 1][m], sxyb);
-        Sb[i][m] = fma(-sxy, bb[m], Sb[i][m]);
-        Sb[j + 1][m] = fma(-sxy, bb[m], Sb[j + 1][m]);
-      }
+      for (int m = 0; m < 4; ++m) sxyb = fma(-bb[m], Sp[i][m] + Sp[j + 1][m], sxyb);
+      axpy4(-sxy, bb, Sb[i]);
+      axpy4(-sxy, bb, Sb[j + 1]);
+      T bb2[4];
+      add4(bb, bb, bb2);  // 2 bb
       // V4: cX_s -= Y.Z, cR_t -= X.Y, by += (X.Z) Y with by_bar = 2 bb
 #pragma unroll
       for (int s = i; s < j; ++s)
@@ -176,13 +200,11 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
           const T xyb = -cRb[t];
           T xzb = T(0);
 #pragma unroll
-          for (int m = 0; m < 4; ++m) xzb = fma(T(2) * bb[m], J[s + 1][t][m], xzb);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            Jb[i][s][m] += gm[m] * (xzb * J[t + 1][j][m] + xyb * J[s + 1][t][m]);
-            Jb[t + 1][j][m] += gm[m] * (xzb * J[i][s][m] + yzb * J[s + 1][t][m]);
-            Jb[s + 1][t][m] += T(2) * xz * bb[m] + gm[m] * (xyb * J[i][s][m] + yzb * J[t + 1][j][m]);
-          }
+          for (int m = 0; m < 4; ++m) xzb = fma(bb2[m], J[s + 1][t][m], xzb);
+          gaxpby4(xzb, J[t + 1][j], xyb, J[s + 1][t], Jb[i][s]);
+          gaxpby4(xzb, J[i][s], yzb, J[s + 1][t], Jb[t + 1][j]);
+          axpy4(xz, bb2, Jb[s + 1][t]);
+          gaxpby4(xyb, J[i][s], yzb, J[t + 1][j], Jb[s + 1][t]);
         }
       // V3: xy_s enters sxy and W = sum_s xy_s S_{s+1}; cR_s = P2.X_s, cX_s = -P2.Y_s
       T P2b[4] = {T(0), T(0), T(0), T(0)};
@@ -190,24 +212,16 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
       for (int s = i; s < j; ++s) {
         T xyb = sxyb;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          xyb = fma(T(2) * bb[m], Sp[s + 1][m], xyb);
-          Sb[s + 1][m] = fma(xy[s], T(2) * bb[m], Sb[s + 1][m]);
-        }
+        for (int m = 0; m < 4; ++m) xyb = fma(bb2[m], Sp[s + 1][m], xyb);
+        axpy4(xy[s], bb2, Sb[s + 1]);
         const T pxb = cRb[s];
         const T pyb = -cXb[s];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          Jb[i][s][m] += gm[m] * (xyb * J[s + 1][j][m] + pxb * P2[m]);
-          Jb[s + 1][j][m] += gm[m] * (xyb * J[i][s][m] + pyb * P2[m]);
-          P2b[m] += gm[m] * (pxb * J[i][s][m] + pyb * J[s + 1][j][m]);
-        }
+        gaxpby4(xyb, J[s + 1][j], pxb, P2, Jb[i][s]);
+        gaxpby4(xyb, J[i][s], pyb, P2, Jb[s + 1][j]);
+        gaxpby4(pxb, J[i][s], pyb, J[s + 1][j], P2b);
       }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        Sb[j + 1][m] = fma(T(2), P2b[m], Sb[j + 1][m]);
-        Sb[i][m] = fma(T(-2), P2b[m], Sb[i][m]);
-      }
+      axpy4(T(2), P2b, Sb[j + 1]);
+      axpy4(T(-2), P2b, Sb[i]);
     }
   }
 }
