@@ -76,6 +76,25 @@ __device__ __forceinline__ void gaxpby4<float>(float a, const float (&x)[4], flo
   upk2(a23, acc[2], acc[3]);
 }
 
+// Euclidean dot product sum_m x[m] y[m] (no metric); in FP32 as one packed
+// multiply, one packed FMA and an add.
+template <typename T>
+__device__ __forceinline__ T edot4(const T (&x)[4], const T (&y)[4]) {
+  T r = T(0);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) r = fma(x[m], y[m], r);
+  return r;
+}
+template <>
+__device__ __forceinline__ float edot4<float>(const float (&x)[4], const float (&y)[4]) {
+  unsigned long long p;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(p) : "l"(pk2(x[0], x[1])), "l"(pk2(y[0], y[1])));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(p) : "l"(pk2(x[2], x[3])), "l"(pk2(y[2], y[3])));
+  float a, b;
+  upk2(p, a, b);
+  return a + b;
+}
+
 // Forward sweep: all currents of one ordering in registers (J[i][i] hold the
 // polarisations); returns the top bracket (the amplitude is en . brtop).
 template <int N, typename T>
@@ -172,12 +191,8 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
       // bracket = sum_s (cX_s X_s + cR_s Y_s) + 2 W + 2 by - sxy (S_i + S_{j+1})
 #pragma unroll
       for (int s = i; s < j; ++s) {
-        T a = T(0), b = T(0);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          a = fma(bb[m], J[i][s][m], a);
-          b = fma(bb[m], J[s + 1][j][m], b);
-        }
+        const T a = edot4(bb, J[i][s]);
+        const T b = edot4(bb, J[s + 1][j]);
         axpy4(cX[s], bb, Jb[i][s]);
         axpy4(cR[s], bb, Jb[s + 1][j]);
         cXb[s] = a;
@@ -198,9 +213,7 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
           const T xz = mdot(J[i][s], J[t + 1][j]);
           const T yzb = -cXb[s];
           const T xyb = -cRb[t];
-          T xzb = T(0);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) xzb = fma(bb2[m], J[s + 1][t][m], xzb);
+          const T xzb = edot4(bb2, J[s + 1][t]);
           gaxpby4(xzb, J[t + 1][j], xyb, J[s + 1][t], Jb[i][s]);
           gaxpby4(xzb, J[i][s], yzb, J[s + 1][t], Jb[t + 1][j]);
           axpy4(xz, bb2, Jb[s + 1][t]);
@@ -210,9 +223,7 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
       T P2b[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
       for (int s = i; s < j; ++s) {
-        T xyb = sxyb;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) xyb = fma(bb2[m], Sp[s + 1][m], xyb);
+        const T xyb = sxyb + edot4(bb2, Sp[s + 1]);
         axpy4(xy[s], bb2, Sb[s + 1]);
         const T pxb = cRb[s];
         const T pyb = -cXb[s];
