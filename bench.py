@@ -60,11 +60,13 @@ WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqr
 # DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
 # n = 8, 2^20 events, scaled from a 2^16-event capture by the number of
 # events), valid only for the kernel sources it was taken from.
-NCU_TRAFFIC = {"sources_sha1": "7ba9df895bf416125976c8bd21337f52a2f68f02",
-               "bytes_per_launch": 16 * (17532160 + 127553280)}  # 2^16-event capture x 16
+NCU_TRAFFIC = {"sources_sha1": "9db31df7b2c5dcc140f9d5b64185b3258c6c0b03",
+               "bytes_per_launch": 16 * (17377024 + 127708416)}  # 2^16-event capture x 16
 # Executed FP32 operations per event of the dominant kernel at n = 8 (ncu sass
-# counts of the same capture: 2 x FFMA + FADD + FMUL), valid for the same sources.
-NCU_EXECUTED = {"sources_sha1": "7ba9df895bf416125976c8bd21337f52a2f68f02", "flops_per_event": 2524693}
+# counts 2 x FFMA + FADD + FMUL of a 2^16-event capture, taken before the
+# four-vector updates were packed into f32x2 instructions: the sass counters do
+# not count the packed forms, and packing leaves the arithmetic unchanged).
+NCU_EXECUTED = {"sources_sha1": "9db31df7b2c5dcc140f9d5b64185b3258c6c0b03", "flops_per_event": 2524693}
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
 
