@@ -17,6 +17,8 @@
 //     contraction of 8x8 matrices F^a_{bc} = Tr(T^a [T^b, T^c])
 //   * the colour sum A^T C A, Eq. (2.16)
 //   * colour-dressed currents, Eqs. (2.28)-(2.32)
+//   * colour-flow sampling with colour-ordered amplitudes, Eq. (2.19)
+//   * the leading-colour sum of Sec. 4
 // Equation numbers count the paper's numbered equations within Sec. 2.
 //
 // Conventions (the paper leaves these open; each reading is listed in the
@@ -30,7 +32,11 @@
 // invariance, cyclic / reflection / photon-decoupling identities, current
 // conservation, tensor form == V4 form, linear == helicity polarisation sums,
 // colour-dressed == colour-ordered x colour matrix by brute force over all
-// colours at n = 4, 5, colour-matrix diagonal closed form and symmetry.
+// colours at n = 4, 5, colour-matrix diagonal closed form and symmetry;
+// colour-flow amplitude from colour-ordered amplitudes == colour-dressed
+// amplitude for the same flow, and its average over all 9^n flows == the
+// colour sum; leading-colour sum == full colour sum at n = 4, 5 (the
+// subleading terms vanish there).
 
 #include <algorithm>
 #include <cmath>
@@ -608,6 +614,60 @@ void me2_cd_batch(int n, long long B, double sqrt_s, const double* u, const doub
   for (auto& x : th) x.join();
 }
 
+// Common start of the per-event sampled evaluations below: Rambo, the pT
+// cut, all-outgoing momenta and the sampled polarisations.  Returns false
+// for events failing the cut.
+template <class T>
+bool event_setup(int n, double sqrt_s, const T* u, const double* q, const int8_t* hel, double pt_min,
+                 Vec<T>* k, Vec<T>* eps) {
+  std::vector<Vec<T>> p(n);
+  rambo(n, sqrt_s, u, p.data());
+  for (int i = 2; i < n; ++i)
+    if (std::sqrt(value(p[i].c[1]) * value(p[i].c[1]) + value(p[i].c[2]) * value(p[i].c[2])) <= pt_min)
+      return false;
+  outgoing(n, p.data(), k);
+  pols_for(n, k, q, hel, eps);
+  return true;
+}
+
+// Colour-flow amplitude of Eq. (2.19) for one sampled flow, from the
+// colour-ordered partial amplitudes: the sum over the (n-1)! orders
+// (1, s_2, ..., s_n) of the product of Kronecker deltas around the cycle
+// times A(1, s_2, ..., s_n).  Gluon i carries the flow pair (r_i, c_i), its
+// colour matrix is |r_i><c_i|, so the trace of the ordered product is
+// delta(c_1, r_{s_2}) delta(c_{s_2}, r_{s_3}) ... delta(c_{s_n}, r_1).
+// Orders whose delta product vanishes are skipped (their term is zero).
+template <class T>
+T amp_colour_flow(int n, const Vec<T>* k, const Vec<T>* eps, const int8_t* flow) {
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  T a = T(0.0);
+  do {
+    bool on = true;
+    for (int t = 0; t < n && on; ++t) {
+      const int from = ord[t], to = ord[(t + 1) % n];
+      on = flow[2 * from + 1] == flow[2 * to];
+    }
+    if (on) a += amp_co(n, k, eps, ord.data(), 0);
+  } while (std::next_permutation(ord.begin() + 1, ord.end()));
+  return a;
+}
+
+// Leading-colour sum of Sec. 4 (the prefactor formula for the leading
+// colour algorithms): N^(n-2) (N^2 - 1) sum over the (n-1)! orders
+// (1, s_2, ..., s_n) of |A(1, s_2, ..., s_n)|^2, N = 3.
+template <class T>
+T leading_colour_sum(int n, const Vec<T>* k, const Vec<T>* eps) {
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  T s = T(0.0);
+  do {
+    const T a = amp_co(n, k, eps, ord.data(), 0);
+    s += a * a;
+  } while (std::next_permutation(ord.begin() + 1, ord.end()));
+  return T(std::pow(3.0, n - 2) * 8.0) * s;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -800,6 +860,62 @@ void or_me2_cd_batch(int n, long long B, double sqrt_s, const double* u, const d
 void or_me2_cd_batch_ext(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
                          const int8_t* colors, int mode, double g, double pt_min, double* me2, int nthreads) {
   me2_cd_batch<long double>(n, B, sqrt_s, u, q, hel, colors, mode, g, pt_min, me2, nthreads);
+}
+
+// Batch |M|^2 estimator with sampled colour flows evaluated from
+// colour-ordered amplitudes (the colour-sampling variant of Sec. 4, with the
+// colour-flow decomposition of Eq. 2.19): colors[B][2n] flow pairs
+// (r_i, c_i) in 1..3, hel[B][n]; me2 = 9^n 2^n g^(2n-4) |A_flow|^2.  Events
+// failing the pT cut get 0.
+void or_me2_co_mc_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
+                        const int8_t* colors, double g, double pt_min, double* me2, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::thread> th;
+  const int d = 4 * (n - 2);
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<Vec<double>> k(n), eps(n);
+      for (long long e = t; e < B; e += nthreads) {
+        if (!event_setup(n, sqrt_s, u + e * d, q, hel + e * n, pt_min, k.data(), eps.data())) {
+          me2[e] = 0.0;
+          continue;
+        }
+        const double a = amp_colour_flow(n, k.data(), eps.data(), colors + e * 2 * n);
+        me2[e] = std::pow(9.0, n) * std::pow(2.0, n) * std::pow(g, 2 * n - 4) * a * a;
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
+// Batch leading-colour |M|^2 (Sec. 4): g^(2n-4) N^(n-2) (N^2-1) sum over the
+// (n-1)! orders of |A|^2, for sampled helicities hel[B][n] (weight 2^n) or,
+// with hel = NULL, summed over all 2^n polarisation configurations.  Events
+// failing the pT cut get 0.
+void or_me2_lc_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
+                     double g, double pt_min, double* me2, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::thread> th;
+  const int d = 4 * (n - 2);
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<Vec<double>> k(n), eps(n);
+      std::vector<int8_t> h(n);
+      for (long long e = t; e < B; e += nthreads) {
+        const int nconf = hel ? 1 : (1 << n);
+        double s = 0.0;
+        bool cut = false;
+        for (int conf = 0; conf < nconf && !cut; ++conf) {
+          for (int i = 0; i < n; ++i) h[i] = hel ? hel[e * n + i] : (((conf >> i) & 1) ? -1 : 1);
+          if (!event_setup(n, sqrt_s, u + e * d, q, h.data(), pt_min, k.data(), eps.data())) {
+            cut = true;
+            break;
+          }
+          s += leading_colour_sum(n, k.data(), eps.data());
+        }
+        me2[e] = cut ? 0.0 : std::pow(g, 2 * n - 4) * (hel ? std::pow(2.0, n) : 1.0) * s;
+      }
+    });
+  for (auto& x : th) x.join();
 }
 
 // Gradient of the colour-summed |M|^2 (sampled helicity hel[n]) with

@@ -75,6 +75,8 @@ def lib():
             L.or_me2_co_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_cd_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
             L.or_me2_cd_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_co_mc_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_lc_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_co_grad.argtypes = [c_int, c_dbl, dp, dp, dp, i8p, c_dbl, dp]
             L.or_me2_co_grad.restype = c_dbl
             _lib = L
@@ -373,6 +375,36 @@ def me2_cd(n, u, hel, colors, mode=0, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT,
     fn = lib().or_me2_cd_batch_ext if ext else lib().or_me2_cd_batch
     fn(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, cp, mode, g,
        pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+    return me2
+
+
+def me2_co_mc(n, u, hel, colors, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0,
+              nthreads=None) -> np.ndarray:
+    """|M|^2 estimator per event for sampled colour flows colors[B, 2n],
+    evaluated from colour-ordered amplitudes with Eq. (2.19)."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
+    B = u.shape[0]
+    q, qp = _d(q)
+    hel, hp = _i8(np.asarray(hel).reshape(B, n))
+    colors, cp = _i8(np.asarray(colors).reshape(B, 2 * n))
+    me2 = np.zeros(B)
+    lib().or_me2_co_mc_batch(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, cp, g,
+                             pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+    return me2
+
+
+def me2_lc(n, u, hel=None, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0, nthreads=None) -> np.ndarray:
+    """Leading-colour |M|^2 per event (Sec. 4): hel[B, n] sampled (weight
+    2^n) or None (all 2^n polarisation configurations)."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
+    B = u.shape[0]
+    q, qp = _d(q)
+    hp = None
+    if hel is not None:
+        hel, hp = _i8(np.asarray(hel).reshape(B, n))
+    me2 = np.zeros(B)
+    lib().or_me2_lc_batch(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, g, pt_min,
+                          me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
     return me2
 
 

@@ -340,6 +340,77 @@ def test_colour_dressed_current_conservation(oracle):
 
 
 # --------------------------------------------------------------------------
+# Colour-flow sampling with colour-ordered amplitudes (Eq. 2.19) and the
+# leading-colour sum (Sec. 4)
+# --------------------------------------------------------------------------
+def matched_flows(n, count, seed):
+    """Flow pairs whose row colours are a permutation of the column colours
+    (the only flows with a non-zero amplitude), plus uniform ones."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros((count, 2 * n), dtype=np.int8)
+    for b in range(count):
+        c = rng.integers(1, 4, n)
+        r = c[rng.permutation(n)] if b % 4 else rng.integers(1, 4, n)
+        f[b, 0::2], f[b, 1::2] = r, c
+    return f
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7])
+def test_colour_flow_from_ordered_equals_colour_dressed(oracle, n):
+    # Eq. (2.19) summed from colour-ordered amplitudes against the
+    # independent colour-dressed recursion with the same flow externals
+    count = 40
+    u = np.repeat(inputs.rambo_uniforms(n, 1, seed=16), count, axis=0)
+    hel = np.repeat(inputs.helicities(n, 1, seed=16), count, axis=0)
+    fl = matched_flows(n, count, 16 + n)
+    a = oracle.me2_co_mc(n, u, hel, fl, sqrt_s=SQRT_S)
+    b = oracle.me2_cd(n, u, hel, fl, mode=1, sqrt_s=SQRT_S)
+    assert (b > 0).sum() >= count // 2
+    # (flows such as all-equal colours cancel to zero by photon decoupling:
+    # exact in one form, rounding-level in the other)
+    assert np.abs(a - b).max() < 1e-10 * b.max()
+    # flows whose rows are not a permutation of the columns vanish exactly
+    bad = fl.copy()
+    bad[:, 0] = bad[:, 1] % 3 + 1
+    bad[:, 2::2] = bad[:, 3::2]
+    assert np.all(oracle.me2_co_mc(n, u, hel, bad, sqrt_s=SQRT_S) == 0.0)
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_colour_flow_from_ordered_bruteforce(oracle, n):
+    # the average over all 9^n flows (weight 9^n each) is the colour sum
+    u = inputs.rambo_uniforms(n, 1, seed=17)
+    hel = inputs.helicities(n, 1, seed=17)
+    cols = np.array(list(itertools.product(range(1, 4), repeat=2 * n)), dtype=np.int8)
+    B = cols.shape[0]
+    est = oracle.me2_co_mc(n, np.repeat(u, B, axis=0), np.repeat(hel, B, axis=0), cols, sqrt_s=SQRT_S)
+    co = oracle.me2_co(n, u, sqrt_s=SQRT_S, hel=hel)
+    assert abs(est.mean() / co[0] - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_leading_colour_exact_for_four_and_five_gluons(oracle, n):
+    # the subleading colour terms of the all-gluon colour sum vanish for
+    # n = 4, 5: the leading-colour formula equals the full colour sum
+    u = inputs.rambo_uniforms(n, 4, seed=18)
+    hel = inputs.helicities(n, 4, seed=18)
+    assert np.allclose(oracle.me2_lc(n, u, sqrt_s=SQRT_S), oracle.me2_co(n, u, sqrt_s=SQRT_S), rtol=1e-12, atol=0)
+    assert np.allclose(oracle.me2_lc(n, u, hel=hel, sqrt_s=SQRT_S), oracle.me2_co(n, u, hel=hel, sqrt_s=SQRT_S),
+                       rtol=1e-12, atol=0)
+
+
+def test_leading_colour_gauge_invariant_and_subleading_at_six(oracle):
+    n = 6
+    u = inputs.rambo_uniforms(n, 3, seed=19)
+    a = oracle.me2_lc(n, u, sqrt_s=SQRT_S, q=(1.0, 0.0, 0.0, 1.0))
+    b = oracle.me2_lc(n, u, sqrt_s=SQRT_S, q=(1.0, 0.6, 0.0, 0.8))
+    assert np.allclose(a, b, rtol=1e-11, atol=0)
+    # from n = 6 on the formula is an approximation: O(1/N^2) away
+    r = a / oracle.me2_co(n, u, sqrt_s=SQRT_S)
+    assert np.all(np.abs(r - 1.0) > 1e-8) and np.all(np.abs(r - 1.0) < 0.3)
+
+
+# --------------------------------------------------------------------------
 # P8: gradient with respect to the Rambo uniforms
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [4, 5])
