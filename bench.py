@@ -10,7 +10,7 @@ accumulation.  Metric: events/s (all generated events of all four
 multiplicities; per-n figures are in "per_n").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload co|cd|grad|mixed]
+                    [--workload co|cd|grad|mixed|comc|lc]
 
 The default workload (co) is the one above.  The others measure the other
 parts of the path with the same timing rules:
@@ -21,7 +21,10 @@ parts of the path with the same timing rules:
   mixed  10^7 events with n uniform in 4..12 in one CUDA-graph launch: tensor-
          core colour sum for n = 6..9 (FP32 CUDA cores for n = 4, 5),
          colour-dressed recursion with sampled adjoint colours for n = 10..12,
-         FP32 currents, pT > 20 GeV, autotuned kernel variants.
+         FP32 currents, pT > 20 GeV, autotuned kernel variants;
+  comc   colour-flow sampling with colour-ordered amplitudes (Eq. 2.19),
+         flows uniform in {1,2,3}^2, n = 8, 10, 12, 2^20 events per n;
+  lc     leading-colour |M|^2 (Sec. 4) on the default events, n = 5..8.
 
 Prints ONE JSON line on rank 0.  N > 1 runs under torch.distributed.run, one
 process per GPU, each with its own events (weak scaling, no collective on the
@@ -667,6 +670,242 @@ def run_cd(args) -> None:
     finish_gpu(world)
 
 
+def flow_order_counts(cols, n: int):
+    """Number of orders (1, s_2, ..., s_n) whose colour-flow chain closes, per
+    event (cols [B, 2n] flow pairs in 1..3): the work of the colour-flow
+    kernel.  Counted by colour types -- the gluons of one (row, column) type
+    are interchangeable -- with a memoised recursion over the remaining
+    types, times the permutations within each type."""
+    import numpy as np
+    r = cols[:, 0::2].astype(np.int64) - 1
+    c = cols[:, 1::2].astype(np.int64) - 1
+    bal = np.all(np.stack([(r == k).sum(1) == (c == k).sum(1) for k in range(3)]), axis=0)
+    out = np.zeros(cols.shape[0], dtype=np.int64)
+    idx = np.nonzero(bal)[0]
+    if idx.size == 0:
+        return out
+    types = r[idx, 1:] * 3 + c[idx, 1:]
+    m = np.stack([(types == t).sum(1) for t in range(9)], axis=1)
+    sig = np.concatenate([r[idx, :1], c[idx, :1], m], axis=1)
+    uniq, inv = np.unique(sig, axis=0, return_inverse=True)
+    from functools import lru_cache
+    vals = np.zeros(len(uniq), dtype=np.int64)
+    for i, row in enumerate(uniq):
+        r0, c0, mm = int(row[0]), int(row[1]), tuple(int(x) for x in row[2:])
+
+        @lru_cache(maxsize=None)
+        def f(cur, rem):
+            if not any(rem):
+                return 1 if cur == r0 else 0
+            tot = 0
+            for cc in range(3):
+                t = cur * 3 + cc
+                if rem[t]:
+                    tot += f(cc, rem[:t] + (rem[t] - 1,) + rem[t + 1:])
+            return tot
+
+        vals[i] = f(c0, mm) * math.prod(math.factorial(x) for x in mm)
+    out[idx] = vals[inv.reshape(-1)]
+    return out
+
+
+COMC_NS = (8, 10, 12)
+
+
+def run_comc(args) -> None:
+    """Colour-flow sampling with colour-ordered amplitudes (Eq. 2.19), uniform
+    flows in {1,2,3}^2 per gluon, the colour-dressed workload's n, batch, cut
+    and arithmetic."""
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    prec = bg.BG_F64 if args.precision == "f64" else bg.BG_F32
+    batch = BATCH if args.precision == "f32" else BATCH >> 4
+    first = rank * batch
+    U, HEL, COL, P, ACC, ME2, host, orders = {}, {}, {}, {}, {}, {}, {}, {}
+    for n in COMC_NS:
+        u = inputs.rambo_uniforms(n, batch, seed=SEED, first_event=first)
+        h = inputs.helicities(n, batch, seed=SEED, first_event=first)
+        c = inputs.flow_colours(n, batch, seed=SEED, first_event=first)
+        orders[n] = flow_order_counts(c, n)
+        h, c = np.ascontiguousarray(h.T), np.ascontiguousarray(c.T)
+        U[n], HEL[n], COL[n] = (torch.from_numpy(x).to(dev) for x in (u, h, c))
+        host[n] = tuple(torch.from_numpy(x).pin_memory() for x in (u, h, c))
+        P[n] = torch.empty((4, n, batch), dtype=torch.float64, device=dev)
+        ACC[n] = torch.empty((batch,), dtype=torch.uint8, device=dev)
+        ME2[n] = torch.empty((batch,), dtype=torch.float64, device=dev)
+    ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for n in COMC_NS}
+    kernel_ms = {n: [0.0, 0.0] for n in COMC_NS}
+
+    def step(record=False):
+        for n in COMC_NS:
+            if record:
+                ev[n][0].record(stream)
+            bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            if record:
+                ev[n][1].record(stream)
+            bg.currents_co_mc(n, P[n], HEL[n], COL[n], prec=prec, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
+                              stream=stream)
+            if record:
+                ev[n][2].record(stream)
+
+    elapsed, clk = timed_steps(step, args, dev, stream)
+    value = world * len(COMC_NS) * batch * args.steps / elapsed
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize(dev)
+        for n in COMC_NS:
+            for j in range(2):
+                kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1]) / args.steps
+    ref = {n: ME2[n].cpu() for n in COMC_NS}
+    out_h = {n: torch.empty((batch,), dtype=torch.float64).pin_memory() for n in COMC_NS}
+    d_in = {n: tuple(torch.empty_like(x, device=dev) for x in host[n]) for n in COMC_NS}
+
+    def e2e_step():
+        for n in COMC_NS:
+            for dst, src in zip(d_in[n], host[n]):
+                dst.copy_(src, non_blocking=True)
+            bg.momenta_rambo(n, d_in[n][0], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            bg.currents_co_mc(n, P[n], d_in[n][1], d_in[n][2], prec=prec, sqrt_s=SQRT_S, accept=ACC[n],
+                              me2=ME2[n], stream=stream)
+            out_h[n].copy_(ME2[n], non_blocking=True)
+
+    e2e_s = timed_host(e2e_step, args, dev)
+    for n in COMC_NS:
+        if not torch.equal(out_h[n], ref[n]):
+            raise RuntimeError(f"e2e colour-flow |M|^2 differs from the device-resident run at n={n}")
+    h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in COMC_NS)
+    n_dom = max(COMC_NS, key=lambda n: kernel_ms[n][1])
+    acc_np = ACC[n_dom].cpu().numpy().astype(bool)
+    n_orders = int(orders[n_dom][acc_np].sum())
+    flops = canonical_recursion_flops(n_dom) * n_orders
+    achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    if prec == bg.BG_F64:
+        peak, peak_source = fma_probe_tflops(bg, bg.BG_F64, stream, dev, 500), "FP64 FMA probe (measured)"
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": ("colour-flow sampling with colour-ordered amplitudes (Eq. 2.19), flows uniform "
+                                    f"in {{1,2,3}}^2 per gluon, n=8,10,12, {batch} Rambo points per n at "
+                                    f"sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, {args.precision.upper()} "
+                                    "currents"),
+                       "n": list(COMC_NS), "batch_per_n": batch, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2"},
+            "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in COMC_NS},
+            "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in COMC_NS},
+            "orders_per_event": {str(n): float(orders[n].mean()) for n in COMC_NS},
+            "roofline": {"kernel": f"comc_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
+                         "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_model": "canonical recursion FLOPs of one order x closing orders of the events "
+                                        "passing the cut",
+                         "flops_per_order": canonical_recursion_flops(n_dom), "orders_computed": n_orders,
+                         "peak_source": peak_source},
+            "e2e": {"value": world * len(COMC_NS) * batch * args.steps / e2e_s, "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(COMC_NS) * batch * 8},
+            "gpu_launches": 2 * len(COMC_NS) * args.steps, "clocks": clk}), flush=True)
+    finish_gpu(world)
+
+
+def run_lc(args) -> None:
+    """Leading-colour |M|^2 (Sec. 4) on the default workload's events: n = 5..8,
+    2^20 events per n, sampled helicities, FP32 currents, (n-1)! orders."""
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    prec = bg.BG_F64 if args.precision == "f64" else bg.BG_F32
+    batch = BATCH if args.precision == "f32" else BATCH >> 4
+    first = rank * batch
+    U, HEL, P, ACC, ME2, WS, host = {}, {}, {}, {}, {}, {}, {}
+    for n in NS:
+        u = inputs.rambo_uniforms(n, batch, seed=SEED, first_event=first)
+        h = np.ascontiguousarray(inputs.helicities(n, batch, seed=SEED, first_event=first).T)
+        U[n], HEL[n] = torch.from_numpy(u).to(dev), torch.from_numpy(h).to(dev)
+        host[n] = (torch.from_numpy(u).pin_memory(), torch.from_numpy(h).pin_memory())
+        P[n] = torch.empty((4, n, batch), dtype=torch.float64, device=dev)
+        ACC[n] = torch.empty((batch,), dtype=torch.uint8, device=dev)
+        ME2[n] = torch.empty((batch,), dtype=torch.float64, device=dev)
+        WS[n] = torch.empty((bg.lc_workspace_bytes(n, batch, True, prec),), dtype=torch.uint8, device=dev)
+    ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for n in NS}
+    kernel_ms = {n: [0.0, 0.0] for n in NS}
+
+    def step(record=False):
+        for n in NS:
+            if record:
+                ev[n][0].record(stream)
+            bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            if record:
+                ev[n][1].record(stream)
+            bg.currents_lc(n, P[n], HEL[n], prec=prec, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n], workspace=WS[n],
+                           stream=stream)
+            if record:
+                ev[n][2].record(stream)
+
+    elapsed, clk = timed_steps(step, args, dev, stream)
+    value = world * len(NS) * batch * args.steps / elapsed
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize(dev)
+        for n in NS:
+            for j in range(2):
+                kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1]) / args.steps
+    ref = {n: ME2[n].cpu() for n in NS}
+    out_h = {n: torch.empty((batch,), dtype=torch.float64).pin_memory() for n in NS}
+    d_in = {n: tuple(torch.empty_like(x, device=dev) for x in host[n]) for n in NS}
+
+    def e2e_step():
+        for n in NS:
+            for dst, src in zip(d_in[n], host[n]):
+                dst.copy_(src, non_blocking=True)
+            bg.momenta_rambo(n, d_in[n][0], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+            bg.currents_lc(n, P[n], d_in[n][1], prec=prec, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
+                           workspace=WS[n], stream=stream)
+            out_h[n].copy_(ME2[n], non_blocking=True)
+
+    e2e_s = timed_host(e2e_step, args, dev)
+    for n in NS:
+        if not torch.equal(out_h[n], ref[n]):
+            raise RuntimeError(f"e2e leading-colour |M|^2 differs from the device-resident run at n={n}")
+    h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in NS)
+    n_dom = max(NS, key=lambda n: kernel_ms[n][1])
+    flops = canonical_recursion_flops(n_dom) * math.factorial(n_dom - 1) * batch
+    achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    if prec == bg.BG_F64:
+        peak, peak_source = fma_probe_tflops(bg, bg.BG_F64, stream, dev, 500), "FP64 FMA probe (measured)"
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": ("leading-colour |M|^2 (Sec. 4), n=5,6,7,8, 2^20 Rambo points per n at "
+                                    f"sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, {args.precision.upper()} "
+                                    "currents for all (n-1)! orders"),
+                       "n": list(NS), "batch_per_n": batch, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2"},
+            "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in NS},
+            "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in NS},
+            "roofline": {"kernel": f"bg_currents_lc at n={n_dom} ({n_dom - 1} recursion launches)",
+                         "bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_model": "canonical recursion FLOPs per order x (n-1)! orders x events",
+                         "flops_per_event": canonical_recursion_flops(n_dom) * math.factorial(n_dom - 1),
+                         "peak_source": peak_source},
+            "e2e": {"value": world * len(NS) * batch * args.steps / e2e_s, "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(NS) * batch * 8},
+            "gpu_launches": sum(1 + 3 * (n - 1) for n in NS) * args.steps, "clocks": clk}), flush=True)
+    finish_gpu(world)
+
+
 GRAD_NS = (6, 8)
 GRAD_BATCH = 1 << 18
 
@@ -846,7 +1085,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed"), default="co")
+    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc"), default="co")
     ap.add_argument("--precision", choices=("f32", "f64"), default="f32",
                     help="recursion arithmetic of the co and cd workloads (f64: the plain FP64 GPU form)")
     ap.add_argument("--profile-n", type=int, default=0,
@@ -863,6 +1102,10 @@ def main(argv=None):
         run_grad(args)
     elif args.workload == "mixed":
         run_mixed(args)
+    elif args.workload == "comc":
+        run_comc(args)
+    elif args.workload == "lc":
+        run_lc(args)
     else:
         run_ours(args)
 

@@ -301,6 +301,57 @@ bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const
                          void* stream);
 
 /* ---------------------------------------------------------------------------
+ * bg_currents_co_mc -- colour sampling with colour-ordered amplitudes (the
+ * colour-sampling variant of the colour-ordered algorithms, Sec. 4, with the
+ * colour-flow decomposition of Eq. 2.19): per event one sampled colour flow
+ * and helicity configuration; the flow amplitude is the sum, over the
+ * (n-1)! orders (1, s_2, ..., s_n) whose chain of Kronecker deltas
+ * delta(c_1, r_{s_2}) delta(c_{s_2}, r_{s_3}) ... delta(c_{s_n}, r_1) closes,
+ * of the colour-ordered amplitudes A(1, s_2, ..., s_n) (Eqs. 2.20-2.22);
+ *   me2 = 9^n * 2^n * g_s^(2n-4) * |A_flow|^2,
+ * the same estimator as bg_currents_cd with BG_COL_FLOW (equal event by
+ * event up to rounding).
+ *   p       [4][n][B]    lab momenta (bg_momenta_rambo)
+ *   hel     [n][B] int8  helicity labels +-1
+ *   colors  [2n][B] int8 rows 2i and 2i+1 the pair (r_i, c_i) in 1..3
+ *           (external colour matrix |r_i><c_i|)
+ *   accept  [B] or NULL  events with accept == 0 get 0
+ *   me2     [B] double   output, GeV^(8-2n)
+ * No workspace: each block keeps its events and the orders being evaluated
+ * in shared memory.  Events with a colour label outside 1..3 get 0 and set
+ * BG_EINVAL in the device status word.  The work per event is the number of
+ * closing orders, (n-1)!/3^n on average and up to (n-1)! for degenerate
+ * flows.  Supported: 4 <= n <= 12.  Errors: BG_EINVAL, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
+                            const int8_t* colors, const double* q, bg_prec prec, double g_s, const uint8_t* accept,
+                            double* me2, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * bg_currents_lc -- leading-colour |M|^2 (Sec. 4, the prefactor formula of
+ * the leading-colour algorithms):
+ *   me2 = g_s^(2n-4) N^(n-2) (N^2-1) sum over the (n-1)! orders
+ *         (1, s_2, ..., s_n) of |A(1, s_2, ..., s_n)|^2   (N = 3),
+ * times 2^n for sampled helicities (hel != NULL) or summed over all 2^n
+ * polarisation configurations (hel == NULL).  Exact for n = 4, 5; an
+ * O(1/N^2) approximation of the colour sum beyond.
+ *   p       [4][n][B]    lab momenta (bg_momenta_rambo)
+ *   hel     [n][B] int8 or NULL
+ *   accept  [B] or NULL  events with accept == 0 get 0
+ *   me2     [B] double   output, GeV^(8-2n)
+ *   workspace, workspace_bytes: caller-owned device scratch of at least
+ *           bg_lc_workspace_bytes(n, B, hel != NULL, prec) bytes, 256-byte
+ *           aligned (relabelled inputs, one run's amplitudes, per-event
+ *           sums); nothing needs to be zeroed.
+ * Runs the colour-ordered recursion n-1 times (once per gluon placed last)
+ * on `stream`.  Supported: 4 <= n <= 9.  Errors: BG_EINVAL, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_lc_workspace_bytes(int n, int64_t B, int hel_sampled, bg_prec prec, int64_t* bytes);
+bg_status bg_currents_lc(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                         bg_prec prec, double g_s, const uint8_t* accept, double* me2, void* workspace,
+                         int64_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Mixed multiplicities: a batch whose events each have their own n in
  * n_min..n_max (Sec. 5 times every n from 4 to 12; a generator of events
  * with several jet multiplicities feeds such batches).  bg_mixed_create

@@ -668,6 +668,35 @@ T leading_colour_sum(int n, const Vec<T>* k, const Vec<T>* eps) {
   return T(std::pow(3.0, n - 2) * 8.0) * s;
 }
 
+// Batch |M|^2 estimator with sampled colour flows evaluated from
+// colour-ordered amplitudes (the colour-sampling variant of Sec. 4, with the
+// colour-flow decomposition of Eq. 2.19): colors[B][2n] flow pairs
+// (r_i, c_i) in 1..3, hel[B][n]; me2 = 9^n 2^n g^(2n-4) |A_flow|^2.  Events
+// failing the pT cut get 0.  T = double, or long double for the
+// extended-precision reference.
+template <class T>
+void me2_co_mc_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
+                     const int8_t* colors, double g, double pt_min, double* me2, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::thread> th;
+  const int d = 4 * (n - 2);
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<Vec<T>> k(n), eps(n);
+      std::vector<T> ul(d);
+      for (long long e = t; e < B; e += nthreads) {
+        for (int i = 0; i < d; ++i) ul[i] = T(u[e * d + i]);
+        if (!event_setup(n, sqrt_s, ul.data(), q, hel + e * n, pt_min, k.data(), eps.data())) {
+          me2[e] = 0.0;
+          continue;
+        }
+        const T a = amp_colour_flow(n, k.data(), eps.data(), colors + e * 2 * n);
+        me2[e] = (double)(T(std::pow(9.0, n) * std::pow(2.0, n) * std::pow(g, 2 * n - 4)) * a * a);
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -862,29 +891,16 @@ void or_me2_cd_batch_ext(int n, long long B, double sqrt_s, const double* u, con
   me2_cd_batch<long double>(n, B, sqrt_s, u, q, hel, colors, mode, g, pt_min, me2, nthreads);
 }
 
-// Batch |M|^2 estimator with sampled colour flows evaluated from
-// colour-ordered amplitudes (the colour-sampling variant of Sec. 4, with the
-// colour-flow decomposition of Eq. 2.19): colors[B][2n] flow pairs
-// (r_i, c_i) in 1..3, hel[B][n]; me2 = 9^n 2^n g^(2n-4) |A_flow|^2.  Events
-// failing the pT cut get 0.
+// Batch |M|^2 estimator with sampled colour flows (me2_co_mc_batch).
 void or_me2_co_mc_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const int8_t* hel,
                         const int8_t* colors, double g, double pt_min, double* me2, int nthreads) {
-  if (nthreads < 1) nthreads = 1;
-  std::vector<std::thread> th;
-  const int d = 4 * (n - 2);
-  for (int t = 0; t < nthreads; ++t)
-    th.emplace_back([&, t]() {
-      std::vector<Vec<double>> k(n), eps(n);
-      for (long long e = t; e < B; e += nthreads) {
-        if (!event_setup(n, sqrt_s, u + e * d, q, hel + e * n, pt_min, k.data(), eps.data())) {
-          me2[e] = 0.0;
-          continue;
-        }
-        const double a = amp_colour_flow(n, k.data(), eps.data(), colors + e * 2 * n);
-        me2[e] = std::pow(9.0, n) * std::pow(2.0, n) * std::pow(g, 2 * n - 4) * a * a;
-      }
-    });
-  for (auto& x : th) x.join();
+  me2_co_mc_batch<double>(n, B, sqrt_s, u, q, hel, colors, g, pt_min, me2, nthreads);
+}
+
+void or_me2_co_mc_batch_ext(int n, long long B, double sqrt_s, const double* u, const double* q,
+                            const int8_t* hel, const int8_t* colors, double g, double pt_min, double* me2,
+                            int nthreads) {
+  me2_co_mc_batch<long double>(n, B, sqrt_s, u, q, hel, colors, g, pt_min, me2, nthreads);
 }
 
 // Batch leading-colour |M|^2 (Sec. 4): g^(2n-4) N^(n-2) (N^2-1) sum over the

@@ -76,6 +76,7 @@ def lib():
             L.or_me2_cd_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
             L.or_me2_cd_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_int, c_dbl, c_dbl, dp, c_int]
             L.or_me2_co_mc_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_co_mc_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_lc_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_co_grad.argtypes = [c_int, c_dbl, dp, dp, dp, i8p, c_dbl, dp]
             L.or_me2_co_grad.restype = c_dbl
@@ -379,17 +380,19 @@ def me2_cd(n, u, hel, colors, mode=0, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT,
 
 
 def me2_co_mc(n, u, hel, colors, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0,
-              nthreads=None) -> np.ndarray:
+              nthreads=None, ext=False) -> np.ndarray:
     """|M|^2 estimator per event for sampled colour flows colors[B, 2n],
-    evaluated from colour-ordered amplitudes with Eq. (2.19)."""
+    evaluated from colour-ordered amplitudes with Eq. (2.19) (ext: in
+    extended precision)."""
     u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
     B = u.shape[0]
     q, qp = _d(q)
     hel, hp = _i8(np.asarray(hel).reshape(B, n))
     colors, cp = _i8(np.asarray(colors).reshape(B, 2 * n))
     me2 = np.zeros(B)
-    lib().or_me2_co_mc_batch(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, cp, g,
-                             pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+    fn = lib().or_me2_co_mc_batch_ext if ext else lib().or_me2_co_mc_batch
+    fn(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, cp, g,
+       pt_min, me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
     return me2
 
 

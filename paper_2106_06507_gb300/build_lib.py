@@ -36,6 +36,9 @@ SOURCES = [
     "grad_rambo.cu",
     "mixed.cu",
     "tune.cu",
+    "comc_f32.cu",
+    "comc_f64.cu",
+    "lc.cu",
 ]
 
 

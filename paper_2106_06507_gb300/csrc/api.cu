@@ -9,6 +9,7 @@
 
 #include "bg_internal.h"
 #include "cd_recursion.cuh"
+#include "comc.cuh"
 
 namespace bg {
 
@@ -271,6 +272,31 @@ bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const
                                    : launch_cd_f64(n, prm, p, hel, colors, accept, me2, workspace,
                                                    device_status_ptr(), sms, (cudaStream_t)stream);
   return cuda_check(e, "bg_currents_cd");
+}
+
+bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
+                            const int8_t* colors, const double* q, bg_prec prec, double g_s, const uint8_t* accept,
+                            double* me2, void* stream) {
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_currents_co_mc: n must be in 4..12");
+  if (B < 0) return fail(BG_EINVAL, "bg_currents_co_mc: B < 0");
+  if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_currents_co_mc: sqrt_s must be > 0");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_currents_co_mc: invalid precision");
+  if (!q) return fail(BG_EINVAL, "bg_currents_co_mc: q is NULL");
+  const double qv = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(q[0] > 0.0) || std::fabs(q[0] - qv) > 1e-12 * q[0])
+    return fail(BG_EINVAL, "bg_currents_co_mc: q must be light-like with q0 > 0");
+  if (B == 0) return BG_OK;
+  if (!p || !hel || !colors || !me2) return fail(BG_EINVAL, "bg_currents_co_mc: NULL argument");
+  if (!aligned(p, 8) || !aligned(me2, 8)) return fail(BG_EINVAL, "bg_currents_co_mc: misaligned pointer");
+  ComcParams prm;
+  prm.B = B;
+  prm.inv_sqrt_s = 1.0 / sqrt_s;
+  prm.scale = std::pow(9.0, n) * std::ldexp(1.0, n) * std::pow(g_s, 2 * n - 4) * std::pow(sqrt_s, 8 - 2 * n) *
+              std::ldexp(1.0, -(n - 2));
+  cudaError_t e = (prec == BG_F32)
+                      ? launch_comc_f32(n, prm, p, hel, colors, accept, q, me2, device_status_ptr(), (cudaStream_t)stream)
+                      : launch_comc_f64(n, prm, p, hel, colors, accept, q, me2, device_status_ptr(), (cudaStream_t)stream);
+  return cuda_check(e, "bg_currents_co_mc");
 }
 
 bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream) {

@@ -1,0 +1,167 @@
+"""GPU parity of colour-flow sampling with colour-ordered amplitudes
+(bg_currents_co_mc, Eq. 2.19) against the oracle on identical host-generated
+inputs, and against the GPU's own colour-dressed recursion with the same
+colour flows (the two estimators are equal event by event).
+
+Tolerances: those of the colour-dressed tests (test_gpu_cd.py), for the same
+reason -- the flow amplitude is a sum of colour-ordered amplitudes that can
+cancel: FP64 as accurate as the plain FP64 oracle against the oracle in
+extended precision; FP32 median relative error < 1e-5 and 99 % of events
+within 1e-3 of max(|M|^2, 1e-2 x the sample's median |M|^2).
+
+Flows are drawn balanced (column colours a permutation of the row colours):
+the others vanish exactly, and uniform flows are balanced for only 3-7 % of
+events.  Degenerate flows (thousands of closing orders in one event) take
+the kernel through several windows of items.
+"""
+import numpy as np
+import pytest
+
+from paper_2106_06507_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SQRT_S = 1000.0
+PT_MIN = 20.0
+
+
+@pytest.fixture(scope="module")
+def bg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_06507_gb300 import bg as _bg, build_lib
+    build_lib.build()
+    _bg.lib()
+    return _bg
+
+
+def run(bg, n, u, hel, cols, prec, pt_min=PT_MIN, cd=False):
+    import torch
+    dev = torch.device("cuda:0")
+    p, acc = bg.momenta_rambo(n, torch.from_numpy(u).to(dev), SQRT_S, pt_min)
+    h = torch.from_numpy(np.ascontiguousarray(hel.T)).to(dev)
+    c = torch.from_numpy(np.ascontiguousarray(cols.T)).to(dev)
+    if cd:
+        out = bg.currents_cd(n, p, h, c, flow=True, prec=prec, sqrt_s=SQRT_S, accept=acc)
+    else:
+        out = bg.currents_co_mc(n, p, h, c, prec=prec, sqrt_s=SQRT_S, accept=acc)
+    return out.cpu().numpy()
+
+
+def split_zeros(got, ref, tol=1e-10):
+    scale = ref.max() if ref.size and ref.max() > 0 else 1.0
+    zero = ref <= 1e-16 * scale
+    assert np.all(np.abs(got[zero]) <= tol * scale)
+    return ~zero
+
+
+def fp32_rel(got, ref):
+    return np.abs(got - ref) / np.maximum(ref, 1e-2 * np.median(ref))
+
+
+def assert_fp64_like(got, ext, f64):
+    nz = split_zeros(got, ext)
+    assert nz.any()
+    rel = np.abs(got[nz] / ext[nz] - 1.0)
+    floor = np.abs(f64[nz] / ext[nz] - 1.0)
+    assert np.median(rel) <= max(1e-13, 8.0 * np.median(floor))
+    assert np.sum(rel > 1e-12) <= 2 + 0.01 * rel.size + 4 * np.sum(floor > 1e-12)
+    assert rel.max() <= max(5e-11, 8.0 * floor.max())
+
+
+def degenerate_flows(n, B):
+    """Flows with (n-2)! closing orders: gluon 1 |1><2|, gluon 2 |2><1|, the
+    rest |1><1|; alternating with |1><2|, |2><1| pairs on gluons 3, 4."""
+    f = np.ones((B, 2 * n), dtype=np.int8)
+    f[:, 1] = 2
+    f[:, 2] = 2
+    f[1::2, 4 + 1] = 2
+    f[1::2, 6] = 2
+    return f
+
+
+@pytest.mark.parametrize("n,B", [(4, 256), (5, 300), (6, 200), (7, 150), (8, 80), (9, 40)])
+def test_comc_fp64_parity(bg, oracle, n, B):
+    u = inputs.rambo_uniforms(n, B, seed=110 + n)
+    hel = inputs.helicities(n, B, seed=110 + n)
+    cols = inputs.balanced_flow_colours(n, B, seed=110 + n)
+    cols[::7] = inputs.flow_colours(n, B, seed=111 + n)[::7]  # some uniform (mostly vanishing) flows
+    got = run(bg, n, u, hel, cols, bg.BG_F64)
+    ext = oracle.me2_co_mc(n, u, hel, cols, sqrt_s=SQRT_S, pt_min=PT_MIN, ext=True)
+    f64 = oracle.me2_co_mc(n, u, hel, cols, sqrt_s=SQRT_S, pt_min=PT_MIN)
+    assert_fp64_like(got, ext, f64)
+
+
+@pytest.mark.parametrize("n,B", [(6, 400), (8, 200), (10, 48), (12, 12)])
+def test_comc_fp32_parity(bg, oracle, n, B):
+    u = inputs.rambo_uniforms(n, B, seed=120 + n)
+    hel = inputs.helicities(n, B, seed=120 + n)
+    cols = inputs.balanced_flow_colours(n, B, seed=120 + n)
+    got = run(bg, n, u, hel, cols, bg.BG_F32, pt_min=-1.0)
+    ref = oracle.me2_co_mc(n, u, hel, cols, sqrt_s=SQRT_S, pt_min=-1.0)
+    nz = split_zeros(got, ref, tol=1e-6)
+    assert nz.sum() >= 2
+    assert np.median(np.abs(got[nz] / ref[nz] - 1.0)) < 1e-5
+    assert np.quantile(fp32_rel(got[nz], ref[nz]), 0.99) < 1e-3
+
+
+@pytest.mark.parametrize("n", [8, 9])
+def test_comc_many_orders_per_event(bg, oracle, n):
+    # (n-2)! = 720 / 5040 closing orders per event: several windows of
+    # items per block, items of one event spread over windows
+    B = 40
+    u = inputs.rambo_uniforms(n, B, seed=130 + n)
+    hel = inputs.helicities(n, B, seed=130 + n)
+    cols = degenerate_flows(n, B)
+    got = run(bg, n, u, hel, cols, bg.BG_F64, pt_min=-1.0)
+    ext = oracle.me2_co_mc(n, u, hel, cols, sqrt_s=SQRT_S, pt_min=-1.0, ext=True)
+    f64 = oracle.me2_co_mc(n, u, hel, cols, sqrt_s=SQRT_S, pt_min=-1.0)
+    assert_fp64_like(got, ext, f64)
+    got32 = run(bg, n, u, hel, cols, bg.BG_F32, pt_min=-1.0)
+    assert np.all(fp32_rel(got32, ext) < 1e-3)
+
+
+@pytest.mark.parametrize("n,B", [(8, 4096), (10, 1024), (12, 256)])
+def test_comc_equals_colour_dressed_flow(bg, n, B):
+    # two different recursions for the same colour flows: colour-ordered
+    # amplitudes summed with Eq. (2.19) vs the colour-dressed currents
+    u = inputs.rambo_uniforms(n, B, seed=140 + n)
+    hel = inputs.helicities(n, B, seed=140 + n)
+    cols = inputs.flow_colours(n, B, seed=140 + n)
+    cols[::2] = inputs.balanced_flow_colours(n, B, seed=140 + n)[::2]
+    a = run(bg, n, u, hel, cols, bg.BG_F64)
+    b = run(bg, n, u, hel, cols, bg.BG_F64, cd=True)
+    nz = split_zeros(a, b)
+    assert nz.sum() >= B // 8
+    rel = np.abs(a[nz] - b[nz]) / np.maximum(b[nz], 1e-6 * np.median(b[nz]))
+    assert np.median(rel) < 1e-12 and rel.max() < 1e-8
+    a32 = run(bg, n, u, hel, cols, bg.BG_F32)
+    assert np.quantile(fp32_rel(a32[nz], b[nz]), 0.99) < 1e-3
+
+
+def test_comc_edge_cases(bg):
+    import torch
+    dev = torch.device("cuda:0")
+    n = 6
+    z = torch.zeros((4, n, 0), dtype=torch.float64, device=dev)
+    out = bg.currents_co_mc(n, z, torch.zeros((n, 0), dtype=torch.int8, device=dev),
+                            torch.zeros((2 * n, 0), dtype=torch.int8, device=dev))
+    assert out.numel() == 0
+    u = inputs.rambo_uniforms(n, 3, seed=150)
+    hel = np.ones((3, n), dtype=np.int8)
+    # unbalanced flow (every gluon |1><2|): no closing order, exactly 0
+    cols = np.tile(np.array([1, 2] * n, dtype=np.int8), (3, 1))
+    assert np.all(run(bg, n, u, hel, cols, bg.BG_F32, pt_min=-1.0) == 0.0)
+    # events failing the cut get 0
+    cut = run(bg, n, u, hel, inputs.balanced_flow_colours(n, 3, seed=150), bg.BG_F32, pt_min=400.0)
+    assert np.all(cut == 0.0)
+    # invalid colour label -> device status, event 0
+    bg.device_status_reset()
+    cols = np.full((3, 2 * n), 4, dtype=np.int8)
+    assert np.all(run(bg, n, u, hel, cols, bg.BG_F32, pt_min=-1.0) == 0.0)
+    assert bg.device_status() == bg.BG_EINVAL
+    bg.device_status_reset()
+    with pytest.raises(bg.BGError) as ei:
+        bg.currents_co_mc(13, z, z, z)
+    assert ei.value.code == bg.BG_EINVAL
