@@ -334,8 +334,11 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
   for (long long w0 = 0; w0 < total; w0 += CAP) {
     const long long w1 = (total - w0 < CAP) ? total : w0 + CAP;
     for (int el = tid; el < EB; el += NT) {
+      // (events without items -- failing the cut, invalid or without a
+      // closing order -- have lo == hi and are not walked)
       const long long lo = s_off[el], hi = s_off[el + 1];
-      if (hi <= w0 || lo >= w1) continue;
+      if (hi <= lo || hi <= w0 || lo >= w1) continue;
+      const long long stop = hi < w1 ? hi : w1;
       const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
       comc_walk<N>(rm, s_cf[el * 4 + 3] & 0x00FFFFFFu, [&](uint64_t pk, int64_t r) {
         const long long g = lo + r;
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
           s_item[g - w0] = pk;
           s_iev[g - w0] = (uint16_t)el;
         }
-        return g + 1 < w1;
+        return g + 1 < stop;
       });
     }
     __syncthreads();
