@@ -780,7 +780,8 @@ def run_comc(args) -> None:
     n_dom = max(COMC_NS, key=lambda n: kernel_ms[n][1])
     acc_np = ACC[n_dom].cpu().numpy().astype(bool)
     n_orders = int(orders[n_dom][acc_np].sum())
-    flops = canonical_recursion_flops(n_dom) * n_orders
+    per_order = canonical_recursion_flops(n_dom) // math.factorial(n_dom - 2)
+    flops = per_order * n_orders
     achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
@@ -805,7 +806,7 @@ def run_comc(args) -> None:
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "flops_model": "canonical recursion FLOPs of one order x closing orders of the events "
                                         "passing the cut",
-                         "flops_per_order": canonical_recursion_flops(n_dom), "orders_computed": n_orders,
+                         "flops_per_order": per_order, "orders_computed": n_orders,
                          "peak_source": peak_source},
             "e2e": {"value": world * len(COMC_NS) * batch * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(COMC_NS) * batch * 8},
@@ -876,7 +877,7 @@ def run_lc(args) -> None:
             raise RuntimeError(f"e2e leading-colour |M|^2 differs from the device-resident run at n={n}")
     h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in NS)
     n_dom = max(NS, key=lambda n: kernel_ms[n][1])
-    flops = canonical_recursion_flops(n_dom) * math.factorial(n_dom - 1) * batch
+    flops = canonical_recursion_flops(n_dom) * (n_dom - 1) * batch  # (n-1)! orders = (n-1) x (n-2)!
     achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
@@ -898,7 +899,7 @@ def run_lc(args) -> None:
                          "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "flops_model": "canonical recursion FLOPs per order x (n-1)! orders x events",
-                         "flops_per_event": canonical_recursion_flops(n_dom) * math.factorial(n_dom - 1),
+                         "flops_per_event": canonical_recursion_flops(n_dom) * (n_dom - 1),
                          "peak_source": peak_source},
             "e2e": {"value": world * len(NS) * batch * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(NS) * batch * 8},

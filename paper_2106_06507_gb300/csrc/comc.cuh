@@ -48,13 +48,20 @@ struct ComcParams {
   double scale;  // 9^n 2^n g^(2n-4) sqrt_s^(8-2n) 2^-(n-2)
 };
 
+// TAB (n >= 10; FP64 from n = 8): the current table of the order being
+// evaluated lives in shared memory (one slice per thread) instead of
+// registers: a register table of 4 n(n-1)/2 values spills there, and the
+// spilled stacks of the resident threads outgrow L1.
 template <int N, typename T>
 struct ComcShape {
-  static constexpr int NT = 128;
+  static constexpr bool TAB = N >= 10 || (sizeof(T) == 8 && N >= 8);
+  static constexpr int NT = (TAB && sizeof(T) == 8) ? 64 : 128;
   static constexpr int M = N - 1;
   static constexpr int NPAIR = N * (N - 1) / 2;
+  static constexpr int NSEG = M * (M + 1) / 2;  // segments (i..j), i <= j, of the off-shell current
+  static constexpr int NSLOT = NSEG + N;         // + prefix sums S_0..S_M of the ordered momenta
   static constexpr int EB = N <= 7 ? 256 : N == 8 ? 128 : N == 9 ? 64 : N <= 11 ? 32 : 16;
-  static constexpr int CAP = 2048;  // items per window
+  static constexpr int CAP = TAB ? 1024 : 2048;  // items per window
 };
 
 // Pair invariants and running P^2 sums: two floats (value + error) for the
@@ -105,8 +112,101 @@ struct ComcSmem {
   static constexpr size_t off_off = off_acc + 8 * S::EB;                              // i64 [EB+1]
   static constexpr size_t off_cf = a16(off_off + 8 * (S::EB + 1));                   // u32 [EB][4]
   static constexpr size_t off_iev = off_cf + 16 * S::EB;                              // u16 [CAP]
-  static constexpr size_t bytes = a16(off_iev + 2 * S::CAP);
+  static constexpr size_t off_tab = a16(off_iev + 2 * S::CAP);                        // T [NSEG][NT][4] (TAB)
+  static constexpr size_t bytes = off_tab + (S::TAB ? sizeof(T) * S::NSLOT * S::NT * 4 : 0);
 };
+
+// Current table in shared memory: segment (i..j), i <= j, of thread t at
+// tab[(seg(i, j) * NT + t) * 4], four consecutive values (one 16-byte load in
+// FP32), consecutive threads in consecutive slots; the prefix sums S_p of the
+// ordered momenta in slots NSEG + p.
+template <int N>
+__host__ __device__ constexpr int comc_seg(int i, int j) {
+  return i * (N - 1) - i * (i - 1) / 2 + (j - i);
+}
+// The loads are volatile so that the compiler keeps them in program order
+// instead of hoisting the whole unrolled recursion's loads ahead of their use
+// (which needs more than 255 registers and spills).
+template <int NT>
+__device__ __forceinline__ void tab_ld(const float* __restrict__ tab, int seg, float (&v)[4]) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(tab + (size_t)seg * NT * 4);
+  asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+               : "r"(a));
+}
+template <int NT>
+__device__ __forceinline__ void tab_st(float* __restrict__ tab, int seg, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(tab + (size_t)seg * NT * 4) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <int NT>
+__device__ __forceinline__ void tab_ld(const double* __restrict__ tab, int seg, double (&v)[4]) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(tab + (size_t)seg * NT * 4);
+  asm volatile("ld.volatile.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+  asm volatile("ld.volatile.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[2]), "=d"(v[3]) : "r"(a + 16));
+}
+template <int NT>
+__device__ __forceinline__ void tab_st(double* __restrict__ tab, int seg, const double (&v)[4]) {
+  *reinterpret_cast<double2*>(tab + (size_t)seg * NT * 4) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(tab + (size_t)seg * NT * 4 + 2) = make_double2(v[2], v[3]);
+}
+
+// Bracket of segment (i..j) (the V3 and V4 sums before the propagator, unit
+// vertex factors) from the shared-memory table: the same terms as the
+// register form of the colour-ordered kernels, with the loop over the second
+// split point outermost so that only the row J(i..s) stays in registers:
+// J(t+1..j) is loaded once per t, the interior J(s+1..t) as it is used, and
+// the coefficient of J(t+1..j) is complete (and applied) at the end of
+// iteration t.
+template <int N, typename T, int NT>
+__device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, const int i, const int j, T (&br)[4]) {
+  constexpr int M = N - 1, NSEG = M * (M + 1) / 2;
+  T X[M][4];
+#pragma unroll
+  for (int s = i; s < j; ++s) tab_ld<NT>(tab, comc_seg<N>(i, s), X[s]);
+  T Si[4], Sj[4], P2[4];
+  tab_ld<NT>(tab, NSEG + i, Si);
+  tab_ld<NT>(tab, NSEG + j + 1, Sj);
+  sub4(Sj, Si, P2);
+  scale4(T(2), P2, P2);
+  T by[4], W[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) { br[m] = T(0); by[m] = T(0); W[m] = T(0); }
+  T sxy = T(0);
+  T cX[M];
+#pragma unroll
+  for (int t = i; t < j; ++t) {
+    T Z[4], St[4];
+    tab_ld<NT>(tab, comc_seg<N>(t + 1, j), Z);
+    tab_ld<NT>(tab, NSEG + t + 1, St);
+    // three-vertex term of the split at t
+    const T xy0 = mdot(X[t], Z);
+    sxy += xy0;
+    axpy4(xy0, St, W);
+    cX[t] = -mdot(P2, Z);
+    T cR = mdot(P2, X[t]);
+    // four-vertex terms (s, t): X = J(i..s), Y = J(s+1..t), Z = J(t+1..j)
+#pragma unroll
+    for (int s = i; s < t; ++s) {
+      T Y[4];
+      tab_ld<NT>(tab, comc_seg<N>(s + 1, t), Y);
+      const T xz = mdot(X[s], Z);
+      const T xy = mdot(X[s], Y);
+      const T yz = mdot(Y, Z);
+      cX[s] -= yz;
+      cR -= xy;
+      axpy4(xz, Y, by);
+    }
+    axpy4(cR, Z, br);
+  }
+#pragma unroll
+  for (int s = i; s < j; ++s) axpy4(cX[s], X[s], br);
+  T t4[4], u4[4];
+  add4(W, by, t4);
+  add4(Si, Sj, u4);
+  add4(t4, t4, t4);
+  axpy4(-sxy, u4, t4);
+  add4(br, t4, br);
+}
 
 // Depth-first walk over the orders (0, g_1, ..., g_{N-1}) (0-based labels)
 // whose colour chain closes: the row colour of each gluon equals the column
@@ -207,6 +307,66 @@ __device__ __forceinline__ T comc_amplitude(uint64_t packed, const T* __restrict
   return amp;
 }
 
+// The same with the current table in shared memory (tab: this thread's
+// slice, see tab_ld).
+template <int N, typename T, typename PT, int NT>
+__device__ __forceinline__ T comc_amplitude_tab(uint64_t packed, const T* __restrict__ ke, const T* __restrict__ ee,
+                                                const PT* __restrict__ pr, T* __restrict__ tab) {
+  constexpr int M = N - 1, NSEG = M * (M + 1) / 2;
+  int gl[N];
+  gl[0] = 0;
+#pragma unroll
+  for (int pos = 1; pos < N; ++pos) gl[pos] = (int)((packed >> (4 * (pos - 1))) & 15u);
+  {
+    T S[4] = {T(0), T(0), T(0), T(0)};
+    tab_st<NT>(tab, NSEG, S);
+#pragma unroll
+    for (int pos = 0; pos < M; ++pos) {
+      const int g = gl[pos];
+      T v[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        v[m] = ee[g * 4 + m];
+        S[m] += ke[g * 4 + m];
+      }
+      tab_st<NT>(tab, comc_seg<N>(pos, pos), v);
+      tab_st<NT>(tab, NSEG + pos + 1, S);
+    }
+  }
+  PT p2[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) p2_zero(p2[i]);
+  T amp = T(0);
+#pragma unroll
+  for (int j = 1; j < M; ++j) {
+    PT c;
+    p2_zero(c);
+#pragma unroll
+    for (int i = j - 1; i >= 0; --i) {
+      T br[4];
+      comc_bracket_tab<N, T, NT>(tab, i, j, br);
+      if (i == 0 && j == M - 1) {
+        T en[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) en[m] = ee[gl[N - 1] * 4 + m];
+        amp = mdot(en, br);
+      } else {
+        const int a = min(gl[i], gl[j]), b = max(gl[i], gl[j]);
+        c = p2_add(c, pr[a * N - a * (a + 1) / 2 + (b - a - 1)]);
+        p2[i] = p2_add(p2[i], c);
+        const T ip = T(1) / T(p2_value(p2[i]));
+        T J[4];
+        scale4(ip, br, J);
+        tab_st<NT>(tab, comc_seg<N>(i, j), J);
+      }
+      // table values are reloaded by each segment rather than kept live in
+      // registers across segments (which would spill)
+      asm volatile("" ::: "memory");
+    }
+  }
+  return amp;
+}
+
 template <int N, typename T>
 __global__ void __launch_bounds__(ComcShape<N, T>::NT)
     comc_kernel(ComcParams prm, const double* __restrict__ p, const int8_t* __restrict__ hel,
@@ -295,10 +455,18 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
         cp |= (uint32_t)(cc - 1) << (2 * g);
       }
     }
+    // a chain can close only if every colour is as often a row as a column
+    // colour: other flows have no closing order and are not walked
+    uint32_t bal = 1;
+    if (ok) {
+      int nc[3] = {0, 0, 0};
+      for (int g = 0; g < N; ++g) ++nc[(cp >> (2 * g)) & 3u];
+      bal = (__popc(rm0) == nc[0] && __popc(rm1) == nc[1] && __popc(rm2) == nc[2]) ? 1u : 0u;
+    }
     s_cf[el * 4 + 0] = rm0;
     s_cf[el * 4 + 1] = rm1;
     s_cf[el * 4 + 2] = rm2;
-    s_cf[el * 4 + 3] = cp | (ok << 30);
+    s_cf[el * 4 + 3] = cp | (ok << 30) | (bal << 29);
   }
   __syncthreads();
 
@@ -307,7 +475,8 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
     const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
     const uint32_t w = s_cf[el * 4 + 3];
     int64_t cnt = 0;
-    if ((w >> 30) & 1u) cnt = comc_walk<N>(rm, w & 0x00FFFFFFu, [](uint64_t, int64_t) { return true; });
+    if (((w >> 30) & 1u) && ((w >> 29) & 1u))
+      cnt = comc_walk<N>(rm, w & 0x00FFFFFFu, [](uint64_t, int64_t) { return true; });
     s_off[el + 1] = (long long)cnt;
     s_acc[el] = 0.0;
   }
@@ -353,7 +522,12 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
     const int nw = (int)(w1 - w0);
     for (int it = tid; it < nw; it += NT) {
       const int el = s_iev[it];
-      s_amp[it] = comc_amplitude<N, T, PT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4, s_pair + el * NPAIR);
+      if constexpr (S::TAB)
+        s_amp[it] = comc_amplitude_tab<N, T, PT, NT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4,
+                                                     s_pair + el * NPAIR,
+                                                     reinterpret_cast<T*>(smem + L::off_tab) + tid * 4);
+      else
+        s_amp[it] = comc_amplitude<N, T, PT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4, s_pair + el * NPAIR);
     }
     __syncthreads();
     for (int el = tid; el < EB; el += NT) {

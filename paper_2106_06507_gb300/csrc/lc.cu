@@ -15,7 +15,11 @@
 namespace bg {
 namespace {
 
-// p2, hel2: the inputs with gluons l and n-1 (0-based) exchanged.
+// p2, hel2: the inputs with gluons l and n-1 (0-based) exchanged.  The
+// recursion takes positions 0 and 1 as the incoming gluons (k = -p there), so
+// a momentum that moves between an incoming and an outgoing position changes
+// sign: every position then yields the all-outgoing momentum of the gluon
+// it now holds.
 __global__ void lc_relabel_kernel(int n, int l, int64_t B, const double* __restrict__ p,
                                   const int8_t* __restrict__ hel, double* __restrict__ p2,
                                   int8_t* __restrict__ hel2) {
@@ -23,8 +27,9 @@ __global__ void lc_relabel_kernel(int n, int l, int64_t B, const double* __restr
   if (e >= B) return;
   for (int g = 0; g < n; ++g) {
     const int src = g == l ? n - 1 : (g == n - 1 ? l : g);
+    const double sg = ((g < 2) != (src < 2)) ? -1.0 : 1.0;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) p2[((int64_t)m * n + g) * B + e] = p[((int64_t)m * n + src) * B + e];
+    for (int m = 0; m < 4; ++m) p2[((int64_t)m * n + g) * B + e] = sg * p[((int64_t)m * n + src) * B + e];
     if (hel) hel2[(int64_t)g * B + e] = hel[(int64_t)src * B + e];
   }
 }
