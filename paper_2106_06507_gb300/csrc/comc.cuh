@@ -21,8 +21,9 @@
 //   2. one thread per event walks the orders whose chain closes (depth-first,
 //      labels in increasing order) and counts them; a warp scan gives each
 //      event its range of item indices;
-//   3. in windows of CAP items: the walk is repeated to write the packed
-//      orders of the window into shared memory, then every thread takes
+//   3. in windows of CAP items: each event's walk is resumed where the last
+//      window paused it, writing the packed orders of the window into shared
+//      memory (an event is walked once in total), then every thread takes
 //      items and evaluates the whole recursion of one order (same code path
 //      for every item), and one thread per event adds its items' amplitudes
 //      in item order (deterministic);
@@ -60,8 +61,8 @@ struct ComcShape {
   static constexpr int NPAIR = N * (N - 1) / 2;
   static constexpr int NSEG = M * (M + 1) / 2;  // segments (i..j), i <= j, of the off-shell current
   static constexpr int NSLOT = NSEG + N;         // + prefix sums S_0..S_M of the ordered momenta
-  static constexpr int EB = N <= 7 ? 256 : N == 8 ? 128 : N == 9 ? 64 : N <= 11 ? 32 : 16;
-  static constexpr int CAP = TAB ? 1024 : 2048;  // items per window
+  static constexpr int EB = N <= 8 ? 128 : N == 9 ? 64 : N <= 11 ? 32 : 16;
+  static constexpr int CAP = TAB ? (sizeof(T) == 8 ? 512 : 1024) : 2048;  // items per window
 };
 
 // Pair invariants and running P^2 sums: two floats (value + error) for the
@@ -98,23 +99,6 @@ __device__ __forceinline__ double p2_add(double a, double b) { return a + b; }
 __device__ __forceinline__ float p2_value(float2 a) { return __fadd_rn(a.x, a.y); }
 __device__ __forceinline__ double p2_value(double a) { return a; }
 
-template <int N, typename T>
-struct ComcSmem {
-  using S = ComcShape<N, T>;
-  using PT = typename ComcPair<T>::type;
-  static constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
-  static constexpr size_t off_k = 0;                                                 // T [EB][N][4]
-  static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                 // T [EB][N][4]
-  static constexpr size_t off_pair = a16(off_e + sizeof(T) * S::EB * N * 4);         // PT [EB][NPAIR]
-  static constexpr size_t off_item = a16(off_pair + sizeof(PT) * S::EB * S::NPAIR);  // u64 [CAP]
-  static constexpr size_t off_amp = off_item + 8 * S::CAP;                            // T [CAP]
-  static constexpr size_t off_acc = a16(off_amp + sizeof(T) * S::CAP);               // double [EB]
-  static constexpr size_t off_off = off_acc + 8 * S::EB;                              // i64 [EB+1]
-  static constexpr size_t off_cf = a16(off_off + 8 * (S::EB + 1));                   // u32 [EB][4]
-  static constexpr size_t off_iev = off_cf + 16 * S::EB;                              // u16 [CAP]
-  static constexpr size_t off_tab = a16(off_iev + 2 * S::CAP);                        // T [NSEG][NT][4] (TAB)
-  static constexpr size_t bytes = off_tab + (S::TAB ? sizeof(T) * S::NSLOT * S::NT * 4 : 0);
-};
 
 // Current table in shared memory: segment (i..j), i <= j, of thread t at
 // tab[(seg(i, j) * NT + t) * 4], four consecutive values (one 16-byte load in
@@ -213,43 +197,75 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
 // colour of the gluon before it, and the column colour of the last gluon
 // equals the row colour of gluon 0.  rm[c]: mask of the gluons with row
 // colour c; cp: column colours, 2 bits per gluon.  Orders are visited in
-// lexicographic order of their labels; visit(packed, index) gets the labels
-// of positions 1..N-1 packed 4 bits each and returns false to stop.  Returns
-// the number of orders visited.
-template <int N, typename F>
-__device__ __forceinline__ int64_t comc_walk(const uint32_t (&rm)[3], uint32_t cp, F&& visit) {
-  const int r0 = (rm[0] & 1u) ? 0 : ((rm[1] & 1u) ? 1 : 2);
-  uint32_t cand[N];
-  int gl[N];
-  uint32_t avail = ((1u << N) - 1u) & ~1u;
-  uint64_t packed = 0;
-  int64_t cnt = 0;
-  int d = 1;
-  cand[1] = avail & rm[cp & 3u];
-  while (d > 0) {
-    if (cand[d]) {
-      const int g = __ffs(cand[d]) - 1;
-      cand[d] &= cand[d] - 1u;
-      const uint64_t pk = (packed & ~(0xFull << (4 * (d - 1)))) | ((uint64_t)g << (4 * (d - 1)));
-      if (d == N - 1) {
-        if ((int)((cp >> (2 * g)) & 3u) == r0) {
-          if (!visit(pk, cnt)) return cnt + 1;
-          ++cnt;
-        }
-        continue;
-      }
-      packed = pk;
-      gl[d] = g;
-      avail &= ~(1u << g);
-      ++d;
-      cand[d] = avail & rm[(cp >> (2 * g)) & 3u];
-    } else {
-      --d;
-      if (d > 0) avail |= 1u << gl[d];
-    }
+// lexicographic order of their labels; visit(packed) gets the labels of
+// positions 1..N-1 packed 4 bits each and returns false to pause the walk
+// after that order.  The state (depth, candidates left per depth, labels
+// chosen, gluons still free) can be saved and the walk resumed where it
+// paused, so that an event whose orders span several windows is walked once
+// in total.
+template <int N>
+struct ComcWalk {
+  uint64_t packed;
+  uint32_t avail;
+  int d;
+  uint16_t cand[N];
+  uint8_t gl[N];
+
+  __device__ __forceinline__ void start(const uint32_t (&rm)[3], uint32_t cp) {
+    packed = 0;
+    avail = ((1u << N) - 1u) & ~1u;
+    d = 1;
+    cand[1] = avail & rm[cp & 3u];
   }
-  return cnt;
-}
+  // Returns the number of orders visited before the walk ended or paused.
+  template <typename F>
+  __device__ __forceinline__ int64_t run(const uint32_t (&rm)[3], uint32_t cp, F&& visit) {
+    const int r0 = (rm[0] & 1u) ? 0 : ((rm[1] & 1u) ? 1 : 2);
+    int64_t cnt = 0;
+    while (d > 0) {
+      if (cand[d]) {
+        const int g = __ffs(cand[d]) - 1;
+        cand[d] &= cand[d] - 1u;
+        const uint64_t pk = (packed & ~(0xFull << (4 * (d - 1)))) | ((uint64_t)g << (4 * (d - 1)));
+        if (d == N - 1) {
+          if ((int)((cp >> (2 * g)) & 3u) == r0) {
+            ++cnt;
+            if (!visit(pk)) return cnt;
+          }
+          continue;
+        }
+        packed = pk;
+        gl[d] = g;
+        avail &= ~(1u << g);
+        ++d;
+        cand[d] = avail & rm[(cp >> (2 * g)) & 3u];
+      } else {
+        --d;
+        if (d > 0) avail |= 1u << gl[d];
+      }
+    }
+    return cnt;
+  }
+};
+
+template <int N, typename T>
+struct ComcSmem {
+  using S = ComcShape<N, T>;
+  using PT = typename ComcPair<T>::type;
+  static constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
+  static constexpr size_t off_k = 0;                                                 // T [EB][N][4]
+  static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                 // T [EB][N][4]
+  static constexpr size_t off_pair = a16(off_e + sizeof(T) * S::EB * N * 4);         // PT [EB][NPAIR]
+  static constexpr size_t off_item = a16(off_pair + sizeof(PT) * S::EB * S::NPAIR);  // u64 [CAP]
+  static constexpr size_t off_amp = off_item + 8 * S::CAP;                            // T [CAP]
+  static constexpr size_t off_acc = a16(off_amp + sizeof(T) * S::CAP);               // double [EB]
+  static constexpr size_t off_off = off_acc + 8 * S::EB;                              // i64 [EB+1]
+  static constexpr size_t off_cf = a16(off_off + 8 * (S::EB + 1));                   // u32 [EB][4]
+  static constexpr size_t off_iev = off_cf + 16 * S::EB;                              // u16 [CAP]
+  static constexpr size_t off_walk = a16(off_iev + 2 * S::CAP);                       // walk states [EB]
+  static constexpr size_t off_tab = a16(off_walk + sizeof(ComcWalk<N>) * S::EB);       // T [NSLOT][NT][4] (TAB)
+  static constexpr size_t bytes = off_tab + (S::TAB ? sizeof(T) * S::NSLOT * S::NT * 4 : 0);
+};
 
 // Colour-ordered amplitude A(g_0, ..., g_{N-1}) of one order with unit vertex
 // factors (Eqs. 2.20-2.22).  ke, ee: the event's momenta and polarisations
@@ -390,6 +406,7 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
   long long* s_off = reinterpret_cast<long long*>(smem + L::off_off);
   uint32_t* s_cf = reinterpret_cast<uint32_t*>(smem + L::off_cf);
   uint16_t* s_iev = reinterpret_cast<uint16_t*>(smem + L::off_iev);
+  ComcWalk<N>* s_walk = reinterpret_cast<ComcWalk<N>*>(smem + L::off_walk);
   const int tid = threadIdx.x;
 
   // ---- 1. momenta, polarisations, pair invariants, colour flows
@@ -475,8 +492,11 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
     const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
     const uint32_t w = s_cf[el * 4 + 3];
     int64_t cnt = 0;
-    if (((w >> 30) & 1u) && ((w >> 29) & 1u))
-      cnt = comc_walk<N>(rm, w & 0x00FFFFFFu, [](uint64_t, int64_t) { return true; });
+    if (((w >> 30) & 1u) && ((w >> 29) & 1u)) {
+      ComcWalk<N> wk;
+      wk.start(rm, w & 0x00FFFFFFu);
+      cnt = wk.run(rm, w & 0x00FFFFFFu, [](uint64_t) { return true; });
+    }
     s_off[el + 1] = (long long)cnt;
     s_acc[el] = 0.0;
   }
@@ -507,16 +527,25 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
       // closing order -- have lo == hi and are not walked)
       const long long lo = s_off[el], hi = s_off[el + 1];
       if (hi <= lo || hi <= w0 || lo >= w1) continue;
+      // the event's orders lo + r, r = 0, 1, ..., are written from where its
+      // walk paused at the end of the previous window
       const long long stop = hi < w1 ? hi : w1;
       const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
-      comc_walk<N>(rm, s_cf[el * 4 + 3] & 0x00FFFFFFu, [&](uint64_t pk, int64_t r) {
-        const long long g = lo + r;
-        if (g >= w0) {
-          s_item[g - w0] = pk;
-          s_iev[g - w0] = (uint16_t)el;
-        }
-        return g + 1 < stop;
+      const uint32_t cp = s_cf[el * 4 + 3] & 0x00FFFFFFu;
+      ComcWalk<N> wk;
+      if (lo >= w0) {
+        wk.start(rm, cp);
+      } else {
+        wk = s_walk[el];
+      }
+      long long g = lo > w0 ? lo : w0;
+      wk.run(rm, cp, [&](uint64_t pk) {
+        s_item[g - w0] = pk;
+        s_iev[g - w0] = (uint16_t)el;
+        ++g;
+        return g < stop;
       });
+      if (hi > w1) s_walk[el] = wk;
     }
     __syncthreads();
     const int nw = (int)(w1 - w0);
