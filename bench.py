@@ -1043,8 +1043,8 @@ def run_mixed(args) -> None:
 
 def run_profile_case(args) -> None:
     """A small case of one multiplicity for ncu captures: `warmup` steps, then
-    one step (Rambo, recursion, colour sum; with --workload cd: Rambo once,
-    then the colour-dressed recursion), on cuda:0."""
+    one step (Rambo, recursion, colour sum; with --workload cd or comc: Rambo
+    once, then the colour-dressed or colour-flow recursion), on cuda:0."""
     import numpy as np
     import torch
 
@@ -1061,6 +1061,17 @@ def run_profile_case(args) -> None:
             me2 = bg.currents_cd(n, p, h, c, prec=bg.BG_F32, sqrt_s=SQRT_S, accept=acc)
         torch.cuda.synchronize(dev)
         print(json.dumps({"profile_case": {"workload": "cd", "n": n, "batch": B,
+                                           "sum_me2": float(me2.sum().item())}}), flush=True)
+        return
+    if args.workload == "comc":
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
+        c = torch.from_numpy(np.ascontiguousarray(inputs.flow_colours(n, B, seed=SEED).T)).to(dev)
+        p, acc = bg.momenta_rambo(n, u, SQRT_S, PT_MIN)
+        for _ in range(args.warmup + 1):
+            me2 = bg.currents_co_mc(n, p, h, c, prec=bg.BG_F32, sqrt_s=SQRT_S, accept=acc)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_case": {"workload": "comc", "n": n, "batch": B,
                                            "sum_me2": float(me2.sum().item())}}), flush=True)
         return
     u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
