@@ -56,7 +56,9 @@ struct ComcParams {
 template <int N, typename T>
 struct ComcShape {
   static constexpr bool TAB = N >= 10 || (sizeof(T) == 8 && N >= 8);
-  static constexpr int NT = (TAB && sizeof(T) == 8) ? 64 : 128;
+  // 64 threads with the shared-memory table: two blocks per SM, so that one
+  // block's per-event phases (walks, sums) overlap the other's recursions
+  static constexpr int NT = TAB ? 64 : 128;
   static constexpr int M = N - 1;
   static constexpr int NPAIR = N * (N - 1) / 2;
   static constexpr int NSEG = M * (M + 1) / 2;  // segments (i..j), i <= j, of the off-shell current
