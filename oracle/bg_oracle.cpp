@@ -19,6 +19,8 @@
 //   * colour-dressed currents, Eqs. (2.28)-(2.32)
 //   * colour-flow sampling with colour-ordered amplitudes, Eq. (2.19)
 //   * the leading-colour sum of Sec. 4
+//   * continuous colour and helicity sampling for the colour-dressed
+//     recursion (Sec. 2.1: colour polarisation vectors, polarisation angle)
 // Equation numbers count the paper's numbered equations within Sec. 2.
 //
 // Conventions (the paper leaves these open; each reading is listed in the
@@ -697,6 +699,83 @@ void me2_co_mc_batch(int n, long long B, double sqrt_s, const double* u, const d
   for (auto& x : th) x.join();
 }
 
+// Continuous colour and helicity sampling (Sec. 2.1): per gluon two real unit
+// colour vectors eta(theta, phi), eta_bar(theta_bar, phi_bar) in the angle
+// form of the paper, the gluon colour polarisation eta^a = eta_i T^a_ij
+// eta_bar_j (Eq. of the gluon colour polarisation), and the polarisation
+// vector e(phi_h) = cos(phi_h) e1 + sin(phi_h) e2.  The external colour matrix
+// of the colour-dressed recursion is sum_a eta^a T^a, built here from the
+// Gell-Mann generators (complex arithmetic; the result is real).
+// ang[5]: cos(theta), phi, cos(theta_bar), phi_bar, phi_h.
+void continuous_external(const double* ang, double E[3][3]) {
+  cplx T[8][3][3];
+  generators(T);
+  double eta[3], etab[3];
+  for (int v = 0; v < 2; ++v) {
+    const double ct = ang[2 * v], ph = ang[2 * v + 1];
+    const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+    double* x = v ? etab : eta;
+    x[0] = ct;
+    x[1] = st * std::cos(ph);
+    x[2] = st * std::sin(ph);
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      cplx acc = 0.0;
+      for (int a = 0; a < 8; ++a) {
+        cplx ea = 0.0;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) ea += eta[i] * T[a][i][j] * etab[j];
+        acc += ea * T[a][k][l];
+      }
+      E[k][l] = acc.real();
+    }
+}
+
+// Batch |M|^2 estimator with continuous colour and helicity sampling:
+// ang[B][5n] (per gluon the five angles of continuous_external); weight per
+// gluon N_c^2 = 9 for the two colour spheres (measure N_c / 4 pi each) and 2
+// for the polarisation angle (the average over phi_h of e e is half the
+// polarisation sum); times g^(2n-4).  Events failing the pT cut get 0.
+template <class T>
+void me2_cd_cont_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const double* ang,
+                       double g, double pt_min, double* me2, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::thread> th;
+  const int d = 4 * (n - 2);
+  for (int t = 0; t < nthreads; ++t)
+    th.emplace_back([&, t]() {
+      std::vector<Vec<T>> p(n), k(n), eps(n);
+      std::vector<T> ul(d);
+      std::vector<double> E(n * 9);
+      for (long long e = t; e < B; e += nthreads) {
+        for (int i = 0; i < d; ++i) ul[i] = T(u[e * d + i]);
+        rambo(n, sqrt_s, ul.data(), p.data());
+        bool cut = false;
+        for (int i = 2; i < n; ++i)
+          if (std::sqrt(value(p[i].c[1]) * value(p[i].c[1]) + value(p[i].c[2]) * value(p[i].c[2])) <= pt_min)
+            cut = true;
+        if (cut) { me2[e] = 0.0; continue; }
+        outgoing(n, p.data(), k.data());
+        for (int i = 0; i < n; ++i) {
+          const double* a = ang + (e * n + i) * 5;
+          Vec<T> e1, e2;
+          polarisations(k[i], q, &e1, &e2);
+          const T c = T(std::cos(a[4])), sn = T(std::sin(a[4]));
+          for (int m = 0; m < 4; ++m) eps[i].c[m] = c * e1.c[m] + sn * e2.c[m];
+          double M[3][3];
+          continuous_external(a, M);
+          for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) E[i * 9 + r * 3 + cc] = M[r][cc];
+        }
+        T a = amp_cd(n, k.data(), eps.data(), reinterpret_cast<const double(*)[3][3]>(E.data()));
+        const double w = std::pow(9.0, n) * std::pow(2.0, n) * std::pow(g, 2 * n - 4);
+        me2[e] = (double)(T(w) * a * a);
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -932,6 +1011,25 @@ void or_me2_lc_batch(int n, long long B, double sqrt_s, const double* u, const d
       }
     });
   for (auto& x : th) x.join();
+}
+
+// Continuous colour and helicity sampling (me2_cd_cont_batch).
+void or_me2_cd_cont_batch(int n, long long B, double sqrt_s, const double* u, const double* q, const double* ang,
+                          double g, double pt_min, double* me2, int nthreads) {
+  me2_cd_cont_batch<double>(n, B, sqrt_s, u, q, ang, g, pt_min, me2, nthreads);
+}
+
+void or_me2_cd_cont_batch_ext(int n, long long B, double sqrt_s, const double* u, const double* q,
+                              const double* ang, double g, double pt_min, double* me2, int nthreads) {
+  me2_cd_cont_batch<long double>(n, B, sqrt_s, u, q, ang, g, pt_min, me2, nthreads);
+}
+
+// Continuous external colour matrix of one gluon from its five angles.
+void or_continuous_external(const double* ang, double* E) {
+  double M[3][3];
+  continuous_external(ang, M);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) E[i * 3 + j] = M[i][j];
 }
 
 // Gradient of the colour-summed |M|^2 (sampled helicity hel[n]) with

@@ -78,6 +78,9 @@ def lib():
             L.or_me2_co_mc_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_co_mc_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, i8p, c_dbl, c_dbl, dp, c_int]
             L.or_me2_lc_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, i8p, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_cd_cont_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, c_dbl, c_dbl, dp, c_int]
+            L.or_me2_cd_cont_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, c_dbl, c_dbl, dp, c_int]
+            L.or_continuous_external.argtypes = [dp, dp]
             L.or_me2_co_grad.argtypes = [c_int, c_dbl, dp, dp, dp, i8p, c_dbl, dp]
             L.or_me2_co_grad.restype = c_dbl
             _lib = L
@@ -408,6 +411,31 @@ def me2_lc(n, u, hel=None, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.
     me2 = np.zeros(B)
     lib().or_me2_lc_batch(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, hp, g, pt_min,
                           me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
+    return me2
+
+
+def continuous_external(ang) -> np.ndarray:
+    """External colour matrix sum_a eta^a T^a of one gluon from its five
+    angles (cos theta, phi, cos theta_bar, phi_bar, phi_h)."""
+    a, ap = _d(np.asarray(ang, dtype=np.float64).reshape(5))
+    E = np.zeros((3, 3))
+    lib().or_continuous_external(ap, E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return E
+
+
+def me2_cd_cont(n, u, ang, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.0, nthreads=None,
+                ext=False) -> np.ndarray:
+    """Colour-dressed |M|^2 estimator with continuous colour and helicity
+    sampling, ang[B, n, 5] = (cos theta, phi, cos theta_bar, phi_bar, phi_h)
+    per gluon (ext: extended precision)."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
+    B = u.shape[0]
+    q, qp = _d(q)
+    ang, angp = _d(np.asarray(ang, dtype=np.float64).reshape(B, n, 5))
+    me2 = np.zeros(B)
+    fn = lib().or_me2_cd_cont_batch_ext if ext else lib().or_me2_cd_cont_batch
+    fn(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, angp, g, pt_min,
+       me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
     return me2
 
 

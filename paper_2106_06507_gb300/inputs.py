@@ -2,7 +2,8 @@
 
 This module holds no part of the method's arithmetic: it only draws the
 random numbers that the method consumes as inputs (Rambo uniforms, sampled
-helicity labels, sampled colours).  Both the CUDA path and the CPU oracle are
+helicity labels, sampled colours, sampled colour-vector and polarisation
+angles).  Both the CUDA path and the CPU oracle are
 fed the arrays it returns, so that they see identical inputs.
 
 Generator: SplitMix64 (Steele, Lea, Flood 2014) used as a counter-based
@@ -90,6 +91,21 @@ def balanced_flow_colours(n: int, batch: int, seed: int = 0, first_event: int = 
     out = np.empty((batch, 2 * n), dtype=np.int8)
     out[:, 0::2] = rows
     out[:, 1::2] = cols
+    return out
+
+
+def continuous_angles(n: int, batch: int, seed: int = 0, first_event: int = 0) -> np.ndarray:
+    """[batch, n, 5] float64 per gluon: cos(theta), phi, cos(theta_bar),
+    phi_bar of two colour unit vectors drawn uniformly on the sphere
+    (cos theta uniform in (-1, 1), phi uniform in (0, 2 pi)), and a
+    polarisation angle phi_h uniform in (0, 2 pi)."""
+    u = uniforms(seed, STREAM_COLOUR + 16 * n + 4, batch * n * 5, first_event * n * 5).reshape(batch, n, 5)
+    out = np.empty_like(u)
+    out[:, :, 0] = 2.0 * u[:, :, 0] - 1.0
+    out[:, :, 2] = 2.0 * u[:, :, 2] - 1.0
+    out[:, :, 1] = 2.0 * np.pi * u[:, :, 1]
+    out[:, :, 3] = 2.0 * np.pi * u[:, :, 3]
+    out[:, :, 4] = 2.0 * np.pi * u[:, :, 4]
     return out
 
 

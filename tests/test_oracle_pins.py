@@ -411,6 +411,86 @@ def test_leading_colour_gauge_invariant_and_subleading_at_six(oracle):
 
 
 # --------------------------------------------------------------------------
+# Continuous colour and helicity sampling (Sec. 2.1)
+# --------------------------------------------------------------------------
+# Representatives of the 4 antipodal pairs of cube vertices: the average of
+# x_i x_j over them is delta_ij / 3, as over the sphere (|A|^2 is of degree
+# two in every colour vector, so this average is exact).
+CUBE = np.array([[1, 1, 1], [1, 1, -1], [1, -1, 1], [-1, 1, 1]], dtype=np.float64) / math.sqrt(3.0)
+
+
+def unit_vector(ct, ph):
+    """(cos theta, sin theta cos phi, sin theta sin phi)."""
+    st = math.sqrt(max(0.0, 1.0 - ct * ct))
+    return np.array([ct, st * math.cos(ph), st * math.sin(ph)])
+
+
+def angles_of(v):
+    """(cos theta, phi) with v = (cos theta, sin theta cos phi, sin theta sin phi)."""
+    return float(v[0]), float(math.atan2(v[2], v[1]))
+
+
+def test_continuous_external_is_fierz_outer_product(oracle):
+    # sum_a (eta T^a eta_bar) T^a = |eta_bar><eta| - (eta.eta_bar / N) 1
+    rng = np.random.default_rng(20)
+    for _ in range(5):
+        a = np.array([rng.uniform(-1, 1), rng.uniform(0, 6.28), rng.uniform(-1, 1), rng.uniform(0, 6.28), 0.0])
+        eta, etab = unit_vector(a[0], a[1]), unit_vector(a[2], a[3])
+        ref = np.outer(etab, eta) - np.dot(eta, etab) / 3.0 * np.eye(3)
+        assert np.abs(oracle.continuous_external(a) - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_continuous_trace_part_decouples(oracle, n):
+    # the -1/N trace part of sum_a eta^a T^a is a U(1) gluon, which decouples
+    # from all-gluon amplitudes: the outer product |eta_bar><eta| alone gives
+    # the same amplitude
+    _, _, k = event(oracle, n, seed=23)
+    hel = inputs.helicities(n, 1, seed=23)[0]
+    eps = oracle.pols_for(k, hel)
+    ang = inputs.continuous_angles(n, 1, seed=23)[0]
+    E = np.stack([oracle.continuous_external(a) for a in ang])
+    outer = np.stack([np.outer(unit_vector(a[2], a[3]), unit_vector(a[0], a[1])) for a in ang])
+    a1 = oracle.amp_cd(k, eps, E)
+    a2 = oracle.amp_cd(k, eps, outer)
+    assert abs(a1 - a2) <= 1e-12 * abs(a1)
+
+
+def test_continuous_colour_average_is_colour_sum(oracle):
+    # exact average over colour vectors from the cube design (4 x 4 per
+    # gluon) at a fixed polarisation angle 0 (e1 for every gluon) = the
+    # colour-summed |M|^2 of that polarisation configuration
+    n = 4
+    u = inputs.rambo_uniforms(n, 1, seed=21)
+    states = [angles_of(x) + angles_of(y) for x in CUBE for y in CUBE]
+    ang = np.array([[s[0], s[1], s[2], s[3], 0.0] for s in states])
+    combos = np.array(list(itertools.product(range(len(states)), repeat=n)))
+    A = ang[combos]  # [B, n, 5]
+    est = oracle.me2_cd_cont(n, np.repeat(u, A.shape[0], axis=0), A, sqrt_s=SQRT_S)
+    co = oracle.me2_co(n, u, sqrt_s=SQRT_S, hel=np.ones((1, n), dtype=np.int8))
+    assert abs(est.mean() / co[0] - 1.0) < 1e-11
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_continuous_polarisation_average_is_helicity_sum(oracle, n):
+    # the polarisation angle averaged over {0, 2pi/3, 4pi/3} per gluon (exact
+    # for cos^2, sin^2, cos sin) with weight 2 each = the sum over the two
+    # linear polarisations, here for one fixed colour-vector assignment
+    u = inputs.rambo_uniforms(n, 1, seed=22 + n)
+    base = inputs.continuous_angles(n, 1, seed=22 + n)[0]
+    combos = np.array(list(itertools.product(range(3), repeat=n)))
+    A = np.repeat(base[None], combos.shape[0], axis=0).copy()
+    A[:, :, 4] = combos * (2.0 * math.pi / 3.0)
+    est = oracle.me2_cd_cont(n, np.repeat(u, A.shape[0], axis=0), A, sqrt_s=SQRT_S).mean()
+    ref = 0.0
+    for lam in itertools.product((0.0, 0.5 * math.pi), repeat=n):
+        B1 = base.copy()
+        B1[:, 4] = lam
+        ref += oracle.me2_cd_cont(n, u, B1[None], sqrt_s=SQRT_S)[0] / 2 ** n
+    assert abs(est / ref - 1.0) < 1e-11
+
+
+# --------------------------------------------------------------------------
 # P8: gradient with respect to the Rambo uniforms
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [4, 5])
