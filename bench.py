@@ -590,7 +590,11 @@ def run_cd(args) -> None:
     for n in CD_NS:
         u = inputs.rambo_uniforms(n, batch, seed=SEED, first_event=first)
         h = np.ascontiguousarray(inputs.helicities(n, batch, seed=SEED, first_event=first).T)
-        c = np.ascontiguousarray(inputs.adjoint_colours(n, batch, seed=SEED, first_event=first).T)
+        if args.colour_sampling == "continuous":
+            c = np.ascontiguousarray(inputs.continuous_angles(n, batch, seed=SEED, first_event=first)
+                                     .reshape(batch, 5 * n).T)
+        else:
+            c = np.ascontiguousarray(inputs.adjoint_colours(n, batch, seed=SEED, first_event=first).T)
         U[n], HEL[n], COL[n] = (torch.from_numpy(x).to(dev) for x in (u, h, c))
         host[n] = tuple(torch.from_numpy(x).pin_memory() for x in (u, h, c))
         P[n] = torch.empty((4, n, batch), dtype=torch.float64, device=dev)
@@ -599,6 +603,12 @@ def run_cd(args) -> None:
     ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for n in CD_NS}
     kernel_ms = {n: [0.0, 0.0] for n in CD_NS}
 
+    def cd_call(n, p, hel, col, me2):
+        if args.colour_sampling == "continuous":
+            bg.currents_cd_cont(n, p, col, prec=cd_prec, sqrt_s=SQRT_S, accept=ACC[n], me2=me2, stream=stream)
+        else:
+            bg.currents_cd(n, p, hel, col, prec=cd_prec, sqrt_s=SQRT_S, accept=ACC[n], me2=me2, stream=stream)
+
     def step(record=False):
         for n in CD_NS:
             if record:
@@ -606,8 +616,7 @@ def run_cd(args) -> None:
             bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
             if record:
                 ev[n][1].record(stream)
-            bg.currents_cd(n, P[n], HEL[n], COL[n], prec=cd_prec, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
-                           stream=stream)
+            cd_call(n, P[n], HEL[n], COL[n], ME2[n])
             if record:
                 ev[n][2].record(stream)
 
@@ -628,8 +637,7 @@ def run_cd(args) -> None:
             for dst, src in zip(d_in[n], host[n]):
                 dst.copy_(src, non_blocking=True)
             bg.momenta_rambo(n, d_in[n][0], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
-            bg.currents_cd(n, P[n], d_in[n][1], d_in[n][2], prec=cd_prec, sqrt_s=SQRT_S, accept=ACC[n],
-                           me2=ME2[n], stream=stream)
+            cd_call(n, P[n], d_in[n][1], d_in[n][2], ME2[n])
             out_h[n].copy_(ME2[n], non_blocking=True)
 
     e2e_s = timed_host(e2e_step, args, dev)
@@ -650,7 +658,10 @@ def run_cd(args) -> None:
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": ("colour-dressed BG with sampled adjoint colours (1..8), n=8,10,12, "
+            "config": {"workload": (("colour-dressed BG with continuous colour (two unit vectors per gluon) and "
+                                     "polarisation-angle sampling, n=8,10,12, "
+                                     if args.colour_sampling == "continuous" else
+                                     "colour-dressed BG with sampled adjoint colours (1..8), n=8,10,12, ") +
                                     f"{batch} Rambo points per n at sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, "
                                     f"{args.precision.upper()} currents"),
                        "n": list(CD_NS), "batch_per_n": batch, "parallelism": f"replicas x{world}",
@@ -1100,6 +1111,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc"), default="co")
     ap.add_argument("--precision", choices=("f32", "f64"), default="f32",
                     help="recursion arithmetic of the co and cd workloads (f64: the plain FP64 GPU form)")
+    ap.add_argument("--colour-sampling", choices=("adjoint", "continuous"), default="adjoint",
+                    help="colour sampling of the cd workload (continuous: colour vectors and polarisation angles)")
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling case: run only multiplicity n (warm-up steps, then one step)")
     ap.add_argument("--profile-batch", type=int, default=1 << 16)

@@ -301,6 +301,27 @@ bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const
                          void* stream);
 
 /* ---------------------------------------------------------------------------
+ * bg_currents_cd_cont -- the colour-dressed recursion of bg_currents_cd with
+ * continuous colour and helicity sampling (Sec. 2.1): per gluon two real
+ * unit colour vectors eta = (cos t, sin t cos f, sin t sin f) and eta_bar,
+ * the gluon colour polarisation eta^a = eta T^a eta_bar, and the
+ * polarisation vector e = cos(phi_h) e1 + sin(phi_h) e2 (e1, e2 of Eq. 2.7);
+ *   me2 = 9^n * 2^n * g_s^(2n-4) * |A(colour vectors, angles)|^2
+ * for cos t, cos t_bar uniform in (-1, 1) and the angles uniform in
+ * (0, 2 pi) (colour weight N_c per sphere, polarisation weight 2).
+ *   p       [4][n][B]    lab momenta (bg_momenta_rambo)
+ *   ang     [5n][B]      double; rows 5g..5g+4 for gluon g: cos(theta),
+ *                        phi, cos(theta_bar), phi_bar, phi_h
+ *   accept  [B] or NULL  events with accept == 0 get 0
+ *   me2     [B] double   output, GeV^(8-2n)
+ *   workspace: as for bg_currents_cd (bg_cd_workspace_bytes(n, prec)).
+ * Supported: 4 <= n <= 12.  Errors: BG_EINVAL, BG_ECUDA.
+ * ------------------------------------------------------------------------- */
+bg_status bg_currents_cd_cont(int n, int64_t B, double sqrt_s, const double* p, const double* ang, const double* q,
+                              bg_prec prec, double g_s, const uint8_t* accept, double* me2, void* workspace,
+                              int64_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * bg_currents_co_mc -- colour sampling with colour-ordered amplitudes (the
  * colour-sampling variant of the colour-ordered algorithms, Sec. 4, with the
  * colour-flow decomposition of Eq. 2.19): per event one sampled colour flow

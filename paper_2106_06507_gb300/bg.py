@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
+        L.bg_currents_cd_cont.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_currents_co_mc.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, dp, c_int, c_dbl, vp, vp, vp]
         L.bg_lc_workspace_bytes.argtypes = [c_int, c_i64, c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_lc.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
@@ -106,7 +107,7 @@ def lib() -> ctypes.CDLL:
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_probe_fma", "bg_cd_workspace_bytes",
-                     "bg_currents_cd", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
+                     "bg_currents_cd", "bg_currents_cd_cont", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
                      "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
                      "bg_tune_load"):
             getattr(L, name).restype = c_int
@@ -247,6 +248,27 @@ def currents_cd(n: int, p: torch.Tensor, hel: torch.Tensor, colors: torch.Tensor
     _check(lib().bg_currents_cd(n, B, sqrt_s, _ptr(p), _ptr(hel), _ptr(colors),
                                 BG_COL_FLOW if flow else BG_COL_ADJOINT, _q(q), prec, g_s, _ptr(accept), _ptr(me2),
                                 _ptr(workspace), workspace.numel(), _stream(stream)))
+    return me2
+
+
+def currents_cd_cont(n: int, p: torch.Tensor, ang: torch.Tensor, prec: int = BG_F32, sqrt_s: float = 1000.0,
+                     g_s: float = G_S_DEFAULT, q=DEFAULT_Q, accept: torch.Tensor | None = None, me2=None,
+                     workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Colour-dressed |M|^2 estimator with continuous colour and helicity
+    sampling: p [4, n, B] float64, ang [5n, B] float64 (per gluon cos theta,
+    phi, cos theta_bar, phi_bar, phi_h)."""
+    B = p.shape[2]
+    if me2 is None:
+        me2 = torch.empty((B,), dtype=torch.float64, device=p.device)
+    if workspace is None:
+        key = (n, prec, p.device.index)
+        workspace = _cd_ws_cache.get(key)
+        if workspace is None:
+            workspace = torch.empty((cd_workspace_bytes(n, prec),), dtype=torch.uint8, device=p.device)
+            _cd_ws_cache[key] = workspace
+    assert ang.dtype == torch.float64 and ang.is_contiguous() and tuple(ang.shape) == (5 * n, B)
+    _check(lib().bg_currents_cd_cont(n, B, sqrt_s, _ptr(p), _ptr(ang), _q(q), prec, g_s, _ptr(accept), _ptr(me2),
+                                     _ptr(workspace), workspace.numel(), _stream(stream)))
     return me2
 
 

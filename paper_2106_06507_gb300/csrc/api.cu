@@ -274,6 +274,42 @@ bg_status bg_currents_cd(int n, int64_t B, double sqrt_s, const double* p, const
   return cuda_check(e, "bg_currents_cd");
 }
 
+bg_status bg_currents_cd_cont(int n, int64_t B, double sqrt_s, const double* p, const double* ang, const double* q,
+                              bg_prec prec, double g_s, const uint8_t* accept, double* me2, void* workspace,
+                              int64_t workspace_bytes, void* stream) {
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_currents_cd_cont: n must be in 4..12");
+  if (B < 0) return fail(BG_EINVAL, "bg_currents_cd_cont: B < 0");
+  if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_currents_cd_cont: sqrt_s must be > 0");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_currents_cd_cont: invalid precision");
+  if (!q) return fail(BG_EINVAL, "bg_currents_cd_cont: q is NULL");
+  const double qv = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(q[0] > 0.0) || std::fabs(q[0] - qv) > 1e-12 * q[0])
+    return fail(BG_EINVAL, "bg_currents_cd_cont: q must be light-like with q0 > 0");
+  if (B == 0) return BG_OK;
+  if (!p || !ang || !me2 || !workspace) return fail(BG_EINVAL, "bg_currents_cd_cont: NULL argument");
+  int64_t need = 0;
+  bg_status st = bg_cd_workspace_bytes(n, prec, &need);
+  if (st != BG_OK) return st;
+  if (workspace_bytes < need)
+    return fail(BG_EINVAL, "bg_currents_cd_cont: workspace smaller than bg_cd_workspace_bytes(n, prec)");
+  if (!aligned(workspace, 256) || !aligned(p, 8) || !aligned(ang, 8) || !aligned(me2, 8))
+    return fail(BG_EINVAL, "bg_currents_cd_cont: misaligned pointer (workspace needs 256-byte alignment)");
+  CdParams prm;
+  prm.B = B;
+  prm.inv_sqrt_s = 1.0 / sqrt_s;
+  prm.scale = std::pow(9.0, n) * std::ldexp(1.0, n) * std::pow(g_s, 2 * n - 4) * std::pow(sqrt_s, 8 - 2 * n) *
+              std::ldexp(1.0, -(n - 2));
+  prm.flow = 2;
+  prm.ang = ang;
+  for (int m = 0; m < 4; ++m) prm.q.v[m] = q[m];
+  const int sms = device_sms();
+  cudaError_t e = (prec == BG_F32) ? launch_cd_f32(n, prm, p, nullptr, nullptr, accept, me2, workspace,
+                                                   device_status_ptr(), sms, (cudaStream_t)stream)
+                                   : launch_cd_f64(n, prm, p, nullptr, nullptr, accept, me2, workspace,
+                                                   device_status_ptr(), sms, (cudaStream_t)stream);
+  return cuda_check(e, "bg_currents_cd_cont");
+}
+
 bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
                             const int8_t* colors, const double* q, bg_prec prec, double g_s, const uint8_t* accept,
                             double* me2, void* stream) {

@@ -45,8 +45,12 @@ struct CdParams {
   const int64_t* dB = nullptr;  // optional device-side event count
   double inv_sqrt_s;
   double scale;  // g^(2n-4) sqrt_s^(8-2n) * colour and helicity weights * 2^-(n-2)
-  int flow;      // 0: adjoint colours [n][B] in 1..8; 1: flow pairs [2n][B] in 1..3
+  int flow;      // 0: adjoint colours [n][B] in 1..8; 1: flow pairs [2n][B] in 1..3;
+                 // 2: continuous colour and polarisation angles (ang)
   Q4 q;
+  // flow == 2: [5n][B] per gluon g rows 5g..5g+4 = cos(theta), phi, cos(theta_bar),
+  // phi_bar, phi_h (hel and col are not read)
+  const double* ang = nullptr;
 };
 
 // Real external colour matrices of the adjoint generators T^a = lambda^a/sqrt2
@@ -322,32 +326,64 @@ __global__ void __launch_bounds__(NT, cd_min_blocks(N, NT)) cd_kernel(CdParams p
       }
       double e1[4], e2[4];
       lc_polarisations(k, prm.q.v, e1, e2);
-      const int h = hel[(int64_t)g * S_ + e];
-      if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
+      if (prm.flow == 2) {
+        // continuous sampling (Sec. 2.1): e = cos(phi_h) e1 + sin(phi_h) e2; the
+        // colour matrix sum_a eta^a T^a of the colour polarisation
+        // eta^a = eta T^a eta_bar is |eta_bar><eta| minus a multiple of the
+        // identity, a U(1) gluon that decouples from all-gluon amplitudes,
+        // so the outer product alone is used
+        const double* a = prm.ang;
+        double v[5];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        s_k[g][m] = k[m];
-        s_e[g][m] = (h < 0) ? e2[m] : e1[m];
-      }
-      if (prm.flow) {
-        const int rr = col[(int64_t)(2 * g) * S_ + e], cc = col[(int64_t)(2 * g + 1) * S_ + e];
-        if (rr < 1 || rr > 3 || cc < 1 || cc > 3) flag_status(status, BG_EINVAL);
-        for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) s_E[g][i][j] = (i == rr - 1 && j == cc - 1) ? 1.0 : 0.0;
-      } else {
-        int a = col[(int64_t)g * S_ + e];
-        if (a < 1 || a > 8) {
-          flag_status(status, BG_EINVAL);
-          a = 1;
+        for (int j = 0; j < 5; ++j) v[j] = a[(int64_t)(5 * g + j) * S_ + e];
+        double sh, ch, eta[3], etab[3];
+        sincos(v[4], &sh, &ch);
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          const double ct = v[2 * w];
+          const double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+          double sp, cp;
+          sincos(v[2 * w + 1], &sp, &cp);
+          double* x = w ? etab : eta;
+          x[0] = ct;
+          x[1] = st * cp;
+          x[2] = st * sp;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          s_k[g][m] = k[m];
+          s_e[g][m] = ch * e1[m] + sh * e2[m];
         }
         for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) s_E[g][i][j] = c_adj_colour[a - 1][i][j];
+          for (int j = 0; j < 3; ++j) s_E[g][i][j] = etab[i] * eta[j];
+      } else {
+        const int h = hel[(int64_t)g * S_ + e];
+        if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          s_k[g][m] = k[m];
+          s_e[g][m] = (h < 0) ? e2[m] : e1[m];
+        }
+        if (prm.flow) {
+          const int rr = col[(int64_t)(2 * g) * S_ + e], cc = col[(int64_t)(2 * g + 1) * S_ + e];
+          if (rr < 1 || rr > 3 || cc < 1 || cc > 3) flag_status(status, BG_EINVAL);
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) s_E[g][i][j] = (i == rr - 1 && j == cc - 1) ? 1.0 : 0.0;
+        } else {
+          int a = col[(int64_t)g * S_ + e];
+          if (a < 1 || a > 8) {
+            flag_status(status, BG_EINVAL);
+            a = 1;
+          }
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) s_E[g][i][j] = c_adj_colour[a - 1][i][j];
+        }
       }
     }
     __syncthreads();
     if (tid == 0) {
       int skip = (accept != nullptr && accept[e] == 0) ? 1 : 0;
-      if (prm.flow && !skip) {  // a colour flow with unequal row/column counts has A = 0
+      if (prm.flow == 1 && !skip) {  // a colour flow with unequal row/column counts has A = 0
         int bal[3] = {0, 0, 0};
         for (int g = 0; g < N; ++g)
           for (int i = 0; i < 3; ++i)

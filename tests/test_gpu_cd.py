@@ -181,3 +181,59 @@ def test_cd_edge_cases(bg):
         bg.currents_cd(n, p, torch.ones((n, 1), dtype=torch.int8, device=dev),
                        torch.ones((n, 1), dtype=torch.int8, device=dev), workspace=ws)
     assert ei.value.code == bg.BG_EINVAL
+
+
+# --------------------------------------------------------------------------
+# continuous colour and helicity sampling (Sec. 2.1)
+# --------------------------------------------------------------------------
+def run_cd_cont(bg, n, u, ang, prec, pt_min=PT_MIN):
+    import torch
+    dev = torch.device("cuda:0")
+    p, acc = bg.momenta_rambo(n, torch.from_numpy(u).to(dev), SQRT_S, pt_min)
+    a = torch.from_numpy(np.ascontiguousarray(ang.reshape(ang.shape[0], 5 * n).T)).to(dev)
+    return bg.currents_cd_cont(n, p, a, prec=prec, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+
+
+@pytest.mark.parametrize("n,B", [(4, 300), (5, 300), (6, 200), (7, 120), (8, 60)])
+def test_cd_cont_fp64_parity(bg, oracle, n, B):
+    u = inputs.rambo_uniforms(n, B, seed=200 + n)
+    ang = inputs.continuous_angles(n, B, seed=200 + n)
+    got = run_cd_cont(bg, n, u, ang, bg.BG_F64)
+    ext = oracle.me2_cd_cont(n, u, ang, sqrt_s=SQRT_S, pt_min=PT_MIN, ext=True)
+    f64 = oracle.me2_cd_cont(n, u, ang, sqrt_s=SQRT_S, pt_min=PT_MIN)
+    assert_fp64_like(got, ext, f64)
+
+
+@pytest.mark.parametrize("n,B", [(6, 400), (8, 200), (10, 64), (12, 24)])
+def test_cd_cont_fp32_parity(bg, oracle, n, B):
+    u = inputs.rambo_uniforms(n, B, seed=210 + n)
+    ang = inputs.continuous_angles(n, B, seed=210 + n)
+    got = run_cd_cont(bg, n, u, ang, bg.BG_F32, pt_min=-1.0)
+    ref = oracle.me2_cd_cont(n, u, ang, sqrt_s=SQRT_S, pt_min=-1.0)
+    nz = split_zeros(got, ref, tol=1e-6)
+    assert nz.sum() >= B // 2
+    assert np.median(np.abs(got[nz] / ref[nz] - 1.0)) < 1e-5
+    assert np.quantile(fp32_rel(got[nz], ref[nz]), 0.99) < 1e-3
+
+
+def test_cd_cont_design_average_equals_colour_ordered(bg):
+    # exact average over colour vectors from the cube design (4 x 4 per
+    # gluon) at polarisation angle 0 = the GPU's colour-ordered |M|^2 with the
+    # colour sum, for e1 on every gluon
+    import math
+    import torch
+    n = 4
+    cube = np.array([[1, 1, 1], [1, 1, -1], [1, -1, 1], [-1, 1, 1]], dtype=np.float64) / math.sqrt(3.0)
+    ang1 = [(v[0], math.atan2(v[2], v[1])) for v in cube]
+    states = np.array([[a[0], a[1], b[0], b[1], 0.0] for a in ang1 for b in ang1])
+    combos = np.array(list(itertools.product(range(len(states)), repeat=n)))
+    A = states[combos]
+    u1 = inputs.rambo_uniforms(n, 1, seed=220)
+    est = run_cd_cont(bg, n, np.repeat(u1, A.shape[0], axis=0), A, bg.BG_F64, pt_min=-1.0)
+    dev = torch.device("cuda:0")
+    C = bg.ColourMatrix(n)
+    p, _ = bg.momenta_rambo(n, torch.from_numpy(u1).to(dev), SQRT_S)
+    amps = bg.currents_co(n, p, torch.ones((n, 1), dtype=torch.int8, device=dev), prec=bg.BG_F64, sqrt_s=SQRT_S)
+    co = bg.color_sum(C, amps, True, mode=bg.BG_CS_F64, sqrt_s=SQRT_S).cpu().numpy()[0]
+    C.close()
+    assert abs(est.mean() / co - 1.0) < 1e-11
