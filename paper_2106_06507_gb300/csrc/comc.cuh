@@ -18,13 +18,16 @@
 //      vectors in T, and the pair invariants 2 k_a.k_b for all pairs of the
 //      n gluons, computed in FP64 and kept as an unevaluated sum of two
 //      floats in the FP32 kernel (FP64 in the FP64 kernel);
-//   2. the orders of an event are split into tasks by their first two
-//      gluons after gluon 1 (prefix (1, s_2, s_3)); every thread takes
-//      tasks in turn, walks a task's closing orders depth-first (labels in
-//      increasing order) one order at a time and runs the whole recursion of
-//      each order found, all lanes that found one together (same code path
-//      for every order); a task's amplitudes are summed in walk order;
-//   3. |M|^2 per event from its task sums, in task order (deterministic).
+//   2. one thread per event walks the orders whose chain closes (depth-first,
+//      labels in increasing order) and counts them; a warp scan gives each
+//      event its range of item indices;
+//   3. in windows of CAP items: each event's walk is resumed where the last
+//      window paused it, writing the packed orders of the window into shared
+//      memory (an event is walked once in total), then every thread takes
+//      items and evaluates the whole recursion of one order (same code path
+//      for every item), and one thread per event adds its items' amplitudes
+//      in item order (deterministic);
+//   4. |M|^2 per event.
 // The propagator denominators P(i..j)^2 of each order are accumulated from
 // the pair invariants column by column, P(i..j)^2 = P(i..j-1)^2 +
 // sum_{a=i}^{j-1} 2 k_{s_a}.k_{s_j}, in double-float arithmetic (Knuth's
@@ -60,8 +63,8 @@ struct ComcShape {
   static constexpr int NPAIR = N * (N - 1) / 2;
   static constexpr int NSEG = M * (M + 1) / 2;  // segments (i..j), i <= j, of the off-shell current
   static constexpr int NSLOT = NSEG + N;         // + prefix sums S_0..S_M of the ordered momenta
-  static constexpr int EB = N <= 7 ? 128 : N == 8 ? (sizeof(T) == 8 ? 64 : 128) : N == 9 ? 64 : N == 10 ? 32 : 16;
-  static constexpr int NTASK = (N - 1) * (N - 2);  // prefixes (0, g1, g2) of an event's orders
+  static constexpr int EB = N <= 8 ? 128 : N == 9 ? 64 : N <= 11 ? 32 : 16;
+  static constexpr int CAP = TAB ? (sizeof(T) == 8 ? 512 : 1024) : 2048;  // items per window
 };
 
 // Pair invariants and running P^2 sums: two floats (value + error) for the
@@ -195,11 +198,13 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
 // whose colour chain closes: the row colour of each gluon equals the column
 // colour of the gluon before it, and the column colour of the last gluon
 // equals the row colour of gluon 0.  rm[c]: mask of the gluons with row
-// colour c; cp: column colours, 2 bits per gluon.  A walk covers the orders
-// that start with a given prefix (0, g_1, g_2) -- one task -- in
+// colour c; cp: column colours, 2 bits per gluon.  Orders are visited in
 // lexicographic order of their labels; visit(packed) gets the labels of
 // positions 1..N-1 packed 4 bits each and returns false to pause the walk
-// after that order (run() then returns 1; 0 once the task is exhausted).
+// after that order.  The state (depth, candidates left per depth, labels
+// chosen, gluons still free) can be saved and the walk resumed where it
+// paused, so that an event whose orders span several windows is walked once
+// in total.
 template <int N>
 struct ComcWalk {
   uint64_t packed;
@@ -208,23 +213,18 @@ struct ComcWalk {
   uint16_t cand[N];
   uint8_t gl[N];
 
-  // Prefix (0, g1, g2); false if its chain is already broken.
-  __device__ __forceinline__ bool start(const uint32_t (&rm)[3], uint32_t cp, int g1, int g2) {
-    const uint32_t c0 = cp & 3u, c1 = (cp >> (2 * g1)) & 3u;
-    if (!((rm[c0] >> g1) & 1u) || !((rm[c1] >> g2) & 1u)) return false;
-    packed = (uint64_t)g1 | ((uint64_t)g2 << 4);
-    avail = ((1u << N) - 1u) & ~1u & ~(1u << g1) & ~(1u << g2);
-    gl[1] = (uint8_t)g1;
-    gl[2] = (uint8_t)g2;
-    d = 3;
-    cand[3] = (uint16_t)(avail & rm[(cp >> (2 * g2)) & 3u]);
-    return true;
+  __device__ __forceinline__ void start(const uint32_t (&rm)[3], uint32_t cp) {
+    packed = 0;
+    avail = ((1u << N) - 1u) & ~1u;
+    d = 1;
+    cand[1] = avail & rm[cp & 3u];
   }
+  // Returns the number of orders visited before the walk ended or paused.
   template <typename F>
   __device__ __forceinline__ int64_t run(const uint32_t (&rm)[3], uint32_t cp, F&& visit) {
     const int r0 = (rm[0] & 1u) ? 0 : ((rm[1] & 1u) ? 1 : 2);
     int64_t cnt = 0;
-    while (d >= 3) {
+    while (d > 0) {
       if (cand[d]) {
         const int g = __ffs(cand[d]) - 1;
         cand[d] &= cand[d] - 1u;
@@ -237,13 +237,13 @@ struct ComcWalk {
           continue;
         }
         packed = pk;
-        gl[d] = (uint8_t)g;
+        gl[d] = g;
         avail &= ~(1u << g);
         ++d;
-        cand[d] = (uint16_t)(avail & rm[(cp >> (2 * g)) & 3u]);
+        cand[d] = avail & rm[(cp >> (2 * g)) & 3u];
       } else {
         --d;
-        if (d >= 3) avail |= 1u << gl[d];
+        if (d > 0) avail |= 1u << gl[d];
       }
     }
     return cnt;
@@ -258,9 +258,14 @@ struct ComcSmem {
   static constexpr size_t off_k = 0;                                                 // T [EB][N][4]
   static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                 // T [EB][N][4]
   static constexpr size_t off_pair = a16(off_e + sizeof(T) * S::EB * N * 4);         // PT [EB][NPAIR]
-  static constexpr size_t off_tsum = a16(off_pair + sizeof(PT) * S::EB * S::NPAIR);  // double [EB][NTASK]
-  static constexpr size_t off_cf = a16(off_tsum + 8 * S::EB * S::NTASK);             // u32 [EB][4]
-  static constexpr size_t off_tab = a16(off_cf + 16 * S::EB);                        // T [NSLOT][NT][4] (TAB)
+  static constexpr size_t off_item = a16(off_pair + sizeof(PT) * S::EB * S::NPAIR);  // u64 [CAP]
+  static constexpr size_t off_amp = off_item + 8 * S::CAP;                            // T [CAP]
+  static constexpr size_t off_acc = a16(off_amp + sizeof(T) * S::CAP);               // double [EB]
+  static constexpr size_t off_off = off_acc + 8 * S::EB;                              // i64 [EB+1]
+  static constexpr size_t off_cf = a16(off_off + 8 * (S::EB + 1));                   // u32 [EB][4]
+  static constexpr size_t off_iev = off_cf + 16 * S::EB;                              // u16 [CAP]
+  static constexpr size_t off_walk = a16(off_iev + 2 * S::CAP);                       // walk states [EB]
+  static constexpr size_t off_tab = a16(off_walk + sizeof(ComcWalk<N>) * S::EB);       // T [NSLOT][NT][4] (TAB)
   static constexpr size_t bytes = off_tab + (S::TAB ? sizeof(T) * S::NSLOT * S::NT * 4 : 0);
 };
 
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
   using S = ComcShape<N, T>;
   using L = ComcSmem<N, T>;
   using PT = typename ComcPair<T>::type;
-  constexpr int EB = S::EB, NT = S::NT, NPAIR = S::NPAIR, NTASK = S::NTASK;
+  constexpr int EB = S::EB, NT = S::NT, CAP = S::CAP, NPAIR = S::NPAIR;
   const int64_t S_ = prm.B;
   const int64_t B = prm.dB ? (*prm.dB < S_ ? *prm.dB : S_) : S_;
   const int64_t e0 = (int64_t)blockIdx.x * EB;
@@ -397,8 +402,13 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
   T* s_k = reinterpret_cast<T*>(smem + L::off_k);
   T* s_e = reinterpret_cast<T*>(smem + L::off_e);
   PT* s_pair = reinterpret_cast<PT*>(smem + L::off_pair);
-  double* s_tsum = reinterpret_cast<double*>(smem + L::off_tsum);
+  uint64_t* s_item = reinterpret_cast<uint64_t*>(smem + L::off_item);
+  T* s_amp = reinterpret_cast<T*>(smem + L::off_amp);
+  double* s_acc = reinterpret_cast<double*>(smem + L::off_acc);
+  long long* s_off = reinterpret_cast<long long*>(smem + L::off_off);
   uint32_t* s_cf = reinterpret_cast<uint32_t*>(smem + L::off_cf);
+  uint16_t* s_iev = reinterpret_cast<uint16_t*>(smem + L::off_iev);
+  ComcWalk<N>* s_walk = reinterpret_cast<ComcWalk<N>*>(smem + L::off_walk);
   const int tid = threadIdx.x;
 
   // ---- 1. momenta, polarisations, pair invariants, colour flows
@@ -479,79 +489,93 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
   }
   __syncthreads();
 
-  // ---- 2. tasks: the orders of event el that start (0, g1, g2), task index
-  // el * NTASK + t with t = (g1 - 1)(N - 2) + rank of g2 among the other
-  // gluons.  Each thread takes tasks tid, tid + NT, ...; it walks a task's
-  // orders one at a time and, between steps of the walk, runs the recursion
-  // of the order found together with the other lanes that found one (the
-  // walks diverge, the recursions do not).  A task's amplitudes are added in
-  // walk order, the tasks of an event in task order: deterministic.
-  {
-    T* tab = nullptr;
-    if constexpr (S::TAB) tab = reinterpret_cast<T*>(smem + L::off_tab) + tid * 4;
-    int tt = tid;          // next task to look at
-    int cur = -1, el = 0;  // current task and its event
-    uint32_t rm[3] = {0u, 0u, 0u}, cp = 0u;
-    ComcWalk<N> wk;
-    double tacc = 0.0;
-    for (;;) {
-      uint64_t pk = 0;
-      bool leaf = false;
-      while (!leaf) {
-        if (cur < 0) {  // next non-empty task
-          while (tt < EB * NTASK) {
-            const int e_l = tt / NTASK, t = tt - e_l * NTASK;
-            const uint32_t w = s_cf[e_l * 4 + 3];
-            bool on = ((w >> 30) & 1u) && ((w >> 29) & 1u);
-            if (on) {
-              const int g1 = 1 + t / (N - 2);
-              int g2 = 1 + t % (N - 2);
-              if (g2 >= g1) ++g2;
-              const uint32_t r3[3] = {s_cf[e_l * 4 + 0], s_cf[e_l * 4 + 1], s_cf[e_l * 4 + 2]};
-              on = wk.start(r3, w & 0x00FFFFFFu, g1, g2);
-              if (on) {
-                rm[0] = r3[0];
-                rm[1] = r3[1];
-                rm[2] = r3[2];
-                cp = w & 0x00FFFFFFu;
-                el = e_l;
-                cur = tt;
-                tacc = 0.0;
-              }
-            }
-            if (!on) s_tsum[tt] = 0.0;
-            tt += NT;
-            if (on) break;
-          }
-          if (cur < 0) break;  // no tasks left for this thread
-        }
-        if (wk.run(rm, cp, [&](uint64_t x) {
-              pk = x;
-              return false;
-            })) {
-          leaf = true;
-        } else {
-          s_tsum[cur] = tacc;
-          cur = -1;
-        }
-      }
-      if (!leaf) break;
-      T a;
-      if constexpr (S::TAB)
-        a = comc_amplitude_tab<N, T, PT, NT>(pk, s_k + el * N * 4, s_e + el * N * 4, s_pair + el * NPAIR, tab);
-      else
-        a = comc_amplitude<N, T, PT>(pk, s_k + el * N * 4, s_e + el * N * 4, s_pair + el * NPAIR);
-      tacc += (double)a;
+  // ---- 2. count the orders of each event, then a scan over the tile
+  for (int el = tid; el < EB; el += NT) {
+    const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
+    const uint32_t w = s_cf[el * 4 + 3];
+    int64_t cnt = 0;
+    if (((w >> 30) & 1u) && ((w >> 29) & 1u)) {
+      ComcWalk<N> wk;
+      wk.start(rm, w & 0x00FFFFFFu);
+      cnt = wk.run(rm, w & 0x00FFFFFFu, [](uint64_t) { return true; });
     }
+    s_off[el + 1] = (long long)cnt;
+    s_acc[el] = 0.0;
   }
   __syncthreads();
+  if (tid < 32) {
+    long long carry = 0;
+    for (int base = 0; base < EB; base += 32) {
+      const int el = base + tid;
+      long long v = el < EB ? s_off[el + 1] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, d);
+        if (tid >= d) v += u;
+      }
+      if (el < EB) s_off[el + 1] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (tid == 0) s_off[0] = 0;
+  }
+  __syncthreads();
+  const long long total = s_off[EB];
 
-  // ---- 3. |M|^2: the task sums of each event in task order
+  // ---- 3. windows of CAP items: write the orders, evaluate, accumulate
+  for (long long w0 = 0; w0 < total; w0 += CAP) {
+    const long long w1 = (total - w0 < CAP) ? total : w0 + CAP;
+    for (int el = tid; el < EB; el += NT) {
+      // (events without items -- failing the cut, invalid or without a
+      // closing order -- have lo == hi and are not walked)
+      const long long lo = s_off[el], hi = s_off[el + 1];
+      if (hi <= lo || hi <= w0 || lo >= w1) continue;
+      // the event's orders lo + r, r = 0, 1, ..., are written from where its
+      // walk paused at the end of the previous window
+      const long long stop = hi < w1 ? hi : w1;
+      const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
+      const uint32_t cp = s_cf[el * 4 + 3] & 0x00FFFFFFu;
+      ComcWalk<N> wk;
+      if (lo >= w0) {
+        wk.start(rm, cp);
+      } else {
+        wk = s_walk[el];
+      }
+      long long g = lo > w0 ? lo : w0;
+      wk.run(rm, cp, [&](uint64_t pk) {
+        s_item[g - w0] = pk;
+        s_iev[g - w0] = (uint16_t)el;
+        ++g;
+        return g < stop;
+      });
+      if (hi > w1) s_walk[el] = wk;
+    }
+    __syncthreads();
+    const int nw = (int)(w1 - w0);
+    for (int it = tid; it < nw; it += NT) {
+      const int el = s_iev[it];
+      if constexpr (S::TAB)
+        s_amp[it] = comc_amplitude_tab<N, T, PT, NT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4,
+                                                     s_pair + el * NPAIR,
+                                                     reinterpret_cast<T*>(smem + L::off_tab) + tid * 4);
+      else
+        s_amp[it] = comc_amplitude<N, T, PT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4, s_pair + el * NPAIR);
+    }
+    __syncthreads();
+    for (int el = tid; el < EB; el += NT) {
+      const long long lo = s_off[el] > w0 ? s_off[el] : w0;
+      const long long hi = s_off[el + 1] < w1 ? s_off[el + 1] : w1;
+      double a = s_acc[el];
+      for (long long g = lo; g < hi; ++g) a += (double)s_amp[g - w0];
+      s_acc[el] = a;
+    }
+    __syncthreads();
+  }
+
+  // ---- 4. |M|^2
   for (int el = tid; el < EB; el += NT) {
     const int64_t e = e0 + el;
     if (e >= B) continue;
-    double a = 0.0;
-    for (int t = 0; t < NTASK; ++t) a += s_tsum[el * NTASK + t];
+    const double a = s_acc[el];
     me2[e] = ((s_cf[el * 4 + 3] >> 30) & 1u) ? prm.scale * a * a : 0.0;
   }
 }

@@ -15,8 +15,8 @@ and each carries the FP32 recursion's ~1e-6 relative error: median < 5e-5,
 
 Flows are drawn balanced (column colours a permutation of the row colours):
 the others vanish exactly, and uniform flows are balanced for only 3-7 % of
-events.  Degenerate flows (thousands of closing orders in one event) spread
-one event's orders over many tasks of one block.
+events.  Degenerate flows (thousands of closing orders in one event) take
+the kernel through several windows of items.
 """
 import numpy as np
 import pytest
@@ -113,8 +113,8 @@ def test_comc_fp32_parity(bg, oracle, n, B):
 
 @pytest.mark.parametrize("n", [8, 9])
 def test_comc_many_orders_per_event(bg, oracle, n):
-    # (n-2)! = 720 / 5040 closing orders per event, spread over the tasks
-    # (prefixes) of one block
+    # (n-2)! = 720 / 5040 closing orders per event: several windows of
+    # items per block, items of one event spread over windows
     B = 40
     u = inputs.rambo_uniforms(n, B, seed=130 + n)
     hel = inputs.helicities(n, B, seed=130 + n)
