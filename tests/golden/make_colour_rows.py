@@ -1,9 +1,12 @@
 """Write the first row C_{id, tau} of the adjoint colour matrix, Eq. (2.17),
-for n = 4..8 gluons, computed by the oracle's explicit SU(3) contraction
+for n = 4..9 gluons, computed by the oracle's explicit SU(3) contraction
 (oracle/bg_oracle.cpp: colour_coefficient).  Orderings tau of the labels
 2..n-1 are in lexicographic order.  Calls only oracle/.
 
     python tests/golden/make_colour_rows.py [n ...]
+
+n = 4..8 take seconds to a minute; n = 9 (5040 entries of 8^9 terms) about two
+hours on 8 cores.
 """
 import math
 import os

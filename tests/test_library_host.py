@@ -48,8 +48,11 @@ def test_num_orderings(libbg):
                                                                   3628800, 0]
 
 
-@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8, 9])
 def test_library_colour_row_matches_oracle(libbg, oracle, n):
+    # n = 9: the golden row (5040 entries by explicit SU(3) contraction, 8^9
+    # terms each, about two hours of the oracle on 8 cores) is read from
+    # tests/golden
     import math
     row = np.zeros(math.factorial(n - 2))
     rc = libbg.bg_colormat_row_host(n, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
@@ -59,9 +62,8 @@ def test_library_colour_row_matches_oracle(libbg, oracle, n):
 
 
 def test_library_colour_row_n9_closed_forms(libbg):
-    # n = 9 has no explicit-contraction golden row (8^9 terms per entry); check
-    # the closed-form diagonal 8 (2N)^(n-2), integrality and the BF16-exactness
-    # of the entries scaled by their gcd.
+    # the closed-form diagonal 8 (2N)^(n-2), integrality and the gcd of the
+    # entries at n = 9
     row = np.zeros(5040)
     assert libbg.bg_colormat_row_host(9, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
     assert row[0] == 8 * 6**7
