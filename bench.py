@@ -10,7 +10,7 @@ accumulation.  Metric: events/s (all generated events of all four
 multiplicities; per-n figures are in "per_n").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload co|cd|grad|mixed|comc|lc]
+                    [--workload co|cd|grad|mixed|comc|lc|paper]
 
 The default workload (co) is the one above.  The others measure the other
 parts of the path with the same timing rules:
@@ -24,7 +24,10 @@ parts of the path with the same timing rules:
          FP32 currents, pT > 20 GeV, autotuned kernel variants;
   comc   colour-flow sampling with colour-ordered amplitudes (Eq. 2.19),
          flows uniform in {1,2,3}^2, n = 8, 10, 12, 2^20 events per n;
-  lc     leading-colour |M|^2 (Sec. 4) on the default events, n = 5..8.
+  lc     leading-colour |M|^2 (Sec. 4) on the default events, n = 5..8;
+  paper  the paper's own setup: sqrt(s) = 14 TeV, pT > 20 GeV, |eta| < 2.5,
+         Delta R > 0.4, colour-ordered n = 5..8 (acceptance, recursion /
+         colour-sum time split, device bytes per event).
 
 Prints ONE JSON line on rank 0.  N > 1 runs under torch.distributed.run, one
 process per GPU, each with its own events (weak scaling, no collective on the
@@ -918,6 +921,109 @@ def run_lc(args) -> None:
     finish_gpu(world)
 
 
+def run_paper(args) -> None:
+    """The paper's own setup (Sec. 5): sqrt(s) = 14 TeV, pT > 20 GeV, |eta| < 2.5,
+    Delta R > 0.4, colour-ordered n = 5..8, 2^20 events per n, sampled
+    helicities, FP32 currents and the exact colour sum (tcgen05 for n >= 6).
+    Reports the acceptance, the time split between the recursion and the
+    colour sum, and the device bytes per event."""
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    sqrt_s, first = 14000.0, rank * BATCH
+    U, HEL, P, ACC, AMPS, ME2, CM, host = {}, {}, {}, {}, {}, {}, {}, {}
+    for n in NS:
+        u = inputs.rambo_uniforms(n, BATCH, seed=SEED, first_event=first)
+        h = np.ascontiguousarray(inputs.helicities(n, BATCH, seed=SEED, first_event=first).T)
+        U[n], HEL[n] = torch.from_numpy(u).to(dev), torch.from_numpy(h).to(dev)
+        host[n] = (torch.from_numpy(u).pin_memory(), torch.from_numpy(h).pin_memory())
+        P[n] = torch.empty((4, n, BATCH), dtype=torch.float64, device=dev)
+        ACC[n] = torch.empty((BATCH,), dtype=torch.uint8, device=dev)
+        AMPS[n] = torch.empty((BATCH, 1, math.factorial(n - 2)), dtype=torch.float32, device=dev)
+        ME2[n] = torch.empty((BATCH,), dtype=torch.float64, device=dev)
+        CM[n] = bg.ColourMatrix(n)
+    ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(4)] for n in NS}
+    kernel_ms = {n: [0.0, 0.0, 0.0] for n in NS}
+
+    def one(n, u, h, record=False):
+        if record:
+            ev[n][0].record(stream)
+        bg.momenta_rambo(n, u, sqrt_s, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
+        bg.apply_cuts(n, P[n], PT_MIN, 2.5, 0.4, accept=ACC[n], stream=stream)
+        if record:
+            ev[n][1].record(stream)
+        bg.currents_co(n, P[n], h, prec=bg.BG_F32, sqrt_s=sqrt_s, amps=AMPS[n], stream=stream)
+        if record:
+            ev[n][2].record(stream)
+        bg.color_sum(CM[n], AMPS[n], True, mode=cs_mode_for(bg, n), sqrt_s=sqrt_s, accept=ACC[n], me2=ME2[n],
+                     stream=stream)
+        if record:
+            ev[n][3].record(stream)
+
+    def step(record=False):
+        for n in NS:
+            one(n, U[n], HEL[n], record)
+
+    elapsed, clk = timed_steps(step, args, dev, stream)
+    value = world * len(NS) * BATCH * args.steps / elapsed
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize(dev)
+        for n in NS:
+            for j in range(3):
+                kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1]) / args.steps
+    ref = {n: ME2[n].cpu() for n in NS}
+    out_h = {n: torch.empty((BATCH,), dtype=torch.float64).pin_memory() for n in NS}
+    d_in = {n: tuple(torch.empty_like(x, device=dev) for x in host[n]) for n in NS}
+
+    def e2e_step():
+        for n in NS:
+            for dst, src in zip(d_in[n], host[n]):
+                dst.copy_(src, non_blocking=True)
+            one(n, d_in[n][0], d_in[n][1])
+            out_h[n].copy_(ME2[n], non_blocking=True)
+
+    e2e_s = timed_host(e2e_step, args, dev)
+    for n in NS:
+        if not torch.equal(out_h[n], ref[n]):
+            raise RuntimeError(f"e2e |M|^2 differs from the device-resident run at n={n}")
+    acceptance = {str(n): float(ACC[n].float().mean().item()) for n in NS}
+    h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in NS)
+    n_dom = max(NS, key=lambda n: kernel_ms[n][1])
+    achieved = canonical_recursion_flops(n_dom) * BATCH / (kernel_ms[n_dom][1] * 1e-3) / 1e12
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    # uniforms, momenta, helicities, cut flags, FP32 amplitudes, |M|^2
+    bytes_per_event = {str(n): 32 * (n - 2) + 32 * n + n + 1 + 4 * math.factorial(n - 2) + 8 for n in NS}
+    for n in NS:
+        CM[n].close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("the paper's setup: colour-ordered BG n=5,6,7,8, 2^20 Rambo points per n at "
+                                    "sqrt(s)=14 TeV, pT>20 GeV, |eta|<2.5, Delta R>0.4, sampled helicities, FP32 "
+                                    "currents, exact colour sum (tcgen05 for n>=6)"),
+                       "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": sqrt_s, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2"},
+            "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) * 1e-3) for n in NS},
+            "acceptance": acceptance,
+            "kernel_ms_per_step": {f"n{n}": {"rambo+cuts": round(kernel_ms[n][0], 3),
+                                             "recursion": round(kernel_ms[n][1], 3),
+                                             "colour_sum": round(kernel_ms[n][2], 3)} for n in NS},
+            "device_bytes_per_event": bytes_per_event,
+            "roofline": {"kernel": f"colour-ordered recursion n={n_dom}", "bound": "alu", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "flops_model": "canonical recursion FLOPs x events",
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
+            "e2e": {"value": world * len(NS) * BATCH * args.steps / e2e_s, "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(NS) * BATCH * 8},
+            "gpu_launches": 4 * len(NS) * args.steps, "clocks": clk}), flush=True)
+    finish_gpu(world)
+
+
 GRAD_NS = (6, 8)
 GRAD_BATCH = 1 << 18
 
@@ -1108,7 +1214,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc"), default="co")
+    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc", "paper"), default="co")
     ap.add_argument("--precision", choices=("f32", "f64"), default="f32",
                     help="recursion arithmetic of the co and cd workloads (f64: the plain FP64 GPU form)")
     ap.add_argument("--colour-sampling", choices=("adjoint", "continuous"), default="adjoint",
@@ -1131,6 +1237,8 @@ def main(argv=None):
         run_comc(args)
     elif args.workload == "lc":
         run_lc(args)
+    elif args.workload == "paper":
+        run_paper(args)
     else:
         run_ours(args)
 

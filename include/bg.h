@@ -114,6 +114,21 @@ bg_status bg_momenta_rambo(int n, int64_t B, double sqrt_s, const double* u, dou
                            uint8_t* accept, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * bg_apply_cuts -- the paper's kinematic constraints (Sec. 5) on the final-
+ * state gluons 3..n of momenta written by bg_momenta_rambo: p_T > pt_min,
+ * |eta| < eta_max and Delta R > dr_min for every pair, with eta =
+ * asinh(p_z / p_T), phi = atan2(p_y, p_x), Delta R^2 = (Delta eta)^2 +
+ * (Delta phi)^2, Delta phi in [0, pi].  eta_max <= 0 or dr_min <= 0 drop that
+ * constraint.  The paper's setup: sqrt_s = 14000, pt_min = 20,
+ * eta_max = 2.5, dr_min = 0.4.
+ *   p       [4][n][B]    lab momenta
+ *   accept  [B]          output 1 if the event passes every constraint, else 0
+ * Errors: BG_EINVAL.  B = 0 is a no-op.
+ * ------------------------------------------------------------------------- */
+bg_status bg_apply_cuts(int n, int64_t B, const double* p, double pt_min, double eta_max, double dr_min,
+                        uint8_t* accept, void* stream);
+
+/* ---------------------------------------------------------------------------
  * bg_currents_co -- colour-ordered Berends-Giele currents, Eqs. (2.20)-(2.22),
  * for every ordering sigma in S_{n-2}: A(1, sigma_2..sigma_{n-1}, n).
  *   p       [4][n][B]    lab momenta (as written by bg_momenta_rambo).

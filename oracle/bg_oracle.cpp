@@ -1032,6 +1032,40 @@ void or_continuous_external(const double* ang, double* E) {
     for (int j = 0; j < 3; ++j) E[i * 3 + j] = M[i][j];
 }
 
+// The paper's kinematic constraints (Sec. 5) on the final-state gluons of
+// the Rambo event of each row of u[B][4(n-2)]: pT > pt_min, |eta| < eta_max,
+// Delta R > dr_min for every pair (eta_max <= 0 or dr_min <= 0 drop that
+// constraint).  Pseudorapidity from the polar angle, eta = -ln tan(theta/2);
+// azimuth difference folded into [0, pi].  acc[B] = 1 if the event passes.
+void or_accept_cuts(int n, long long B, double sqrt_s, const double* u, double pt_min, double eta_max,
+                    double dr_min, uint8_t* acc) {
+  const int d = 4 * (n - 2);
+  std::vector<Vec<double>> p(n);
+  std::vector<double> eta(n), phi(n);
+  for (long long e = 0; e < B; ++e) {
+    rambo(n, sqrt_s, u + e * d, p.data());
+    bool ok = true;
+    for (int i = 2; i < n; ++i) {
+      const double px = p[i].c[1], py = p[i].c[2], pz = p[i].c[3];
+      const double pt = std::sqrt(px * px + py * py);
+      if (!(pt > pt_min)) ok = false;
+      const double theta = std::atan2(pt, pz);
+      eta[i] = -std::log(std::tan(0.5 * theta));
+      phi[i] = std::atan2(py, px);
+      if (eta_max > 0.0 && !(std::fabs(eta[i]) < eta_max)) ok = false;
+    }
+    if (dr_min > 0.0)
+      for (int i = 2; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+          double dphi = std::fabs(phi[i] - phi[j]);
+          if (dphi > M_PI) dphi = 2.0 * M_PI - dphi;
+          const double dr = std::sqrt((eta[i] - eta[j]) * (eta[i] - eta[j]) + dphi * dphi);
+          if (!(dr > dr_min)) ok = false;
+        }
+    acc[e] = ok ? 1 : 0;
+  }
+}
+
 // Gradient of the colour-summed |M|^2 (sampled helicity hel[n]) with
 // respect to the 4(n-2) Rambo uniforms of one event, by forward-mode dual
 // numbers through Rambo, the polarisations, the recursion and the colour

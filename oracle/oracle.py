@@ -81,6 +81,7 @@ def lib():
             L.or_me2_cd_cont_batch.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, c_dbl, c_dbl, dp, c_int]
             L.or_me2_cd_cont_batch_ext.argtypes = [c_int, c_ll, c_dbl, dp, dp, dp, c_dbl, c_dbl, dp, c_int]
             L.or_continuous_external.argtypes = [dp, dp]
+            L.or_accept_cuts.argtypes = [c_int, c_ll, c_dbl, dp, c_dbl, c_dbl, c_dbl, ctypes.POINTER(ctypes.c_uint8)]
             L.or_me2_co_grad.argtypes = [c_int, c_dbl, dp, dp, dp, i8p, c_dbl, dp]
             L.or_me2_co_grad.restype = c_dbl
             _lib = L
@@ -437,6 +438,16 @@ def me2_cd_cont(n, u, ang, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, pt_min=-1.
     fn(n, B, sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), qp, angp, g, pt_min,
        me2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nthreads or n_cores())
     return me2
+
+
+def accept_cuts(n, u, sqrt_s=1000.0, pt_min=20.0, eta_max=2.5, dr_min=0.4) -> np.ndarray:
+    """Per-event acceptance [B] uint8 of the paper's kinematic constraints
+    (Sec. 5) for the Rambo events of u[B, 4(n-2)]."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4 * (n - 2)))
+    acc = np.zeros(u.shape[0], dtype=np.uint8)
+    lib().or_accept_cuts(n, u.shape[0], sqrt_s, u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pt_min, eta_max,
+                         dr_min, acc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return acc
 
 
 def me2_co_grad(n, u, hel, sqrt_s=1000.0, q=DEFAULT_Q, g=G_S_DEFAULT, C=None):

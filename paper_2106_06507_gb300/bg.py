@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
+        L.bg_apply_cuts.argtypes = [c_int, c_i64, vp, c_dbl, c_dbl, c_dbl, vp, vp]
         L.bg_currents_cd_cont.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_currents_co_mc.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, dp, c_int, c_dbl, vp, vp, vp]
         L.bg_lc_workspace_bytes.argtypes = [c_int, c_i64, c_int, c_int, ctypes.POINTER(c_i64)]
@@ -107,7 +108,7 @@ def lib() -> ctypes.CDLL:
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_probe_fma", "bg_cd_workspace_bytes",
-                     "bg_currents_cd", "bg_currents_cd_cont", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
+                     "bg_currents_cd", "bg_currents_cd_cont", "bg_apply_cuts", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
                      "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
                      "bg_tune_load"):
             getattr(L, name).restype = c_int
@@ -187,6 +188,17 @@ def momenta_rambo(n: int, u: torch.Tensor, sqrt_s: float = 1000.0, pt_min: float
         accept = torch.empty((B,), dtype=torch.uint8, device=u.device)
     _check(lib().bg_momenta_rambo(n, B, sqrt_s, _ptr(u), _ptr(p), pt_min, _ptr(accept), _stream(stream)))
     return p, accept
+
+
+def apply_cuts(n: int, p: torch.Tensor, pt_min: float = 20.0, eta_max: float = 2.5, dr_min: float = 0.4,
+               accept=None, stream=None) -> torch.Tensor:
+    """The paper's kinematic constraints (Sec. 5) on p [4, n, B] -> accept [B]
+    uint8 (eta_max <= 0 or dr_min <= 0 drop that constraint)."""
+    B = p.shape[2]
+    if accept is None:
+        accept = torch.empty((B,), dtype=torch.uint8, device=p.device)
+    _check(lib().bg_apply_cuts(n, B, _ptr(p), pt_min, eta_max, dr_min, _ptr(accept), _stream(stream)))
+    return accept
 
 
 def currents_co(n: int, p: torch.Tensor, hel: torch.Tensor | None = None, q=DEFAULT_Q, prec: int = BG_F32,

@@ -39,6 +39,7 @@ SOURCES = [
     "comc_f32.cu",
     "comc_f64.cu",
     "lc.cu",
+    "cuts.cu",
 ]
 
 

@@ -112,3 +112,17 @@ def test_plan_async_host_buffers_on_streams(bg):
     for ref, out, plan in zip(res, outs, plans):
         assert torch.equal(ref, out)
         plan.close()
+
+
+@pytest.mark.parametrize("n", [4, 6, 8, 10, 12])
+def test_apply_cuts_matches_oracle(bg, oracle, n):
+    # the paper's constraints at sqrt(s) = 14 TeV, and each constraint alone:
+    # acceptance flags bit for bit equal to the oracle's
+    import torch
+    B = 1 << 14
+    u = inputs.rambo_uniforms(n, B, seed=230 + n)
+    p, _ = bg.momenta_rambo(n, torch.from_numpy(u).to(torch.device("cuda:0")), 14000.0)
+    for cuts in ((20.0, 2.5, 0.4), (20.0, 0.0, 0.0), (-1.0, 2.5, 0.0), (-1.0, 0.0, 0.4)):
+        got = bg.apply_cuts(n, p, *cuts).cpu().numpy()
+        ref = oracle.accept_cuts(n, u, sqrt_s=14000.0, pt_min=cuts[0], eta_max=cuts[1], dr_min=cuts[2])
+        assert np.array_equal(got, ref), (cuts, int((got != ref).sum()))

@@ -491,6 +491,46 @@ def test_continuous_polarisation_average_is_helicity_sum(oracle, n):
 
 
 # --------------------------------------------------------------------------
+# The paper's kinematic constraints (Sec. 5)
+# --------------------------------------------------------------------------
+def test_eta_cut_acceptance_closed_form(oracle):
+    # isotropic back-to-back gluons (n = 4): |eta| < eta_max <=> |cos theta| <
+    # tanh(eta_max), so the acceptance is tanh(eta_max); pT and Delta R cuts off
+    n, B = 4, 200000
+    u = inputs.rambo_uniforms(n, B, seed=30)
+    for eta_max in (0.5, 2.5):
+        acc = oracle.accept_cuts(n, u, sqrt_s=14000.0, pt_min=-1.0, eta_max=eta_max, dr_min=0.0)
+        p = math.tanh(eta_max)
+        assert abs(acc.mean() - p) < 4.0 * math.sqrt(p * (1 - p) / B)
+    # back to back: Delta eta = 2 |eta|, Delta phi = pi > 0.4, every event passes
+    assert oracle.accept_cuts(n, u[:1000], sqrt_s=14000.0, pt_min=-1.0, eta_max=0.0, dr_min=0.4).all()
+
+
+@pytest.mark.parametrize("n", [5, 7])
+def test_cuts_against_direct_evaluation(oracle, n):
+    # eta from arctanh(p_z/|p|) and Delta phi from the angle between the
+    # transverse momenta (a route independent of the oracle's polar-angle
+    # form and of its folding of the azimuth difference)
+    B = 3000
+    u = inputs.rambo_uniforms(n, B, seed=31)
+    got = oracle.accept_cuts(n, u, sqrt_s=14000.0, pt_min=20.0, eta_max=2.5, dr_min=0.4)
+    ref = np.zeros(B, dtype=np.uint8)
+    for e in range(B):
+        p = oracle.rambo(n, 14000.0, u[e])[2:]
+        pt = np.hypot(p[:, 1], p[:, 2])
+        eta = np.arctanh(p[:, 3] / np.linalg.norm(p[:, 1:], axis=1))
+        ok = np.all(pt > 20.0) and np.all(np.abs(eta) < 2.5)
+        for i in range(n - 2):
+            for j in range(i + 1, n - 2):
+                c = np.dot(p[i, 1:3], p[j, 1:3]) / (pt[i] * pt[j])
+                dphi = math.acos(max(-1.0, min(1.0, c)))
+                ok = ok and (eta[i] - eta[j]) ** 2 + dphi ** 2 > 0.16
+        ref[e] = ok
+    assert np.array_equal(got, ref)
+    assert 0.05 < got.mean() < 0.95
+
+
+# --------------------------------------------------------------------------
 # P8: gradient with respect to the Rambo uniforms
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [4, 5])
