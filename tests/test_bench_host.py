@@ -58,3 +58,24 @@ def test_canonical_flop_model():
     assert bench.canonical_recursion_flops(8) == 720 * 7119
     assert bench.canonical_recursion_flops(4) == 2 * (65 * 4 + 46 * 1 + 12 * 3 + 7)
     assert bench.colour_sum_flops(8) == 2 * 720 * 720 + 2 * 720
+
+
+def test_flow_order_counts_brute_force():
+    # the bench's count of closing colour-flow orders (by colour types) against
+    # the direct enumeration of the (n-1)! orders
+    import itertools
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2106_06507_gb300 import inputs
+    for n in (4, 6, 7):
+        cols = inputs.flow_colours(n, 400, seed=7)
+        cols[::2] = inputs.balanced_flow_colours(n, 400, seed=7)[::2]
+        got = bench.flow_order_counts(cols, n)
+        for e in range(0, 400, 7):
+            r, c = cols[e, 0::2], cols[e, 1::2]
+            ref = sum(all(c[o[t]] == r[o[(t + 1) % n]] for t in range(n))
+                      for o in ((0,) + p for p in itertools.permutations(range(1, n))))
+            assert got[e] == ref, (n, e)
+        assert got.max() > 0
