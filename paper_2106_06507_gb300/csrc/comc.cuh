@@ -207,17 +207,39 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
 // in total.
 template <int N>
 struct ComcWalk {
+  // All state in scalars (no dynamically indexed arrays, which would live in
+  // local memory): the candidates left at depth d are the 16-bit lane d & 3
+  // of word d >> 2 of c[0..2]; the label chosen at depth d is nibble d - 1
+  // of `packed`.
   uint64_t packed;
+  uint64_t c0, c1, c2;
   uint32_t avail;
   int d;
-  uint16_t cand[N];
-  uint8_t gl[N];
+
+  __device__ __forceinline__ static uint32_t rmask(const uint32_t (&rm)[3], uint32_t colour) {
+    return colour == 0u ? rm[0] : (colour == 1u ? rm[1] : rm[2]);
+  }
+  __device__ __forceinline__ uint32_t cand(int k) const {
+    const uint64_t w = k < 4 ? c0 : (k < 8 ? c1 : c2);
+    return (uint32_t)((w >> (16 * (k & 3))) & 0xFFFFull);
+  }
+  __device__ __forceinline__ void set_cand(int k, uint32_t v) {
+    const int sh = 16 * (k & 3);
+    const uint64_t m = ~(0xFFFFull << sh), x = (uint64_t)(v & 0xFFFFu) << sh;
+    if (k < 4)
+      c0 = (c0 & m) | x;
+    else if (k < 8)
+      c1 = (c1 & m) | x;
+    else
+      c2 = (c2 & m) | x;
+  }
 
   __device__ __forceinline__ void start(const uint32_t (&rm)[3], uint32_t cp) {
     packed = 0;
+    c0 = c1 = c2 = 0;
     avail = ((1u << N) - 1u) & ~1u;
     d = 1;
-    cand[1] = avail & rm[cp & 3u];
+    set_cand(1, avail & rmask(rm, cp & 3u));
   }
   // Returns the number of orders visited before the walk ended or paused.
   template <typename F>
@@ -225,9 +247,10 @@ struct ComcWalk {
     const int r0 = (rm[0] & 1u) ? 0 : ((rm[1] & 1u) ? 1 : 2);
     int64_t cnt = 0;
     while (d > 0) {
-      if (cand[d]) {
-        const int g = __ffs(cand[d]) - 1;
-        cand[d] &= cand[d] - 1u;
+      const uint32_t cd = cand(d);
+      if (cd) {
+        const int g = __ffs(cd) - 1;
+        set_cand(d, cd & (cd - 1u));
         const uint64_t pk = (packed & ~(0xFull << (4 * (d - 1)))) | ((uint64_t)g << (4 * (d - 1)));
         if (d == N - 1) {
           if ((int)((cp >> (2 * g)) & 3u) == r0) {
@@ -237,13 +260,12 @@ struct ComcWalk {
           continue;
         }
         packed = pk;
-        gl[d] = g;
         avail &= ~(1u << g);
         ++d;
-        cand[d] = avail & rm[(cp >> (2 * g)) & 3u];
+        set_cand(d, avail & rmask(rm, (cp >> (2 * g)) & 3u));
       } else {
         --d;
-        if (d > 0) avail |= 1u << gl[d];
+        if (d > 0) avail |= 1u << (int)((packed >> (4 * (d - 1))) & 0xFull);
       }
     }
     return cnt;
