@@ -159,11 +159,20 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
   for (int m = 0; m < 4; ++m) { br[m] = T(0); by[m] = T(0); W[m] = T(0); }
   T sxy = T(0);
   T cX[M];
+  // loads are issued one step ahead of their use (J(t+2..j) and S_{t+2}
+  // during iteration t, J(s+2..t) during iteration s), so that the shared-
+  // memory latency overlaps arithmetic; the arithmetic order is unchanged
+  T Z[4], St[4];
+  tab_ld<NT>(tab, comc_seg<N>(i + 1, j), Z);
+  tab_ld<NT>(tab, NSEG + i + 1, St);
 #pragma unroll
   for (int t = i; t < j; ++t) {
-    T Z[4], St[4];
-    tab_ld<NT>(tab, comc_seg<N>(t + 1, j), Z);
-    tab_ld<NT>(tab, NSEG + t + 1, St);
+    T Zn[4], Stn[4], Y[4];
+    if (t + 1 < j) {
+      tab_ld<NT>(tab, comc_seg<N>(t + 2, j), Zn);
+      tab_ld<NT>(tab, NSEG + t + 2, Stn);
+    }
+    if (i < t) tab_ld<NT>(tab, comc_seg<N>(i + 1, t), Y);
     // three-vertex term of the split at t
     const T xy0 = mdot(X[t], Z);
     sxy += xy0;
@@ -173,16 +182,27 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
     // four-vertex terms (s, t): X = J(i..s), Y = J(s+1..t), Z = J(t+1..j)
 #pragma unroll
     for (int s = i; s < t; ++s) {
-      T Y[4];
-      tab_ld<NT>(tab, comc_seg<N>(s + 1, t), Y);
+      T Yn[4];
+      if (s + 1 < t) tab_ld<NT>(tab, comc_seg<N>(s + 2, t), Yn);
       const T xz = mdot(X[s], Z);
       const T xy = mdot(X[s], Y);
       const T yz = mdot(Y, Z);
       cX[s] -= yz;
       cR -= xy;
       axpy4(xz, Y, by);
+      if (s + 1 < t) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Y[m] = Yn[m];
+      }
     }
     axpy4(cR, Z, br);
+    if (t + 1 < j) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        Z[m] = Zn[m];
+        St[m] = Stn[m];
+      }
+    }
   }
 #pragma unroll
   for (int s = i; s < j; ++s) axpy4(cX[s], X[s], br);
