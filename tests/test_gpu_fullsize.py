@@ -12,7 +12,11 @@ times, on sampled events that the oracle evaluates one by one.
 - mixed batch, 10^7 events with n uniform in 4..12 in one graph launch: the
   criteria above per branch (the colour-dressed samples, 8 per n, each
   within 1e-3 of max(|M|^2, 1e-2 x the sample median)); at n = 9, bit for bit
-  equal to the single-multiplicity path.
+  equal to the single-multiplicity path;
+- colour-flow sampling with colour-ordered amplitudes, n = 12, 2^20 events,
+  uniform flows; colour-dressed with continuous colour and polarisation-angle
+  sampling, n = 12, 2^20 events; leading colour, n = 8, 2^20 events: the FP32
+  criteria of test_gpu_comc.py, test_gpu_cd.py and test_gpu_lc.py.
 
 The sample always contains the first and last events and the events at the
 edges of 128-event tiles, plus seeded random picks.
@@ -181,3 +185,69 @@ def test_mixed_full_size(bg, oracle):
             assert np.all(np.abs(g[zero]) <= 1e-6 * scale)
             nz = ~zero
             assert np.all(fp32_rel_cd(g[nz], ref[nz]) < 1e-3), (n, g, ref)
+
+
+def test_comc_fp32_full_size(bg, oracle):
+    # colour-flow sampling with colour-ordered amplitudes, n = 12, 2^20 events,
+    # uniform flows (the bench workload): sampled events with a non-zero
+    # estimate against the oracle, the colour-flow FP32 criterion of
+    # test_gpu_comc.py at n >= 10
+    import torch
+    dev = torch.device("cuda:0")
+    n, B = 12, 1 << 20
+    u = inputs.rambo_uniforms(n, B, seed=0)
+    hel = inputs.helicities(n, B, seed=0)
+    cols = inputs.flow_colours(n, B, seed=0)
+    p, acc = bg.momenta_rambo(n, torch.from_numpy(u).to(dev), SQRT_S, PT_MIN)
+    got = bg.currents_co_mc(n, p, torch.from_numpy(np.ascontiguousarray(hel.T)).to(dev),
+                            torch.from_numpy(np.ascontiguousarray(cols.T)).to(dev), prec=bg.BG_F32,
+                            sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    live = np.nonzero(got > 0)[0]
+    rng = np.random.default_rng(50)
+    idx = np.unique(np.concatenate([sample_indices(B, 0, 0), rng.choice(live, 24, replace=False)]))
+    ref = oracle.me2_co_mc(n, u[idx], hel[idx], cols[idx], sqrt_s=SQRT_S, pt_min=PT_MIN)
+    g, r = got[idx], ref
+    scale = r.max()
+    zero = r <= 1e-16 * scale
+    assert np.all(np.abs(g[zero]) <= 1e-6 * scale)
+    nz = ~zero
+    assert nz.sum() >= 12
+    assert np.median(np.abs(g[nz] / r[nz] - 1.0)) < 5e-5
+    assert np.quantile(fp32_rel_cd(g[nz], r[nz]), 0.99) < 2e-3
+
+
+def test_cd_continuous_fp32_full_size(bg, oracle):
+    # colour-dressed with continuous colour and polarisation-angle sampling,
+    # n = 12, 2^20 events: sampled events against the oracle
+    import torch
+    dev = torch.device("cuda:0")
+    n, B = 12, 1 << 20
+    u = inputs.rambo_uniforms(n, B, seed=0)
+    ang = inputs.continuous_angles(n, B, seed=0)
+    p, acc = bg.momenta_rambo(n, torch.from_numpy(u).to(dev), SQRT_S, PT_MIN)
+    a = torch.from_numpy(np.ascontiguousarray(ang.reshape(B, 5 * n).T)).to(dev)
+    got = bg.currents_cd_cont(n, p, a, prec=bg.BG_F32, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    acc_np = acc.cpu().numpy().astype(bool)
+    rng = np.random.default_rng(51)
+    idx = np.unique(np.concatenate([sample_indices(B, 0, 0), rng.choice(np.nonzero(acc_np)[0], 8, replace=False)]))
+    ref = oracle.me2_cd_cont(n, u[idx], ang[idx], sqrt_s=SQRT_S, pt_min=PT_MIN)
+    assert np.all(got[idx][ref == 0] == 0.0)
+    nz = ref > 0
+    assert nz.sum() >= 4
+    assert np.all(fp32_rel_cd(got[idx][nz], ref[nz]) < 2e-3)
+
+
+def test_lc_fp32_full_size(bg, oracle):
+    # leading-colour sum, n = 8, 2^20 events: sampled events against the
+    # oracle (a sum of squares: the FP32 colour-ordered criterion)
+    import torch
+    dev = torch.device("cuda:0")
+    n, B = 8, 1 << 20
+    u = inputs.rambo_uniforms(n, B, seed=0)
+    hel = inputs.helicities(n, B, seed=0)
+    p, acc = bg.momenta_rambo(n, torch.from_numpy(u).to(dev), SQRT_S, PT_MIN)
+    got = bg.currents_lc(n, p, torch.from_numpy(np.ascontiguousarray(hel.T)).to(dev), prec=bg.BG_F32,
+                         sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    idx = sample_indices(B, 40, 52)
+    ref = oracle.me2_lc(n, u[idx], hel=hel[idx], sqrt_s=SQRT_S, pt_min=PT_MIN)
+    check_fp32(got[idx], ref, 2e-6, 1e-3)
