@@ -442,7 +442,8 @@ def run_ours(args) -> None:
         ex = NCU_EXECUTED["flops_per_event"] * BATCH / dom_s / 1e12
         executed = {"achieved": ex, "frac": ex / (NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
                     "flops_per_event": NCU_EXECUTED["flops_per_event"],
-                    "source": "ncu sass counts 2*FFMA+FADD+FMUL of a 2^16-event capture"}
+                    "source": ("ncu sass counts 2*FFMA+FADD+FMUL of a 2^16-event capture, taken before the "
+                               "four-vector updates were packed into f32x2 instructions (same arithmetic)")}
     total_ms = sum(sum(v) for v in kernel_ms.values()) / args.steps
     shares = {f"n{n}_{name}": kernel_ms[n][j] / args.steps / total_ms
               for n in NS for j, name in enumerate(("rambo", "co_recursion", "colour_sum"))}
