@@ -262,6 +262,25 @@ def test_colour_matrix_closed_forms(oracle, n):
     np.linalg.cholesky(C)
 
 
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 9])
+def test_colour_row_integer_scaling(oracle, n):
+    # every entry is a multiple of 432 = 2 N^2 (N^2 - 1) (N = 3); the scaled
+    # entries are integers of at most 8 significant bits up to n = 8 (exact in
+    # BF16, which the tensor-core colour sum relies on) and within the
+    # diagonal 8 (2N)^(n-2) / 432 in magnitude
+    row = np.round(oracle.colour_row(n)).astype(np.int64)
+    assert np.gcd.reduce(np.abs(row)) == 432
+    v = row // 432
+    assert np.all(v * 432 == row)
+    assert np.abs(v).max() == v[0] == 8 * 6 ** (n - 2) // 432
+    nz = np.abs(v[v != 0])
+    sh = np.maximum(np.floor(np.log2(nz)).astype(np.int64) - 7, 0)
+    exact8 = np.all(((nz >> sh) << sh) == nz)
+    # up to n = 8 one BF16 plane holds C / 432 exactly; at n = 9 it does not
+    # (the tensor-core path splits C / 432 into two BF16 planes there)
+    assert exact8 == (n <= 8)
+
+
 def test_colour_matrix_depends_on_relative_permutation(oracle):
     for n in (5, 6):
         k = math.factorial(n - 2)
