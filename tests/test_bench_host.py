@@ -79,3 +79,23 @@ def test_flow_order_counts_brute_force():
                       for o in ((0,) + p for p in itertools.permutations(range(1, n))))
             assert got[e] == ref, (n, e)
         assert got.max() > 0
+
+
+def test_reference_arm_json_contract(monkeypatch, capsys):
+    # the reference arm (the oracle on the host cores) prints one JSON line
+    # with the contract's keys; tiny per-step samples keep this quick
+    import json
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "REF_STEP_SAMPLE", {5: 16, 6: 8, 7: 4, 8: 2})
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.run_reference(types.SimpleNamespace(gpus=1, steps=2, warmup=0))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "events/s" and line["value"] > 0
+    assert line["higher_is_better"] is True and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "events/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
