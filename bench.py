@@ -56,25 +56,60 @@ SQRT_S = 1000.0
 PT_MIN = 20.0
 SEED = 0
 FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
 L2_BYTES = 129 * 1024 * 1024
 
 WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqrt(s)=1 TeV, pT>20 GeV, "
             "sampled helicities, FP32 currents for all (n-2)! orderings, exact colour sum A^T C A")
 
-# DRAM traffic of the dominant kernel from one ncu capture (bytes per launch at
-# n = 8, 2^20 events, scaled from a 2^16-event capture by the number of
-# events), valid only for the kernel sources it was taken from.
-NCU_TRAFFIC = {"sources_sha1": "9db31df7b2c5dcc140f9d5b64185b3258c6c0b03",
-               "bytes_per_launch": 16 * (17377024 + 127708416)}  # 2^16-event capture x 16
-# Executed FP32 operations per event of the dominant kernel at n = 8 (ncu sass
-# counts 2 x FFMA + FADD + FMUL of a 2^16-event capture, taken before the
-# four-vector updates were packed into f32x2 instructions: the sass counters do
-# not count the packed forms, and packing leaves the arithmetic unchanged).
-NCU_EXECUTED = {"sources_sha1": "9db31df7b2c5dcc140f9d5b64185b3258c6c0b03", "flops_per_event": 2524693}
+# The ncu figures of the dominant kernel (executed FP32 operations per event
+# and DRAM bytes per event) are read from the committed summary of the capture,
+# which states the kernel sources it was taken on; they are used only while
+# those sources are unchanged.
+NCU_SUMMARY = os.path.join(ROOT, "profiles", "co_kernel_dfs_n8.md")
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
+
+
+def ncu_figures(path: str = NCU_SUMMARY) -> dict | None:
+    """The `bench-figures:` line of an ncu summary: key=value pairs
+    (sources_sha1, executed_flops_per_event, dram_bytes_per_event, ...)."""
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("bench-figures:"):
+                    out = {}
+                    for kv in line.split(":", 1)[1].split():
+                        k, v = kv.split("=", 1)
+                        out[k] = v if k == "sources_sha1" else float(v)
+                    return out
+    except OSError:
+        return None
+    return None
+
+
+def fp32_peak_tflops(sms: int) -> float:
+    """FP32 pipe peak from unit counts: SMs x 128 lanes x 2 FLOP x max clock."""
+    return sms * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+
+
+def fp32_peak_source(sms: int) -> str:
+    return f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x {MAX_SM_MHZ:.0f} MHz (unit counts, max clock)"
+
+
+def roofline(kernel: str, bound: str, achieved: float, peak: float, unit: str, peak_source: str,
+             traffic=None, **extra) -> dict:
+    """The roofline object of a bench line: achieved / peak of one kernel."""
+    d = {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+         "frac": (achieved / peak) if (achieved is not None and peak) else None, "traffic": traffic,
+         "peak_source": peak_source}
+    d.update(extra)
+    return d
+
+
+def device_sms(dev) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 def cs_mode_for(bg, n: int) -> int:
@@ -193,71 +228,65 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
-CPU_SAMPLE = {5: 1 << 22, 6: 1 << 21, 7: 1 << 19, 8: 1 << 17}
-REF_STEP_SAMPLE = {5: 1 << 16, 6: 1 << 14, 7: 1 << 12, 8: 1 << 10}
+CPU_SAMPLE_PER_N = 1 << 17  # cpu_baseline: events of each n (about 10 s of the oracle on 16 Arm cores)
+REF_STEP_PER_N = 8192       # reference arm: events of each n per step
 
 
-def oracle_rates(sample: dict) -> tuple[dict, int, float]:
-    """events/s of the oracle per n on `sample[n]` events (all host cores)."""
+def oracle_step(per_n: int) -> tuple[dict, int]:
+    """The oracle on the first `per_n` events of each multiplicity of the
+    default workload (its own seeded inputs, made before the clock starts),
+    on all host cores; returns the seconds per n and the core count."""
     from oracle import oracle as O
     from paper_2106_06507_gb300 import inputs
-    rates = {}
-    total = 0.0
+    secs = {}
     for n in NS:
-        B = sample[n]
-        u = inputs.rambo_uniforms(n, B, seed=SEED + 1)
-        hel = inputs.helicities(n, B, seed=SEED + 1)
+        u = inputs.rambo_uniforms(n, per_n, seed=SEED)
+        hel = inputs.helicities(n, per_n, seed=SEED)
         O.colour_matrix(n)
         t0 = time.perf_counter()
         O.me2_co(n, u, sqrt_s=SQRT_S, hel=hel, pt_min=PT_MIN)
-        dt = time.perf_counter() - t0
-        rates[n] = B / dt
-        total += dt
-    return rates, O.n_cores(), total
-
-
-def aggregate_rate(rates: dict, batch: int = BATCH) -> float:
-    """events/s of a step (batch events of every n) from per-n rates."""
-    t = sum(batch / rates[n] for n in NS)
-    return len(NS) * batch / t
+        secs[n] = time.perf_counter() - t0
+    return secs, O.n_cores()
 
 
 def cpu_baseline() -> dict:
-    rates, cores, secs = oracle_rates(CPU_SAMPLE)
-    return {"value": aggregate_rate(rates), "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": ("FP64 C++ oracle, all host threads, per n: "
-                       + ", ".join(f"n={n}: {CPU_SAMPLE[n]} events" for n in NS)
-                       + f" of the same workload ({secs:.1f} s); value = events/s of the full step "
-                       "extrapolated from the per-n rates"),
-            "per_n": {str(n): rates[n] for n in NS}}
+    secs, cores = oracle_step(CPU_SAMPLE_PER_N)
+    total = sum(secs.values())
+    return {"value": len(NS) * CPU_SAMPLE_PER_N / total, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 C++ oracle on all host threads, the first {CPU_SAMPLE_PER_N} events of each n of the "
+                       f"default workload (n = 5..8 in equal numbers, as in the workload): {total:.1f} s"),
+            "per_n": {str(n): CPU_SAMPLE_PER_N / secs[n] for n in NS}}
 
 
 def run_reference(args) -> None:
+    """The oracle as the reference arm: each step runs it on REF_STEP_PER_N
+    events of each multiplicity of the default workload (equal numbers per n,
+    as in the workload), so that events/s is directly the workload's rate."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_rates(REF_STEP_SAMPLE)
-    step_rates = []
+        oracle_step(REF_STEP_PER_N)
     t_total = 0.0
+    per_n_secs = {n: 0.0 for n in NS}
+    cores = 0
     for _ in range(args.steps):
-        rates, cores, secs = oracle_rates(REF_STEP_SAMPLE)
-        step_rates.append(rates)
-        t_total += secs
-    per_n = {n: statistics.median(r[n] for r in step_rates) for n in NS}
-    value = aggregate_rate(per_n)
-    sample = ("FP64 C++ oracle on all host threads, each step per n: "
-              + ", ".join(f"n={n}: {REF_STEP_SAMPLE[n]} events" for n in NS)
-              + "; value = events/s of the full step extrapolated from the per-n rates")
+        secs, cores = oracle_step(REF_STEP_PER_N)
+        t_total += sum(secs.values())
+        for n in NS:
+            per_n_secs[n] += secs[n]
+    events = len(NS) * REF_STEP_PER_N * args.steps
+    value = events / t_total
+    sample = (f"FP64 C++ oracle on all host threads; each step the first {REF_STEP_PER_N} events of each n = 5..8 "
+              "of the default workload")
     print(json.dumps({
         "impl": "reference", "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(NS) * BATCH / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S,
-                   "pt_min_gev": PT_MIN},
+        "config": ref_arm_config() | {"events_per_step": len(NS) * REF_STEP_PER_N},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "per_n": {str(n): per_n[n] for n in NS},
+        "per_n": {str(n): REF_STEP_PER_N * args.steps / per_n_secs[n] for n in NS},
     }), flush=True)
 
 
@@ -278,6 +307,7 @@ def run_ours(args) -> None:
     from paper_2106_06507_gb300 import bg, build_lib, inputs
     build_lib.build()
     bg.lib()
+    sms = device_sms(dev)
 
     stream = torch.cuda.current_stream(dev)
     f64 = args.precision == "f64"
@@ -339,18 +369,9 @@ def run_ours(args) -> None:
             if record:
                 ev[n][3].record(stream)
 
-    # FP32 / FP64 pipe peaks measured by the FMA probe (for context)
-    def probe(prec, iters):
-        bg.probe_fma(prec, NUM_SMS * 8, 64, stream=stream)
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        fl = bg.probe_fma(prec, NUM_SMS * 8, iters, stream=stream)
-        s1.record(stream)
-        torch.cuda.synchronize(dev)
-        return fl / (s0.elapsed_time(s1) * 1e-3) / 1e12
-
-    probe_f32 = probe(bg.BG_F32, 20000)
-    probe_f64 = probe(bg.BG_F64, 500)
+    # FP32 / FP64 pipe rates of the FMA probe (measured, for context)
+    probe_f32 = fma_probe_tflops(True, sms, stream, dev, 20000)
+    probe_f64 = fma_probe_tflops(False, sms, stream, dev, 500)
     # kernel variants of the recursion chosen by the library's autotuner on
     # this GPU (they give bitwise identical results)
     probe_batch = (1 << 14) if f64 else (1 << 18)
@@ -361,11 +382,7 @@ def run_ours(args) -> None:
     torch.cuda.synchronize(dev)
     barrier()
 
-    props = torch.cuda.get_device_properties(dev)
-    gpu_id = str(getattr(props, "uuid", "")) or str(local)
-    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
-        gpu_id = "GPU-" + gpu_id
-    clocks = ClockSampler(gpu_id)
+    clocks = ClockSampler(gpu_uuid(dev, local))
     clocks.start()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -424,72 +441,277 @@ def run_ours(args) -> None:
     for n in NS:
         if not torch.equal(host_m[n], ME2[n].cpu()):
             raise RuntimeError(f"e2e |M|^2 differs from the device-resident run at n={n}")
+    for n in NS:
+        plans[n].close()
+    del host_u, host_h, host_m
 
-    # roofline of the dominant kernel (colour-ordered recursion at n = 8)
+    # roofline of the dominant kernel (the colour-ordered recursion at n = 8)
     n_dom = max(NS, key=lambda n: kernel_ms[n][1])
     dom_s = kernel_ms[n_dom][1] / args.steps * 1e-3
-    flops = canonical_recursion_flops(n_dom) * BATCH
-    achieved = flops / dom_s / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    if f64:  # FP64 pipe: no unit count to quote; the FMA probe's measured rate
-        peak = probe_f64
-    traffic = None
-    executed = None
     dfs = tuned.get(n_dom, 0) != 0  # the ncu figures are for the depth-first kernel
-    if NCU_TRAFFIC["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64 and dfs:
-        traffic = NCU_TRAFFIC["bytes_per_launch"]
-    if NCU_EXECUTED["sources_sha1"] == sources_sha1() and n_dom == 8 and not f64 and dfs:
-        ex = NCU_EXECUTED["flops_per_event"] * BATCH / dom_s / 1e12
-        executed = {"achieved": ex, "frac": ex / (NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
-                    "flops_per_event": NCU_EXECUTED["flops_per_event"],
-                    "source": ("ncu sass counts 2*FFMA+FADD+FMUL of a 2^16-event capture, taken before the "
-                               "four-vector updates were packed into f32x2 instructions (same arithmetic)")}
+    kname = (f"{'co_kernel_dfs' if dfs else 'co_kernel'}<{n_dom},{'double' if f64 else 'float'}> "
+             f"(colour-ordered recursion, tuned variant {tuned.get(n_dom, 0)})")
+    canonical = canonical_recursion_flops(n_dom) * BATCH
+    canon = {"achieved": canonical / dom_s / 1e12, "flops_per_launch": canonical,
+             "flops_model": "canonical (V3=65, V4=46, prop=12, final=7 per ordering)"}
+    if f64:  # FP64 pipe: the FMA probe's measured rate
+        canon["frac"] = canon["achieved"] / probe_f64
+        roof = roofline(kname, "alu", canon["achieved"], probe_f64, "TFLOP/s", "FP64 FMA probe (measured)",
+                        canonical=canon)
+    else:
+        peak = fp32_peak_tflops(sms)
+        canon["frac"] = canon["achieved"] / peak
+        fig = ncu_figures()
+        valid = bool(fig) and fig.get("sources_sha1") == sources_sha1() and n_dom == 8 and dfs
+        if valid:
+            ex_flops = fig["executed_flops_per_event"] * BATCH
+            roof = roofline(kname, "alu", ex_flops / dom_s / 1e12, peak, "TFLOP/s", fp32_peak_source(sms),
+                            traffic=fig["dram_bytes_per_event"] * BATCH,
+                            flops_per_launch=ex_flops,
+                            flops_model=("executed FP32 operations counted by ncu on these kernel sources: "
+                                         "2 FFMA + FADD + FMUL + 2 (2 FFMA2 + FADD2 + FMUL2) per event x events"),
+                            ncu_summary=os.path.relpath(NCU_SUMMARY, ROOT), sources_sha1=fig["sources_sha1"],
+                            canonical=canon, probe_fp32_tflops=probe_f32, probe_fp64_tflops=probe_f64)
+        else:
+            roof = roofline(kname, "alu", canon["achieved"], peak, "TFLOP/s", fp32_peak_source(sms),
+                            flops_per_launch=canonical,
+                            flops_model=("canonical (no ncu count of executed operations for these kernel "
+                                         "sources)"), canonical=canon,
+                            probe_fp32_tflops=probe_f32, probe_fp64_tflops=probe_f64)
     total_ms = sum(sum(v) for v in kernel_ms.values()) / args.steps
     shares = {f"n{n}_{name}": kernel_ms[n][j] / args.steps / total_ms
               for n in NS for j, name in enumerate(("rambo", "co_recursion", "colour_sum"))}
+    per_n = {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS}
+    for n in NS:  # free the headline's buffers before the other workloads
+        CM[n].close()
+    del U, HEL, P, ACC, AMPS, ME2
+    torch.cuda.empty_cache()
+
+    # the other workloads of the scope table, measured in the same run with
+    # the same rules (CUDA events on the launching stream, warm-up steps, L2
+    # flushed between timed steps): the plain FP64 GPU form of this workload,
+    # the colour-dressed recursion, the gradient and a mixed batch
+    extra_launches = 0
+    per_precision = workloads = None
+    side_clk = None
+    if not f64 and not args.headline_only:
+        side_clocks = ClockSampler(gpu_uuid(dev, local))
+        side_clocks.start()
+        per_precision, l0 = side_fp64(bg, inputs, dev, stream, rank, value, per_n)
+        cd, l1 = side_cd(bg, inputs, dev, stream, rank, sms)
+        grad, l2 = side_grad(bg, inputs, dev, stream, rank)
+        mixed, l3 = side_mixed(bg, inputs, dev, stream, rank)
+        side_clk = side_clocks.stop()
+        workloads = {"cd": cd, "grad": grad, "mixed": mixed}
+        extra_launches = l0 + l1 + l2 + l3
 
     if rank == 0:
         line = {
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S,
-                       "pt_min_gev": PT_MIN, "helicities": "sampled, weight 2^n",
-                       "precision": ("FP64 currents and FP64 colour sum (CUDA cores)" if f64 else
-                                     "FP32 currents; colour sum on tcgen05 tensor cores (BF16x3 amplitude split, "
-                                     "FP32 accumulate) for n=6..8, FP32 CUDA cores for n=5; "
-                                     "FP64 Rambo/polarisations/per-event accumulation"),
-                       "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB of uniforms per step",
-                       "tuned_variants": {str(n): v for n, v in tuned.items()}},
-            "per_n": {str(n): BATCH * world / (sum(kernel_ms[n]) / args.steps * 1e-3) for n in NS},
+            "config": ref_arm_config() | {
+                "precision": ("FP64 currents and FP64 colour sum (CUDA cores)" if f64 else
+                              "FP32 currents; colour sum on tcgen05 tensor cores (BF16x3 amplitude split, "
+                              "FP32 accumulate) for n=6..8, FP32 CUDA cores for n=5; "
+                              "FP64 Rambo/polarisations/per-event accumulation"),
+                "parallelism": f"replicas x{world}",
+                "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB of uniforms per step",
+                "tuned_variants": {str(n): v for n, v in tuned.items()}},
+            "per_n": per_n,
             "kernel_ms_per_step": {f"n{n}": [round(x / args.steps, 4) for x in kernel_ms[n]] for n in NS},
             "schedule": ("Rambo for all n on a side stream ahead of the recursions and colour sums (FP64 and FP32 "
                          "pipes overlap); kernel_ms_per_step and kernel_share from the same step serialised"),
             "kernel_share": {k: round(v, 4) for k, v in shares.items()},
-            "roofline": {"kernel": (f"{'co_kernel_dfs' if dfs else 'co_kernel'}<{n_dom},{'double' if f64 else 'float'}> "
-                                    f"(colour-ordered recursion, tuned variant {tuned.get(n_dom, 0)})"),
-                         "bound": "alu",
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": traffic,
-                         "flops_per_launch": flops, "flops_model": "canonical (V3=65, V4=46, prop=12, final=7)",
-                         "executed": executed,
-                         "peak_source": ("FP64 FMA probe (measured)" if f64 else
-                                         "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (unit counts, max clock)"),
-                         "probe_fp32_tflops": probe_f32, "probe_fp64_tflops": probe_f64},
+            "roofline": roof,
             "cpu_baseline": None,
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
         }
+        if per_precision is not None:
+            line["per_precision"] = per_precision
+            line["workloads"] = workloads
+            line["workloads_clocks"] = side_clk
+            line["workloads_gpu_launches"] = extra_launches
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
-    for n in NS:
-        plans[n].close()
-        CM[n].close()
     if world > 1 and dist.is_initialized():
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the other workloads, reported beside the headline in the default line
+# ---------------------------------------------------------------------------
+SIDE_WARMUP = 3
+SIDE_STEPS = 3
+FP64_BATCH = 1 << 18     # plain FP64 GPU form of the default workload, per n
+CD_SIDE_BATCH = 1 << 17  # colour-dressed, per n
+MIXED_SIDE_EVENTS = 1_000_000
+
+
+def flush_l2(dev):
+    import torch
+    buf = getattr(flush_l2, "buf", None)
+    if buf is None or buf.device != dev:
+        buf = flush_l2.buf = torch.empty((2 * L2_BYTES,), dtype=torch.uint8, device=dev)
+    buf.fill_(1)
+
+
+def timed_side(step, dev, stream) -> float:
+    """SIDE_WARMUP untimed steps, then SIDE_STEPS steps each between CUDA events
+    on `stream`, with L2 flushed (outside the events) before each; returns the
+    seconds per step (max over ranks)."""
+    import torch
+    for _ in range(SIDE_WARMUP):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    total = 0.0
+    for _ in range(SIDE_STEPS):
+        flush_l2(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        total += a.elapsed_time(b) * 1e-3
+    return max_over_ranks(total / SIDE_STEPS, dev)
+
+
+def side_fp64(bg, inputs, dev, stream, rank, value32, per_n32):
+    """The plain FP64 GPU form of the default workload (FP64 currents, FP64
+    colour sum on CUDA cores), FP64_BATCH events per n."""
+    import numpy as np
+    import torch
+    B = FP64_BATCH
+    first = rank * BATCH
+    bufs = {}
+    for n in NS:
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED, first_event=first)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED, first_event=first).T)).to(dev)
+        bufs[n] = (u, h, torch.empty((4, n, B), dtype=torch.float64, device=dev),
+                   torch.empty((B,), dtype=torch.uint8, device=dev),
+                   torch.empty((B, 1, math.factorial(n - 2)), dtype=torch.float64, device=dev),
+                   torch.empty((B,), dtype=torch.float64, device=dev), bg.ColourMatrix(n))
+
+    def one(n):
+        u, h, p, acc, amps, me2, C = bufs[n]
+        bg.momenta_rambo(n, u, SQRT_S, PT_MIN, p=p, accept=acc, stream=stream)
+        bg.currents_co(n, p, h, prec=bg.BG_F64, sqrt_s=SQRT_S, amps=amps, stream=stream)
+        bg.color_sum(C, amps, True, mode=bg.BG_CS_F64, sqrt_s=SQRT_S, accept=acc, me2=me2, stream=stream)
+
+    for n in NS:
+        if n >= 6:
+            bg.autotune(bg.BG_ALGO_CO, n, bg.BG_F64, probe_batch=1 << 14, stream=stream)
+    per_n = {str(n): B / timed_side(lambda n=n: one(n), dev, stream) for n in NS}
+    value = len(NS) * B / sum(B / per_n[str(n)] for n in NS)
+    for n in NS:
+        bufs[n][-1].close()
+    launches = (SIDE_WARMUP + SIDE_STEPS) * 3 * len(NS)
+    return {"f64": {"value": value, "unit": "events/s", "per_n": per_n, "batch_per_n": B,
+                    "precision": "FP64 currents, FP64 colour sum (CUDA cores), FP64 Rambo",
+                    "steps": SIDE_STEPS, "warmup": SIDE_WARMUP, "l2": "flushed before each timed step"},
+            "f32": {"value": value32, "unit": "events/s", "per_n": per_n32,
+                    "precision": "the headline (FP32 currents, tensor-core colour sum)"},
+            "f32_over_f64": value32 / value,
+            "f32_over_f64_per_n": {str(n): per_n32[str(n)] / per_n[str(n)] for n in NS}}, launches
+
+
+def side_cd(bg, inputs, dev, stream, rank, sms):
+    """Colour-dressed recursion with sampled adjoint colours (config 3: n = 8,
+    10, 12, FP32), CD_SIDE_BATCH events per n."""
+    import numpy as np
+    import torch
+    B = CD_SIDE_BATCH
+    first = rank * BATCH
+    bufs = {}
+    for n in CD_NS:
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED, first_event=first)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED, first_event=first).T)).to(dev)
+        c = torch.from_numpy(np.ascontiguousarray(inputs.adjoint_colours(n, B, seed=SEED, first_event=first).T)).to(dev)
+        bufs[n] = (u, h, c, torch.empty((4, n, B), dtype=torch.float64, device=dev),
+                   torch.empty((B,), dtype=torch.uint8, device=dev), torch.empty((B,), dtype=torch.float64, device=dev))
+    times = {}
+    for n in CD_NS:
+        u, h, c, p, acc, me2 = bufs[n]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+        def full_step(n=n, u=u, h=h, c=c, p=p, acc=acc, me2=me2, ev=ev):
+            bg.momenta_rambo(n, u, SQRT_S, PT_MIN, p=p, accept=acc, stream=stream)
+            ev[0].record(stream)
+            bg.currents_cd(n, p, h, c, prec=bg.BG_F32, sqrt_s=SQRT_S, accept=acc, me2=me2, stream=stream)
+            ev[1].record(stream)
+
+        step_s = timed_side(full_step, dev, stream)
+        times[n] = (step_s, ev[0].elapsed_time(ev[1]) * 1e-3)  # kernel time of the last timed step
+    per_n = {str(n): B / times[n][0] for n in CD_NS}
+    value = len(CD_NS) * B / sum(times[n][0] for n in CD_NS)
+    n_dom = 12
+    accepted = int(bufs[n_dom][4].sum().item())
+    flops = cd_dense_flops(n_dom) * accepted
+    peak = fp32_peak_tflops(sms)
+    roof = roofline(f"cd_kernel<{n_dom},float> (colour-dressed recursion)", "alu", flops / times[n_dom][1] / 1e12,
+                    peak, "TFLOP/s", fp32_peak_source(sms),
+                    flops_model=("dense 3x3x3 colour products per ordered partition (56 FMA per (r,l,c), 4 per "
+                                 "(r,l)) x events passing the cut"),
+                    flops_per_event=cd_dense_flops(n_dom), events_computed=accepted,
+                    kernel_ms=times[n_dom][1] * 1e3)
+    launches = (SIDE_WARMUP + SIDE_STEPS) * 2 * len(CD_NS)
+    return {"workload": ("colour-dressed BG with sampled adjoint colours (1..8), n=8,10,12, "
+                         f"{B} Rambo points per n at sqrt(s)=1 TeV, pT>20 GeV, sampled helicities, FP32 currents "
+                         "(the 2^20-event configuration at an eighth of the batch)"),
+            "value": value, "unit": "events/s", "per_n": per_n, "batch_per_n": B, "steps": SIDE_STEPS,
+            "warmup": SIDE_WARMUP, "l2": "flushed before each timed step", "roofline": roof}, launches
+
+
+def side_grad(bg, inputs, dev, stream, rank):
+    """|M|^2 and d|M|^2/du (config 4: n = 6, 8, 2^18 events per n, FP32)."""
+    import numpy as np
+    import torch
+    B = GRAD_BATCH
+    first = rank * B
+    per_n, launches = {}, 0
+    for n in GRAD_NS:
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED, first_event=first)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED, first_event=first).T)).to(dev)
+        g = torch.empty_like(u)
+        m = torch.empty((B,), dtype=torch.float64, device=dev)
+        plan = bg.Plan(n, B, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_F32, hel_sampled=True, grad=True)
+        per_n[str(n)] = B / timed_side(lambda: plan.grad(u, h, me2=m, out=g, stream=stream), dev, stream)
+        plan.close()
+        launches += (SIDE_WARMUP + SIDE_STEPS) * 5
+    value = len(GRAD_NS) * B / sum(B / per_n[str(n)] for n in GRAD_NS)
+    return {"workload": ("|M|^2 and d|M|^2/du (4(n-2) Rambo uniforms), colour-ordered FP32 with full colour sum, "
+                         "n=6,8, 2^18 events per n, pT>20 GeV, sampled helicities"),
+            "value": value, "unit": "events/s", "per_n": per_n, "batch_per_n": B, "steps": SIDE_STEPS,
+            "warmup": SIDE_WARMUP, "l2": "flushed before each timed step"}, launches
+
+
+def side_mixed(bg, inputs, dev, stream, rank):
+    """A mixed batch (config 5 at a tenth of its size): MIXED_SIDE_EVENTS
+    events with n uniform in 4..12, one launch."""
+    import numpy as np
+    import torch
+    B = MIXED_SIDE_EVENTS
+    evs = inputs.mixed_events(B, 4, 12, seed=SEED + rank, colours="adjoint")
+    mx = bg.Mixed(4, 12, B, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_TC_BF16,
+                  color_mode=bg.BG_COL_ADJOINT, n_co_max=9, autotune=True)
+    mx.n_per_event.copy_(torch.from_numpy(evs["nev"]))
+    mx.u.copy_(torch.from_numpy(evs["u"]))
+    mx.hel.copy_(torch.from_numpy(np.ascontiguousarray(evs["hel"].T)))
+    mx.colors.copy_(torch.from_numpy(np.ascontiguousarray(evs["colors"].T)))
+    t = timed_side(lambda: mx.run(B, stream=stream), dev, stream)
+    counts = mx.counts()[4:]
+    mx.close()
+    return {"workload": ("mixed batch: 10^6 events (the 10^7-event configuration at a tenth of its size) with n "
+                         "uniform in 4..12 in one launch: colour-ordered + tensor-core colour sum for n=6..9 (FP32 "
+                         "CUDA cores n=4,5), colour-dressed with sampled adjoint colours for n=10..12, FP32 currents, "
+                         "FP64 Rambo and accumulation, pT>20 GeV, autotuned kernel variants"),
+            "value": B / t, "unit": "events/s", "events": B, "counts_per_n": counts, "seconds_per_step": t,
+            "steps": SIDE_STEPS, "warmup": SIDE_WARMUP, "l2": "flushed before each timed step",
+            "launch": "one CUDA-graph launch per step"}, 0
 
 
 def timed_steps(step, args, dev, stream) -> tuple[float, dict]:
@@ -501,11 +723,7 @@ def timed_steps(step, args, dev, stream) -> tuple[float, dict]:
         step()
     torch.cuda.synchronize(dev)
     barrier()
-    props = torch.cuda.get_device_properties(dev)
-    gpu_id = str(getattr(props, "uuid", "")) or str(dev.index)
-    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
-        gpu_id = "GPU-" + gpu_id
-    clocks = ClockSampler(gpu_id)
+    clocks = ClockSampler(gpu_uuid(dev, dev.index))
     clocks.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
@@ -533,16 +751,42 @@ def timed_host(step, args, dev) -> float:
     return max_over_ranks(time.perf_counter() - w0, dev)
 
 
-def fma_probe_tflops(bg, prec, stream, dev, iters: int) -> float:
-    """Measured FMA-pipe rate (TFLOP/s) of the library's probe kernel."""
+def fma_probe_tflops(f32: bool, sms: int, stream, dev, iters: int) -> float:
+    """Measured FMA-pipe rate (TFLOP/s) of the probe kernel of libbg_probe.so
+    (8 blocks of 256 threads per SM)."""
+    import ctypes
+
     import torch
-    bg.probe_fma(prec, NUM_SMS * 8, 64, stream=stream)
+    from paper_2106_06507_gb300 import build_lib
+    lib = ctypes.CDLL(build_lib.PROBE_LIB)
+    lib.bgprobe_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                ctypes.c_void_p]
+    flops = ctypes.c_double(0.0)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    if lib.bgprobe_fma(int(f32), sms * 8, 64, ctypes.byref(flops), sp) != 0:
+        raise RuntimeError("FMA probe launch failed")
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(stream)
-    fl = bg.probe_fma(prec, NUM_SMS * 8, iters, stream=stream)
+    if lib.bgprobe_fma(int(f32), sms * 8, iters, ctypes.byref(flops), sp) != 0:
+        raise RuntimeError("FMA probe launch failed")
     s1.record(stream)
     torch.cuda.synchronize(dev)
-    return fl / (s0.elapsed_time(s1) * 1e-3) / 1e12
+    return flops.value / (s0.elapsed_time(s1) * 1e-3) / 1e12
+
+
+def gpu_uuid(dev, local: int) -> str:
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", "")) or str(local)
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    return gpu_id
+
+
+def ref_arm_config() -> dict:
+    """The workload keys of the default line, shared by both arms."""
+    return {"workload": WORKLOAD, "n": list(NS), "batch_per_n": BATCH, "sqrt_s_gev": SQRT_S, "pt_min_gev": PT_MIN,
+            "helicities": "sampled, weight 2^n"}
 
 
 def cd_dense_flops(n: int) -> int:
@@ -653,10 +897,10 @@ def run_cd(args) -> None:
     accepted = int(ACC[n_dom].sum().item())  # events failing the cut are skipped by the kernel
     flops = cd_dense_flops(n_dom) * accepted
     achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    sms = device_sms(dev)
+    peak, peak_source = fp32_peak_tflops(sms), fp32_peak_source(sms)
     if cd_prec == bg.BG_F64:
-        peak, peak_source = fma_probe_tflops(bg, bg.BG_F64, stream, dev, 500), "FP64 FMA probe (measured)"
+        peak, peak_source = fma_probe_tflops(False, sms, stream, dev, 500), "FP64 FMA probe (measured)"
     if rank == 0:
         print(json.dumps({
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -672,13 +916,11 @@ def run_cd(args) -> None:
                        "l2": "inputs larger than L2"},
             "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in CD_NS},
             "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in CD_NS},
-            "roofline": {"kernel": f"cd_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
-                         "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "flops_model": "dense 3x3x3 colour products per ordered partition (56 FMA per "
-                                        "(r,l,c), 4 per (r,l)) x events passing the cut",
-                         "flops_per_event": cd_dense_flops(n_dom), "events_computed": accepted,
-                         "peak_source": peak_source},
+            "roofline": roofline(f"cd_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
+                                 "alu", achieved, peak, "TFLOP/s", peak_source,
+                                 flops_model=("dense 3x3x3 colour products per ordered partition (56 FMA per "
+                                              "(r,l,c), 4 per (r,l)) x events passing the cut"),
+                                 flops_per_event=cd_dense_flops(n_dom), events_computed=accepted),
             "e2e": {"value": world * len(CD_NS) * batch * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(CD_NS) * batch * 8},
             "gpu_launches": 2 * len(CD_NS) * args.steps, "clocks": clk}), flush=True)
@@ -798,10 +1040,10 @@ def run_comc(args) -> None:
     per_order = canonical_recursion_flops(n_dom) // math.factorial(n_dom - 2)
     flops = per_order * n_orders
     achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    sms = device_sms(dev)
+    peak, peak_source = fp32_peak_tflops(sms), fp32_peak_source(sms)
     if prec == bg.BG_F64:
-        peak, peak_source = fma_probe_tflops(bg, bg.BG_F64, stream, dev, 500), "FP64 FMA probe (measured)"
+        peak, peak_source = fma_probe_tflops(False, sms, stream, dev, 500), "FP64 FMA probe (measured)"
     if rank == 0:
         print(json.dumps({
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -816,13 +1058,11 @@ def run_comc(args) -> None:
             "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in COMC_NS},
             "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in COMC_NS},
             "orders_per_event": {str(n): float(orders[n].mean()) for n in COMC_NS},
-            "roofline": {"kernel": f"comc_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
-                         "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "flops_model": "canonical recursion FLOPs of one order x closing orders of the events "
-                                        "passing the cut",
-                         "flops_per_order": per_order, "orders_computed": n_orders,
-                         "peak_source": peak_source},
+            "roofline": roofline(f"comc_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
+                                 "alu", achieved, peak, "TFLOP/s", peak_source,
+                                 flops_model=("canonical recursion FLOPs of one order x closing orders of the "
+                                              "events passing the cut"),
+                                 flops_per_order=per_order, orders_computed=n_orders),
             "e2e": {"value": world * len(COMC_NS) * batch * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(COMC_NS) * batch * 8},
             "gpu_launches": 2 * len(COMC_NS) * args.steps, "clocks": clk}), flush=True)
@@ -894,10 +1134,10 @@ def run_lc(args) -> None:
     n_dom = max(NS, key=lambda n: kernel_ms[n][1])
     flops = canonical_recursion_flops(n_dom) * (n_dom - 1) * batch  # (n-1)! orders = (n-1) x (n-2)!
     achieved = flops / (kernel_ms[n_dom][1] * 1e-3) / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    peak_source = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    sms = device_sms(dev)
+    peak, peak_source = fp32_peak_tflops(sms), fp32_peak_source(sms)
     if prec == bg.BG_F64:
-        peak, peak_source = fma_probe_tflops(bg, bg.BG_F64, stream, dev, 500), "FP64 FMA probe (measured)"
+        peak, peak_source = fma_probe_tflops(False, sms, stream, dev, 500), "FP64 FMA probe (measured)"
     if rank == 0:
         print(json.dumps({
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -910,12 +1150,10 @@ def run_lc(args) -> None:
                        "l2": "inputs larger than L2"},
             "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in NS},
             "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in NS},
-            "roofline": {"kernel": f"bg_currents_lc at n={n_dom} ({n_dom - 1} recursion launches)",
-                         "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "flops_model": "canonical recursion FLOPs per order x (n-1)! orders x events",
-                         "flops_per_event": canonical_recursion_flops(n_dom) * (n_dom - 1),
-                         "peak_source": peak_source},
+            "roofline": roofline(f"bg_currents_lc at n={n_dom} ({n_dom - 1} recursion launches)", "alu",
+                                 achieved, peak, "TFLOP/s", peak_source,
+                                 flops_model="canonical recursion FLOPs per order x (n-1)! orders x events",
+                                 flops_per_event=canonical_recursion_flops(n_dom) * (n_dom - 1)),
             "e2e": {"value": world * len(NS) * batch * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(NS) * batch * 8},
             "gpu_launches": sum(1 + 3 * (n - 1) for n in NS) * args.steps, "clocks": clk}), flush=True)
@@ -994,7 +1232,8 @@ def run_paper(args) -> None:
     h2d = sum(sum(x.numel() * x.element_size() for x in host[n]) for n in NS)
     n_dom = max(NS, key=lambda n: kernel_ms[n][1])
     achieved = canonical_recursion_flops(n_dom) * BATCH / (kernel_ms[n_dom][1] * 1e-3) / 1e12
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    sms = device_sms(dev)
+    peak = fp32_peak_tflops(sms)
     # uniforms, momenta, helicities, cut flags, FP32 amplitudes, |M|^2
     bytes_per_event = {str(n): 32 * (n - 2) + 32 * n + n + 1 + 4 * math.factorial(n - 2) + 8 for n in NS}
     for n in NS:
@@ -1015,10 +1254,8 @@ def run_paper(args) -> None:
                                              "recursion": round(kernel_ms[n][1], 3),
                                              "colour_sum": round(kernel_ms[n][2], 3)} for n in NS},
             "device_bytes_per_event": bytes_per_event,
-            "roofline": {"kernel": f"colour-ordered recursion n={n_dom}", "bound": "alu", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "flops_model": "canonical recursion FLOPs x events",
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
+            "roofline": roofline(f"colour-ordered recursion n={n_dom}", "alu", achieved, peak, "TFLOP/s",
+                                 fp32_peak_source(sms), flops_model="canonical recursion FLOPs x events"),
             "e2e": {"value": world * len(NS) * BATCH * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(NS) * BATCH * 8},
             "gpu_launches": 4 * len(NS) * args.steps, "clocks": clk}), flush=True)
@@ -1215,6 +1452,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload only: skip the FP64 form and the other workloads in the line")
     ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc", "paper"), default="co")
     ap.add_argument("--precision", choices=("f32", "f64"), default="f32",
                     help="recursion arithmetic of the co and cd workloads (f64: the plain FP64 GPU form)")

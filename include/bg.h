@@ -248,11 +248,13 @@ bg_status bg_me2_batch_async(bg_plan* plan, int64_t B, const double* u, const in
  * with the limit in bg_last_error().  The call allocates nothing.  Its first
  * call on each device looks up the array's device address with the runtime
  * (that device must be current); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
- * (different streams or threads without ordering between them) race on it
- * and give wrong results.  Nothing in the array needs to start at zero: a
- * call writes every byte it reads.  Invalid helicity labels are not
- * reported in the device status word by this entry point.
+ * capture (a first call made during capture returns BG_EINVAL and says so).
+ * All calls share the one array: calls that overlap on the GPU (different
+ * streams or threads without ordering between them) race on it and give
+ * wrong results.  Nothing in the array needs to start at zero: a call writes
+ * every byte it reads.  As for the other entry points, an invalid helicity
+ * label or a tensor-core wait that gave up is recorded in the device status
+ * word (bg_device_status); in that case me2 is not valid.
  * Errors: BG_EINVAL, BG_EUNSUPPORTED, BG_ECUDA.
  * ------------------------------------------------------------------------- */
 bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, double pt_min, double g_s,
@@ -263,7 +265,8 @@ bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, d
  * bg_me2_grad -- |M|^2 and its gradient with respect to the 4(n-2) Rambo
  * uniforms of each event, d|M|^2/du, by reverse mode through the colour sum
  * (Eq. 2.16: d|M|^2/dA = 2 scale C A), the colour-ordered recursion (Eqs.
- * 2.20-2.22, one ordering per thread, adjoint currents in shared memory),
+ * 2.20-2.22, one ordering per thread, currents and their adjoints in
+ * registers),
  * the light-cone polarisations (Eq. 2.7) and Rambo (forward-mode Jacobian,
  * FP64).  The paper computes no gradients; this serves gradient-trained
  * phase-space mappings.
@@ -280,13 +283,6 @@ bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, double sqrt_s, d
  * ------------------------------------------------------------------------- */
 bg_status bg_me2_grad(bg_plan* plan, int64_t B, const double* u, const int8_t* hel, const double* upstream,
                       double* me2, double* grad_u, void* stream);
-
-/* Measurement utility (no counterpart in the paper): a kernel of
- * independent fused multiply-adds in FP32 (prec = BG_F32) or FP64, on
- * `blocks` blocks of 256 threads, `iters` iterations of 16 FMAs per thread.
- * *flops receives the number of floating-point operations it performs
- * (2 per FMA); time it with events on `stream` to measure the pipe peak. */
-bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream);
 
 /* ---------------------------------------------------------------------------
  * bg_currents_cd -- colour-dressed Berends-Giele recursion with sampled

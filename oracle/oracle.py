@@ -255,7 +255,33 @@ def colour_row(n: int) -> np.ndarray:
 
 def relabel_index(n: int) -> np.ndarray:
     """R[s, t] = index of the relative ordering rho = sigma_s^-1 o sigma_t,
-    rho_j = position in sigma_s of the label sigma_t[j]."""
+    rho_j = position in sigma_s of the label sigma_t[j].
+
+    The index of rho is looked up in a table addressed by the digits of rho
+    in base m+1 (m = n-2), filled from the list of orderings itself, so the
+    lookup needs no ranking formula; rows are done in blocks with numpy
+    (5040 x 5040 at n = 9 in seconds)."""
+    ords = orderings(n).astype(np.int64)          # [k, m], labels 1..m
+    kk, m = ords.shape
+    base = m + 1
+    weights = base ** np.arange(m - 1, -1, -1, dtype=np.int64)
+    table = np.full(base ** m, -1, dtype=np.int64)
+    table[ords @ weights] = np.arange(kk)
+    pos = np.zeros((kk, base), dtype=np.int64)    # pos[s, label] = position (1..m) in sigma_s
+    pos[np.arange(kk)[:, None], ords] = np.arange(1, m + 1)[None, :]
+    R = np.empty((kk, kk), dtype=np.int64)
+    block = max(1, (1 << 22) // (kk * m))
+    for s0 in range(0, kk, block):
+        s1 = min(kk, s0 + block)
+        rho = pos[s0:s1][:, ords]                 # [blk, k, m]: rho[s, t, j] = pos_s[sigma_t[j]]
+        R[s0:s1] = table[rho @ weights]
+    assert R.min() >= 0
+    return R
+
+
+def relabel_index_loop(n: int) -> np.ndarray:
+    """relabel_index written as the plain double loop over (s, t) with a
+    dictionary lookup (slow; kept as the definition it is checked against)."""
     ords = orderings(n)
     kk = ords.shape[0]
     m = n - 2

@@ -80,7 +80,6 @@ def lib() -> ctypes.CDLL:
         L.bg_me2_batch.argtypes = [vp, c_i64, vp, vp, vp, vp, vp]
         L.bg_me2_batch_async.argtypes = [vp, c_i64, vp, vp, vp, vp]
         L.bg_me2_grad.argtypes = [vp, c_i64, vp, vp, vp, vp, vp, vp]
-        L.bg_probe_fma.argtypes = [c_int, c_int, c_int, dp, vp]
         L.bg_cd_workspace_bytes.argtypes = [c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_apply_cuts.argtypes = [c_int, c_i64, vp, c_dbl, c_dbl, c_dbl, vp, vp]
@@ -474,12 +473,6 @@ def _vptr(x):
         assert x.is_contiguous()
         return ctypes.c_void_p(x.data_ptr())
     return ctypes.c_void_p(x.ctypes.data)  # numpy array (host memory)
-
-
-def probe_fma(prec: int, blocks: int, iters: int, stream=None) -> float:
-    flops = ctypes.c_double(0.0)
-    _check(lib().bg_probe_fma(prec, blocks, iters, ctypes.byref(flops), _stream(stream)))
-    return flops.value
 
 
 def tune_num_variants(algo: int, n: int) -> int:

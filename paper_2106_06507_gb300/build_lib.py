@@ -1,5 +1,7 @@
 """Build libbg.so in-tree for sm_103a (nvcc; translation units compiled in
-parallel, then linked).  Output: paper_2106_06507_gb300/_build/libbg.so.
+parallel, then linked).  Output: paper_2106_06507_gb300/_build/libbg.so, and
+beside it libbg_probe.so, the FMA-throughput probe the benchmark uses to
+measure the pipe peaks (include/bg_probe.h; not part of libbg.so).
 
     python -m paper_2106_06507_gb300.build_lib [--verbose-ptxas]
 """
@@ -15,10 +17,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbg.so")
+PROBE_LIB = os.path.join(BUILD, "libbg_probe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC] + ARCH
+
+PROBE_SOURCE = "probe.cu"
 
 SOURCES = [
     "api.cu",
@@ -30,7 +35,6 @@ SOURCES = [
     "cd_f32.cu",
     "cd_f64.cu",
     "colormat.cpp",
-    "probe.cu",
     "noalloc.cu",
     "co_grad.cu",
     "grad_rambo.cu",
@@ -60,9 +64,9 @@ def _deps() -> list[str]:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
@@ -86,18 +90,24 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
             raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")
         return obj, res.stderr
 
-    jobs = jobs or min(len(SOURCES), os.cpu_count() or 4)
+    srcs = SOURCES + [PROBE_SOURCE]
+    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+        results = list(ex.map(compile_one, srcs))
     if verbose_ptxas:
-        for src, (_, log) in zip(SOURCES, results):
+        for src, (_, log) in zip(srcs, results):
             sys.stdout.write(f"==== {src}\n{log}")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [tool] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", tmp] + [o for o, _ in results]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
+
+    def link(out: str, objs: list[str]) -> None:
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [tool] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", tmp] + objs
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+        os.replace(tmp, out)
+
+    link(LIB, [o for o, _ in results[:-1]])
+    link(PROBE_LIB, [results[-1][0]])
     return LIB
 
 

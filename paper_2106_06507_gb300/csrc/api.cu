@@ -2,6 +2,7 @@
 // argument checking, colour-matrix objects and kernel launches on the
 // caller's stream.  No entry point allocates except the create calls.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -47,6 +48,29 @@ int* device_status_ptr() {
 
 static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
 
+// Allocation counting for BG_FAIL_ALLOC (see bg_internal.h).
+static thread_local int t_alloc_depth = 0;
+static thread_local int t_alloc_count = 0;
+
+AllocScope::AllocScope() {
+  if (t_alloc_depth++ == 0) t_alloc_count = 0;
+}
+AllocScope::~AllocScope() { --t_alloc_depth; }
+
+cudaError_t device_alloc(void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  ++t_alloc_count;
+  const char* inject = std::getenv("BG_FAIL_ALLOC");
+  if (inject && std::atoi(inject) == t_alloc_count) return cudaErrorMemoryAllocation;
+  return cudaMalloc(ptr, bytes);
+}
+
+bg_status alloc_failure(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a non-sticky error
+  if (e == cudaErrorMemoryAllocation) return fail(BG_ENOMEM, std::string(what) + ": device allocation failed");
+  return fail(BG_ECUDA, std::string(what) + ": device allocation failed: " + cudaGetErrorString(e));
+}
+
 }  // namespace bg
 
 using namespace bg;
@@ -85,6 +109,7 @@ bg_status bg_colormat_row_host(int n, double* row) {
 }
 
 bg_status bg_colormat_create(int n, bg_colormat** out) {
+  AllocScope scope;
   if (!out) return fail(BG_EINVAL, "bg_colormat_create: out is NULL");
   *out = nullptr;
   if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_colormat_create: n must be in 4..12");
@@ -107,11 +132,11 @@ bg_status bg_colormat_create(int n, bg_colormat** out) {
   std::vector<float> dense32(dense.size());
   for (size_t i = 0; i < dense.size(); ++i) dense32[i] = (float)dense[i];
   const size_t kk = (size_t)C->k * C->k;
-  if (cudaMalloc(&C->C64, kk * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&C->C32, kk * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
+  cudaError_t ae = device_alloc((void**)&C->C64, kk * sizeof(double));
+  if (ae == cudaSuccess) ae = device_alloc((void**)&C->C32, kk * sizeof(float));
+  if (ae != cudaSuccess) {
     bg_colormat_destroy(C);
-    return fail(BG_ENOMEM, "bg_colormat_create: device allocation failed");
+    return alloc_failure(ae, "bg_colormat_create");
   }
   bg_status st = cuda_check(cudaMemcpy(C->C64, dense.data(), kk * sizeof(double), cudaMemcpyHostToDevice),
                             "bg_colormat_create: upload");
@@ -124,10 +149,10 @@ bg_status bg_colormat_create(int n, bg_colormat** out) {
   }
   std::vector<uint16_t> tiles;
   if (build_tc_tiles(n, dense, C->k, tiles, C->tc_g, C->tc_nt, C->tc_ntiles, C->tc_kchunks, C->tc_cpl)) {
-    if (cudaMalloc(&C->tc_tiles_raw, tiles.size() * 2) != cudaSuccess) {
-      cudaGetLastError();
+    ae = device_alloc((void**)&C->tc_tiles_raw, tiles.size() * 2);
+    if (ae != cudaSuccess) {
       bg_colormat_destroy(C);
-      return fail(BG_ENOMEM, "bg_colormat_create: device allocation failed");
+      return alloc_failure(ae, "bg_colormat_create");
     }
     st = cuda_check(cudaMemcpy(C->tc_tiles_raw, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice),
                     "bg_colormat_create: upload");
@@ -335,13 +360,6 @@ bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, co
   return cuda_check(e, "bg_currents_co_mc");
 }
 
-bg_status bg_probe_fma(bg_prec prec, int blocks, int iters, double* flops, void* stream) {
-  if (blocks < 1 || iters < 1 || !flops) return fail(BG_EINVAL, "bg_probe_fma: invalid arguments");
-  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_probe_fma: invalid precision");
-  *flops = 2.0 * 16.0 * 256.0 * (double)blocks * (double)iters;
-  return cuda_check(launch_probe_fma(prec == BG_F32, blocks, iters, (cudaStream_t)stream), "bg_probe_fma");
-}
-
 // ---------------------------------------------------------------------------
 // plans
 // ---------------------------------------------------------------------------
@@ -366,6 +384,7 @@ void bg_plan_destroy(bg_plan* P) {
 int64_t bg_plan_workspace_bytes(const bg_plan* P) { return P ? P->bytes : 0; }
 
 bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
+  AllocScope scope;
   if (!d || !out) return fail(BG_EINVAL, "bg_plan_create: NULL argument");
   *out = nullptr;
   const int n = d->n;
@@ -415,10 +434,10 @@ bg_status bg_plan_create(const bg_plan_desc* d, bg_plan** out) {
   P->bytes = (int64_t)P->C->k * P->C->k * 12;
   for (auto& r : reqs) {
     if (r.bytes == 0) continue;
-    if (cudaMalloc(r.ptr, r.bytes) != cudaSuccess) {
-      cudaGetLastError();
+    cudaError_t ae = device_alloc(r.ptr, r.bytes);
+    if (ae != cudaSuccess) {
       bg_plan_destroy(P);
-      return fail(BG_ENOMEM, "bg_plan_create: device allocation failed");
+      return alloc_failure(ae, "bg_plan_create");
     }
     P->bytes += (int64_t)r.bytes;
   }

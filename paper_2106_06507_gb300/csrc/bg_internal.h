@@ -30,6 +30,21 @@ int64_t perm_rank(const int* perm, int m);
 // Dense matrix from the row: C[s][t] = row[rank(sigma_s^-1 o sigma_t)].
 void colour_dense(int n, const std::vector<double>& row, std::vector<double>& dense);
 
+// Device allocation of the create calls (api.cu).  It returns
+// cudaErrorMemoryAllocation without allocating when the environment variable
+// BG_FAIL_ALLOC=k is set and this is the k-th allocation of the current
+// top-level create call (counted from 1 across nested creates): a host-side
+// hook that lets the tests reach every BG_ENOMEM path.  AllocScope marks a
+// create call; nested scopes share the outer count.
+cudaError_t device_alloc(void** ptr, size_t bytes);
+struct AllocScope {
+  AllocScope();
+  ~AllocScope();
+};
+// BG_ENOMEM for an out-of-memory error, BG_ECUDA with the runtime's message
+// for any other failed allocation (no device, an earlier sticky error).
+bg_status alloc_failure(cudaError_t e, const char* what);
+
 // Device status word and SM count of the current device (api.cu; 0 if
 // there is no device).
 int* device_status_ptr();
@@ -71,7 +86,6 @@ struct ColourSumArgs {
   const int64_t* dB = nullptr;  // optional device-side event count (<= B)
 };
 cudaError_t launch_color_sum_f64(const ColourSumArgs& a, cudaStream_t s);
-cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s);
 
 // Colour-dressed recursion (cd_f32.cu, cd_f64.cu): workspace bytes and
 // launchers; CdParams is defined in cd_recursion.cuh.

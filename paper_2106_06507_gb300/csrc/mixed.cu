@@ -154,10 +154,10 @@ namespace {
 bg_status mixed_alloc(bg_mixed* P, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) return BG_OK;
-  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
-    cudaGetLastError();
+  cudaError_t e = device_alloc(ptr, bytes);
+  if (e != cudaSuccess) {
     *ptr = nullptr;
-    return fail(BG_ENOMEM, "bg_mixed_create: device allocation failed");
+    return alloc_failure(e, "bg_mixed_create");
   }
   P->allocs.push_back(*ptr);
   P->bytes += (int64_t)bytes;
@@ -259,6 +259,7 @@ void bg_mixed_destroy(bg_mixed* P) {
 }
 
 bg_status bg_mixed_create(const bg_mixed_desc* d, bg_mixed** out) {
+  AllocScope scope;
   if (!d || !out) return fail(BG_EINVAL, "bg_mixed_create: NULL argument");
   *out = nullptr;
   if (d->n_min < 4 || d->n_max > kMaxN || d->n_min > d->n_max)

@@ -29,18 +29,29 @@ unsigned char* g_noalloc_ptr[kMaxDevices];  // zero-initialised: not set up yet
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device (set up once).
-bg_status noalloc_scratch(unsigned char** out) {
+// Device address of the scratch array on the current device (set up once,
+// together with the device status word's address).
+bg_status noalloc_scratch(cudaStream_t s, unsigned char** out) {
   int dev = 0;
   bg_status st = cuda_check(cudaGetDevice(&dev), "bg_me2_batch_noalloc: cudaGetDevice");
   if (st != BG_OK) return st;
   if (dev < 0 || dev >= kMaxDevices) return fail(BG_EUNSUPPORTED, "bg_me2_batch_noalloc: device index >= 64");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
+    // The first call on a device must not be captured into a graph: the
+    // symbol lookup (and the status-word lookup below) are runtime calls.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+      return fail(BG_EINVAL,
+                  "bg_me2_batch_noalloc: the first call on a device sets up the scratch address and must not run "
+                  "during stream capture; make one call on this device (current) before capturing");
     void* ptr = nullptr;
     st = cuda_check(cudaGetSymbolAddress(&ptr, g_noalloc_scratch),
-                    "bg_me2_batch_noalloc: cudaGetSymbolAddress of the scratch array");
+                    "bg_me2_batch_noalloc: cudaGetSymbolAddress of the scratch array (first call on this device; "
+                    "the device must be current and no stream capture active)");
     if (st != BG_OK) return st;
+    if (!device_status_ptr())
+      return fail(BG_ECUDA, "bg_me2_batch_noalloc: cannot look up the device status word on this device");
     g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
   }
   *out = g_noalloc_ptr[dev];
@@ -84,8 +95,9 @@ extern "C" bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, doubl
   }
   if (B == 0) return BG_OK;
   if (!u || !me2) return fail(BG_EINVAL, "bg_me2_batch_noalloc: NULL u or me2");
+  cudaStream_t s = (cudaStream_t)stream;
   unsigned char* scratch = nullptr;
-  bg_status st = noalloc_scratch(&scratch);
+  bg_status st = noalloc_scratch(s, &scratch);
   if (st != BG_OK) return st;
   double* p = reinterpret_cast<double*>(scratch);
   void* amps = scratch + align256(4 * (size_t)n * 8 * B);
@@ -93,13 +105,14 @@ extern "C" bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, doubl
                                                align256((size_t)B * H * C->k * amp_size));
   // Every scratch byte read below is written earlier in this same call, so
   // nothing has to start at zero and leftovers of an earlier call are harmless.
-  // The kernels are launched directly (no device status word: invalid
-  // helicity labels are not reported by this entry point).
-  cudaStream_t s = (cudaStream_t)stream;
+  // The device status word (a fixed library symbol, no allocation) receives
+  // invalid helicity labels and a timed-out tensor-core wait, as for the
+  // other entry points.
+  int* status = device_status_ptr();
   st = cuda_check(launch_rambo(n, B, sqrt_s, u, p, pt_min, accept, s), "bg_me2_batch_noalloc: Rambo");
   if (st != BG_OK) return st;
-  st = cuda_check(prec == BG_F32 ? launch_co_f32(n, B, sqrt_s, p, hel, q, static_cast<float*>(amps), nullptr, s)
-                                 : launch_co_f64(n, B, sqrt_s, p, hel, q, static_cast<double*>(amps), nullptr, s),
+  st = cuda_check(prec == BG_F32 ? launch_co_f32(n, B, sqrt_s, p, hel, q, static_cast<float*>(amps), status, s)
+                                 : launch_co_f64(n, B, sqrt_s, p, hel, q, static_cast<double*>(amps), status, s),
                   "bg_me2_batch_noalloc: recursion");
   if (st != BG_OK) return st;
   ColourSumArgs a;
@@ -116,6 +129,6 @@ extern "C" bg_status bg_me2_batch_noalloc(const bg_colormat* C, int64_t B, doubl
   a.me2 = me2;
   cudaError_t e = (cs_mode == BG_CS_F64)   ? launch_color_sum_f64(a, s)
                   : (cs_mode == BG_CS_F32) ? launch_color_sum_f32(a, s)
-                                           : launch_color_sum_tc(a, C, nullptr, s);
+                                           : launch_color_sum_tc(a, C, status, s);
   return cuda_check(e, "bg_me2_batch_noalloc: colour sum");
 }

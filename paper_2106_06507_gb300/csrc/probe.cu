@@ -1,8 +1,10 @@
-// probe.cu -- FMA throughput probe used to measure the FP32 / FP64 pipe
-// peaks of the device (a measurement utility, not part of the method).
-#include "bg_internal.h"
+// probe.cu -- libbg_probe.so: an FMA throughput probe used by the benchmark
+// to measure the FP32 / FP64 pipe peaks of the device.  A measurement
+// utility, not part of the method, kept out of libbg.so (include/bg_probe.h).
+#include <cuda_runtime.h>
 
-namespace bg {
+#include "../../include/bg_probe.h"
+
 namespace {
 
 __device__ double g_probe_sink;
@@ -25,12 +27,13 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T seed) {
 
 }  // namespace
 
-cudaError_t launch_probe_fma(bool f32, int blocks, int iters, cudaStream_t s) {
+extern "C" int bgprobe_fma(int f32, int blocks, int iters, double* flops, void* stream) {
+  if (blocks < 1 || iters < 1 || !flops) return 1;
+  *flops = 2.0 * 16.0 * 256.0 * (double)blocks * (double)iters;
+  cudaStream_t s = (cudaStream_t)stream;
   if (f32)
     fma_probe_kernel<float><<<blocks, 256, 0, s>>>(iters, 1.0f);
   else
     fma_probe_kernel<double><<<blocks, 256, 0, s>>>(iters, 1.0);
-  return cudaGetLastError();
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
-
-}  // namespace bg

@@ -111,7 +111,7 @@ struct ProbeBuffers {
   template <typename P>
   bool alloc(P** out, size_t bytes) {
     void* v = nullptr;
-    if (cudaMalloc(&v, bytes) != cudaSuccess) {
+    if (device_alloc(&v, bytes) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -157,6 +157,7 @@ bg_status bg_tune_get(bg_algo algo, int n, bg_prec prec, int* variant) {
 
 bg_status bg_autotune(bg_algo algo, int n, bg_prec prec, int64_t probe_batch, void* stream, int* best,
                       float* ms) {
+  AllocScope scope;
   bg_status st = check_args("bg_autotune", algo, n, prec);
   if (st != BG_OK) return st;
   const int fam = family_of(algo);

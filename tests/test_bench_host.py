@@ -1,5 +1,6 @@
 """Host logic of bench.py on CPU: the max-over-ranks timing reduction with a
-world_size-2 gloo group, and the per-n rate aggregation."""
+world_size-2 gloo group, the ncu-figure and roofline helpers, the flop and
+colour-flow order counts, and the reference arm's JSON line."""
 import os
 import sys
 
@@ -42,14 +43,25 @@ def test_max_over_ranks_gloo_world2():
     assert res == {0: 2.5, 1: 2.5}
 
 
-def test_aggregate_rate():
+def test_ncu_figures_line(tmp_path):
+    # the bench reads the dominant kernel's ncu figures from the summary's
+    # "bench-figures:" line, and uses them only for the sources they name
     sys.path.insert(0, ROOT)
     import bench
-    rates = {n: 1.0e6 for n in bench.NS}
-    assert bench.aggregate_rate(rates, batch=1000) == pytest.approx(1.0e6)
-    rates = {5: 4.0, 6: 4.0, 7: 2.0, 8: 1.0}
-    # 4 batches of 4 events take 1 + 1 + 2 + 4 = 8 s
-    assert bench.aggregate_rate(rates, batch=4) == pytest.approx(16 / 8)
+    f = tmp_path / "summary.md"
+    f.write_text("# x\n\nbench-figures: sources_sha1=abc executed_flops_per_event=123.5 "
+                 "dram_bytes_per_event=2880\n")
+    assert bench.ncu_figures(str(f)) == {"sources_sha1": "abc", "executed_flops_per_event": 123.5,
+                                         "dram_bytes_per_event": 2880.0}
+    assert bench.ncu_figures(str(tmp_path / "missing.md")) is None
+
+
+def test_roofline_helper():
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.roofline("k", "alu", 40.0, 80.0, "TFLOP/s", "src", traffic=5, extra=1)
+    assert r["frac"] == 0.5 and r["traffic"] == 5 and r["extra"] == 1 and r["bound"] == "alu"
+    assert bench.fp32_peak_tflops(152) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
 
 
 def test_canonical_flop_model():
@@ -88,7 +100,7 @@ def test_reference_arm_json_contract(monkeypatch, capsys):
     import types
     sys.path.insert(0, ROOT)
     import bench
-    monkeypatch.setattr(bench, "REF_STEP_SAMPLE", {5: 16, 6: 8, 7: 4, 8: 2})
+    monkeypatch.setattr(bench, "REF_STEP_PER_N", 4)
     monkeypatch.delenv("WORLD_SIZE", raising=False)
     monkeypatch.delenv("RANK", raising=False)
     bench.run_reference(types.SimpleNamespace(gpus=1, steps=2, warmup=0))
@@ -99,3 +111,8 @@ def test_reference_arm_json_contract(monkeypatch, capsys):
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "events/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+    # the step time is the time actually spent: events per step / rate
+    assert line["ms_per_step"] == pytest.approx(1e3 * 16 / line["value"])
+    # the same workload keys as the GPU arm's line
+    for k, v in bench.ref_arm_config().items():
+        assert line["config"][k] == v

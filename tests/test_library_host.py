@@ -19,27 +19,34 @@ def libbg():
     return ctypes.CDLL(path)
 
 
-def declared_symbols():
-    names = set()
-    for fn in os.listdir(os.path.join(ROOT, "include")):
-        if not fn.endswith(".h"):
-            continue
-        text = open(os.path.join(ROOT, "include", fn)).read()
-        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(bg_[a-z0-9_]+)\s*\(", text):
-            names.add(m.group(1))
-    return sorted(names)
+def declared_symbols(header: str = "bg.h"):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted({m.group(1) for m in re.finditer(r"\b(bg[a-z0-9_]*_[a-z0-9_]+)\s*\(", text)})
 
 
 def test_header_declares_the_boundary():
     names = declared_symbols()
-    for required in ("bg_momenta_rambo", "bg_currents_co", "bg_color_sum", "bg_colormat_create"):
+    for required in ("bg_momenta_rambo", "bg_currents_co", "bg_color_sum", "bg_colormat_create", "bg_currents_cd",
+                     "bg_me2_batch", "bg_me2_grad"):
         assert required in names
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["bg.h", "bg_probe.h"]
 
 
 def test_library_exports_every_declared_symbol(libbg):
     missing = [n for n in declared_symbols() if not hasattr(libbg, n)]
     assert not missing, missing
+
+
+def test_probe_library_is_separate(libbg):
+    # the FMA probe is a measurement utility in its own library, not part of
+    # the product ABI
+    from paper_2106_06507_gb300 import build_lib
+    probe = ctypes.CDLL(build_lib.PROBE_LIB)
+    names = declared_symbols("bg_probe.h")
+    assert names == ["bgprobe_fma"]
+    assert all(hasattr(probe, n) for n in names)
+    assert not hasattr(libbg, "bgprobe_fma") and not hasattr(libbg, "bg_probe_fma")
 
 
 def test_num_orderings(libbg):

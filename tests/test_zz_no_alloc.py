@@ -3,8 +3,10 @@ device memory (its intermediate buffers sit in a fixed array of device memory
 inside the library).  Called through the C ABI and compared with the
 allocating entry point bg_me2_batch on the same inputs, for two calls in a
 row, within the FP64 parity tolerance of the other tests (1e-12 relative; the
-two paths run the same kernels, so the results are expected to be equal).
-This file is collected last on purpose."""
+two paths run the same kernels, so the results are expected to be equal); at
+the largest batch the fixed array holds; and with an invalid helicity label,
+which the device status word must report.  This file is collected last on
+purpose."""
 import ctypes
 
 import numpy as np
@@ -67,6 +69,58 @@ def test_noalloc_matches_allocating_entry_point(bg, n, prec_name, cs_name, sampl
         nz = ref != 0
         assert np.all(np.abs(got[nz] / ref[nz] - 1.0) <= 1e-12)
     plan.close()
+    C.close()
+
+
+def noalloc_max_events(n, k, amp_bytes, H):
+    # the library's own sizing rule: momenta [4][n][B] double, amplitudes
+    # [B][H][k], cut flags [B], each region padded to 256 bytes
+    per_event = 4 * n * 8 + H * k * amp_bytes + 1
+    return ((64 << 20) - 3 * 256) // per_event
+
+
+def test_noalloc_at_its_largest_batch(bg):
+    # n = 8, FP32 amplitudes, sampled helicities: the batch that fills the
+    # fixed array (21392 events) matches the plan path; one more is rejected
+    import torch
+    dev = torch.device("cuda:0")
+    n = 8
+    B = noalloc_max_events(n, 720, 4, 1)
+    assert B == 21392
+    C = bg.ColourMatrix(n)
+    plan = bg.Plan(n, B + 1, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_TC_BF16, hel_sampled=True)
+    u = torch.from_numpy(inputs.rambo_uniforms(n, B + 1, seed=62)).to(dev)
+    hel = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B + 1, seed=62).T)).to(dev)
+    ref = plan.me2(u[:B], hel[:, :B].contiguous()).cpu().numpy()
+    out = torch.full((B + 1,), -1.0, dtype=torch.float64, device=dev)
+    hb = hel[:, :B].contiguous()
+    assert noalloc(bg, C, B, u, hb, out, bg.BG_F32, bg.BG_CS_TC_BF16, PT_MIN) == bg.BG_OK
+    got = out[:B].cpu().numpy()
+    assert out[B].item() == -1.0  # nothing written past the batch
+    assert np.array_equal(got == 0, ref == 0)
+    nz = ref != 0
+    assert np.all(np.abs(got[nz] / ref[nz] - 1.0) <= 1e-12)
+    assert noalloc(bg, C, B + 1, u, hel, out, bg.BG_F32, bg.BG_CS_TC_BF16, PT_MIN) == bg.BG_EINVAL
+    assert f"at most {B} events" in bg.lib().bg_last_error().decode()
+    plan.close()
+    C.close()
+
+
+def test_noalloc_reports_invalid_helicity_label(bg):
+    import torch
+    dev = torch.device("cuda:0")
+    n, B = 7, 400
+    C = bg.ColourMatrix(n)
+    u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=63)).to(dev)
+    hel = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=63).T)).to(dev)
+    out = torch.zeros((B,), dtype=torch.float64, device=dev)
+    bg.device_status_reset()
+    assert noalloc(bg, C, B, u, hel, out, bg.BG_F32, bg.BG_CS_TC_BF16, PT_MIN) == bg.BG_OK
+    assert bg.device_status() == 0
+    hel[2, 5] = -2
+    assert noalloc(bg, C, B, u, hel, out, bg.BG_F32, bg.BG_CS_TC_BF16, PT_MIN) == bg.BG_OK
+    assert bg.device_status() == bg.BG_EINVAL
+    bg.device_status_reset()
     C.close()
 
 
