@@ -620,8 +620,9 @@ def side_fp64(bg, inputs, dev, stream, rank, value32, per_n32):
 
 
 def side_cd(bg, inputs, dev, stream, rank, sms):
-    """Colour-dressed recursion with sampled adjoint colours (config 3: n = 8,
-    10, 12, FP32), CD_SIDE_BATCH events per n."""
+    """Colour-dressed recursion with sampled adjoint colours, n = 8, 10, 12,
+    FP32 currents, CD_SIDE_BATCH events per n (the 2^20-event workload at an
+    eighth of its batch)."""
     import numpy as np
     import torch
     B = CD_SIDE_BATCH
@@ -667,7 +668,8 @@ def side_cd(bg, inputs, dev, stream, rank, sms):
 
 
 def side_grad(bg, inputs, dev, stream, rank):
-    """|M|^2 and d|M|^2/du (config 4: n = 6, 8, 2^18 events per n, FP32)."""
+    """|M|^2 and d|M|^2/du with respect to the Rambo uniforms, n = 6, 8, 2^18
+    events per n, FP32 currents with the full colour sum."""
     import numpy as np
     import torch
     B = GRAD_BATCH
@@ -690,8 +692,8 @@ def side_grad(bg, inputs, dev, stream, rank):
 
 
 def side_mixed(bg, inputs, dev, stream, rank):
-    """A mixed batch (config 5 at a tenth of its size): MIXED_SIDE_EVENTS
-    events with n uniform in 4..12, one launch."""
+    """A mixed batch of MIXED_SIDE_EVENTS events with n uniform in 4..12 (the
+    10^7-event mixed workload at a tenth of its size), one launch per step."""
     import numpy as np
     import torch
     B = MIXED_SIDE_EVENTS
