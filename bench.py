@@ -27,7 +27,9 @@ parts of the path with the same timing rules:
   lc     leading-colour |M|^2 (Sec. 4) on the default events, n = 5..8;
   paper  the paper's own setup: sqrt(s) = 14 TeV, pT > 20 GeV, |eta| < 2.5,
          Delta R > 0.4, colour-ordered n = 5..8 (acceptance, recursion /
-         colour-sum time split, device bytes per event).
+         colour-sum time split, device bytes per event);
+  forms  the colour-ordered recursion with the four-gluon vertex against the
+         tensor form (Eqs. 2.23-2.26), n = 6..9, kernel times and FLOP counts.
 
 Prints ONE JSON line on rank 0.  N > 1 runs under torch.distributed.run, one
 process per GPU, each with its own events (weak scaling, no collective on the
@@ -1398,6 +1400,90 @@ def run_mixed(args) -> None:
     finish_gpu(world)
 
 
+FORMS_NS = (6, 7, 8, 9)
+FORMS_BATCH = {6: 1 << 18, 7: 1 << 18, 8: 1 << 18, 9: 1 << 15}
+
+
+def tensor_form_flops(n: int) -> int:
+    """Canonical FLOPs per event of the tensor form of the colour-ordered
+    recursion (all (n-2)! orderings): per split V3 = 65, each tensor
+    contraction T X or Y T = 24 (present unless the tensor belongs to a
+    single gluon), the wedge into the segment's tensor = 24 (not for the full
+    current); propagator = 12, final contraction = 7."""
+    m = n - 1
+    per_order = 7
+    for L in range(2, m + 1):
+        segs = m - L + 1
+        splits = L - 1
+        f = 65 * splits + 24 * 2 * (L - 2)
+        if L < m:
+            f += 24 * splits + 12
+        per_order += segs * f
+    return math.factorial(n - 2) * per_order
+
+
+def run_forms(args) -> None:
+    """Four-vertex form against the tensor form (Eqs. 2.23-2.26) of the
+    colour-ordered recursion, FP32, sampled helicities: kernel time per event
+    of the one-thread-per-ordering kernel with each form, and of the tuned
+    depth-first four-vertex kernel.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2106_06507_gb300 import inputs
+    world, rank, dev, bg = setup_gpu()
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+    for n in FORMS_NS:
+        B = FORMS_BATCH[n]
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
+        p, acc = bg.momenta_rambo(n, u, SQRT_S, PT_MIN)
+        amps = torch.empty((B, 1, math.factorial(n - 2)), dtype=torch.float32, device=dev)
+        tuned = bg.autotune(bg.BG_ALGO_CO, n, bg.BG_F32, probe_batch=min(B, 1 << 16), stream=stream)[0]
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            total = 0.0
+            for _ in range(args.steps):
+                flush_l2(dev)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                total += a.elapsed_time(b)
+            return total / args.steps
+
+        bg.tune_set(bg.BG_ALGO_CO, n, bg.BG_F32, 0)
+        t_v4 = timed(lambda: bg.currents_co(n, p, h, prec=bg.BG_F32, sqrt_s=SQRT_S, amps=amps, stream=stream))
+        ref = amps.clone()
+        bg.tune_set(bg.BG_ALGO_CO, n, bg.BG_F32, tuned)
+        t_dfs = timed(lambda: bg.currents_co(n, p, h, prec=bg.BG_F32, sqrt_s=SQRT_S, amps=amps, stream=stream))
+        t_tf = timed(lambda: bg.currents_co(n, p, h, prec=bg.BG_F32, sqrt_s=SQRT_S, amps=amps, stream=stream,
+                                            tensor_form=True))
+        diff = float(((amps - ref).abs().amax(dim=2) / ref.abs().amax(dim=2).clamp_min(1e-300)).median().item())
+        rows[str(n)] = {"batch": B, "tuned_variant": tuned,
+                        "ms_per_2^20_events": {"four_vertex_one_thread_per_ordering": t_v4 * (1 << 20) / B,
+                                               "four_vertex_depth_first_tuned": t_dfs * (1 << 20) / B,
+                                               "tensor_form_one_thread_per_ordering": t_tf * (1 << 20) / B},
+                        "canonical_flops_per_event": {"four_vertex": canonical_recursion_flops(n),
+                                                      "tensor_form": tensor_form_flops(n)},
+                        "tensor_over_four_vertex_time": t_tf / t_v4,
+                        "median_rel_amplitude_difference": diff}
+    if rank == 0:
+        n8 = rows["8"]["ms_per_2^20_events"]
+        print(json.dumps({
+            "metric": "events/s", "value": (1 << 20) / (n8["tensor_form_one_thread_per_ordering"] * 1e-3),
+            "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": n8["tensor_form_one_thread_per_ordering"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("colour-ordered recursion alone, four-vertex form against the tensor form, FP32, "
+                                    "sampled helicities, pT>20 GeV, n=6..9; value: tensor form at n=8")},
+            "forms": rows, "e2e": None, "gpu_launches": None}), flush=True)
+    finish_gpu(world)
+
+
 def run_profile_case(args) -> None:
     """A small case of one multiplicity for ncu captures: `warmup` steps, then
     one step (Rambo, recursion, colour sum; with --workload cd or comc: Rambo
@@ -1456,7 +1542,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="default workload only: skip the FP64 form and the other workloads in the line")
-    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc", "paper"), default="co")
+    ap.add_argument("--workload", choices=("co", "cd", "grad", "mixed", "comc", "lc", "paper", "forms"), default="co")
     ap.add_argument("--precision", choices=("f32", "f64"), default="f32",
                     help="recursion arithmetic of the co and cd workloads (f64: the plain FP64 GPU form)")
     ap.add_argument("--colour-sampling", choices=("adjoint", "continuous"), default="adjoint",
@@ -1481,6 +1567,8 @@ def main(argv=None):
         run_lc(args)
     elif args.workload == "paper":
         run_paper(args)
+    elif args.workload == "forms":
+        run_forms(args)
     else:
         run_ours(args)
 

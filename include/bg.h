@@ -150,6 +150,21 @@ bg_status bg_currents_co(int n, int64_t B, double sqrt_s, const double* p, const
                          bg_prec prec, void* amps, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * bg_currents_co_tensor -- the colour-ordered currents of bg_currents_co with
+ * the four-gluon vertex replaced by the auxiliary antisymmetric tensor field
+ * of Eqs. (2.23)-(2.26): every segment (i..j) also carries the tensor
+ * current T(i..j) = sum_s J(i..s) ^ J(s+1..j), which enters the brackets of
+ * the longer segments through T(s+1..j) J(i..s) + J(s+1..j) T(i..s).  The
+ * amplitudes equal those of bg_currents_co up to rounding (not bit for bit:
+ * the sums run in another order).  Arguments, layouts and errors as for
+ * bg_currents_co (one thread per ordering; 4 <= n <= 9).  It performs more
+ * arithmetic than the four-vertex form for n <= 9 and is kept for the
+ * comparison of the two forms.
+ * ------------------------------------------------------------------------- */
+bg_status bg_currents_co_tensor(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                                bg_prec prec, void* amps, void* stream);
+
+/* ---------------------------------------------------------------------------
  * bg_color_sum -- |M|^2 = g_s^(2n-4) sqrt_s^(8-2n) w sum_h sum_{s,s'}
  * C_{s s'} A_{h s} A_{h s'}, Eq. (2.16), with w = 2^n if hel_sampled (one
  * sampled polarisation configuration per event, H = 1) else 1.

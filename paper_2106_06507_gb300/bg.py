@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
         L.bg_colormat_row_host.argtypes = [c_int, dp]
         L.bg_momenta_rambo.argtypes = [c_int, c_i64, c_dbl, vp, vp, c_dbl, vp, vp]
         L.bg_currents_co.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, vp, vp]
+        L.bg_currents_co_tensor.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, vp, vp]
         L.bg_color_sum.argtypes = [vp, c_i64, c_int, vp, c_int, c_int, c_dbl, c_dbl, c_int, vp, vp, vp]
         L.bg_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(vp)]
         L.bg_plan_destroy.argtypes = [vp]
@@ -105,8 +106,8 @@ def lib() -> ctypes.CDLL:
         L.bg_device_status.argtypes = [ctypes.POINTER(c_int)]
         L.bg_device_status_reset.argtypes = []
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
-                     "bg_currents_co", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
-                     "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_probe_fma", "bg_cd_workspace_bytes",
+                     "bg_currents_co", "bg_currents_co_tensor", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
+                     "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_cd_workspace_bytes",
                      "bg_currents_cd", "bg_currents_cd_cont", "bg_apply_cuts", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
                      "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
                      "bg_tune_load"):
@@ -201,9 +202,10 @@ def apply_cuts(n: int, p: torch.Tensor, pt_min: float = 20.0, eta_max: float = 2
 
 
 def currents_co(n: int, p: torch.Tensor, hel: torch.Tensor | None = None, q=DEFAULT_Q, prec: int = BG_F32,
-                sqrt_s: float = 1000.0, amps=None, stream=None) -> torch.Tensor:
+                sqrt_s: float = 1000.0, amps=None, stream=None, tensor_form: bool = False) -> torch.Tensor:
     """p [4, n, B] float64, hel [n, B] int8 or None (all 2^n configurations)
-    -> amps [B, H, (n-2)!] (float32 or float64)."""
+    -> amps [B, H, (n-2)!] (float32 or float64).  tensor_form: the auxiliary
+    tensor field in place of the four-gluon vertex (bg_currents_co_tensor)."""
     B = p.shape[2]
     H = 1 if hel is not None else 2**n
     k = num_orderings(n)
@@ -212,7 +214,8 @@ def currents_co(n: int, p: torch.Tensor, hel: torch.Tensor | None = None, q=DEFA
         amps = torch.empty((B, H, k), dtype=dt, device=p.device)
     if hel is not None:
         assert hel.dtype == torch.int8 and hel.is_contiguous() and tuple(hel.shape) == (n, B)
-    _check(lib().bg_currents_co(n, B, sqrt_s, _ptr(p), _ptr(hel), _q(q), prec, _ptr(amps), _stream(stream)))
+    fn = lib().bg_currents_co_tensor if tensor_form else lib().bg_currents_co
+    _check(fn(n, B, sqrt_s, _ptr(p), _ptr(hel), _q(q), prec, _ptr(amps), _stream(stream)))
     return amps
 
 

@@ -30,6 +30,7 @@ SOURCES = [
     "rambo.cu",
     "co_f32.cu",
     "co_f64.cu",
+    "co_tensor.cu",
     "color_sum.cu",
     "color_sum_tc.cu",
     "cd_f32.cu",

@@ -214,6 +214,29 @@ bg_status bg_currents_co(int n, int64_t B, double sqrt_s, const double* p, const
   return cuda_check(e, "bg_currents_co");
 }
 
+bg_status bg_currents_co_tensor(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                                bg_prec prec, void* amps, void* stream) {
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_currents_co_tensor: n must be in 4..12");
+  if (n > kMaxNCO) return fail(BG_EUNSUPPORTED, "bg_currents_co_tensor: colour-ordered path supports n <= 9");
+  if (B < 0) return fail(BG_EINVAL, "bg_currents_co_tensor: B < 0");
+  if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_currents_co_tensor: sqrt_s must be > 0");
+  if (!q) return fail(BG_EINVAL, "bg_currents_co_tensor: q is NULL");
+  const double qv = std::sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(q[0] > 0.0) || std::fabs(q[0] - qv) > 1e-12 * q[0])
+    return fail(BG_EINVAL, "bg_currents_co_tensor: q must be light-like with q0 > 0");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_currents_co_tensor: invalid precision");
+  if (B == 0) return BG_OK;
+  if (!p || !amps) return fail(BG_EINVAL, "bg_currents_co_tensor: NULL p or amps");
+  if (!aligned(p, 8) || !aligned(amps, prec == BG_F32 ? 4 : 8))
+    return fail(BG_EINVAL, "bg_currents_co_tensor: misaligned p or amps");
+  int* status = device_status_ptr();
+  cudaError_t e = (prec == BG_F32) ? launch_co_tensor_f32(n, B, sqrt_s, p, hel, q, static_cast<float*>(amps), status,
+                                                          (cudaStream_t)stream)
+                                   : launch_co_tensor_f64(n, B, sqrt_s, p, hel, q, static_cast<double*>(amps),
+                                                          status, (cudaStream_t)stream);
+  return cuda_check(e, "bg_currents_co_tensor");
+}
+
 bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps, bg_prec amp_prec,
                        bg_cs_mode mode, double g_s, double sqrt_s, int hel_sampled, const uint8_t* accept,
                        double* me2, void* stream) {

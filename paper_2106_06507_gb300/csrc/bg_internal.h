@@ -64,6 +64,12 @@ cudaError_t launch_co_f32(int n, int64_t B, double sqrt_s, const double* p, cons
 cudaError_t launch_co_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
                           double* amps, int* status, cudaStream_t s, const int64_t* dB = nullptr, int variant = -1);
 int co_variants(int n, bool helicity_sum);  // number of recursion variants
+// The same currents with the auxiliary tensor field in place of the
+// four-gluon vertex (co_tensor.cu).
+cudaError_t launch_co_tensor_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
+                                 const double* q, float* amps, int* status, cudaStream_t s);
+cudaError_t launch_co_tensor_f64(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
+                                 const double* q, double* amps, int* status, cudaStream_t s);
 
 // Autotuner table (tune.cu): the chosen variant of a kernel family for
 // (n, precision) on the current device, or -1 (default).

@@ -65,25 +65,6 @@ __constant__ double c_adj_colour[8][3][3] = {
     {{0, 0, 0}, {0, 0, -0.70710678118654752440}, {0, 0.70710678118654752440, 0}},
     {{0.40824829046386301637, 0, 0}, {0, 0.40824829046386301637, 0}, {0, 0, -0.81649658092772603273}}};
 
-// (T X)^nu = T^{nu b} X_b and (Y T)^nu = Y_a T^{a nu} for an antisymmetric
-// tensor stored as its 6 upper components t01 t02 t03 t12 t13 t23.
-template <typename T>
-__device__ __forceinline__ void ten_vec_acc(const T* t, const T* X, T* acc) {
-  // X_b = g_bb X^b: X_0 = X0, X_i = -Xi
-  acc[0] += -t[0] * X[1] - t[1] * X[2] - t[2] * X[3];
-  acc[1] += -t[0] * X[0] - t[3] * X[2] - t[4] * X[3];
-  acc[2] += -t[1] * X[0] + t[3] * X[1] - t[5] * X[3];
-  acc[3] += -t[2] * X[0] + t[4] * X[1] + t[5] * X[2];
-}
-template <typename T>
-__device__ __forceinline__ void vec_ten_acc(const T* Y, const T* t, T* acc) {
-  // (Y T)^nu = Y_a T^{a nu} = -(T Y)^nu for antisymmetric T
-  acc[0] -= -t[0] * Y[1] - t[1] * Y[2] - t[2] * Y[3];
-  acc[1] -= -t[0] * Y[0] - t[3] * Y[2] - t[4] * Y[3];
-  acc[2] -= -t[1] * Y[0] + t[3] * Y[1] - t[5] * Y[3];
-  acc[3] -= -t[2] * Y[0] + t[4] * Y[1] + t[5] * Y[2];
-}
-
 // j-th submask (1-based, increasing order) of S: deposit the bits of j into
 // the set positions of S.
 __device__ __forceinline__ int submask_at(int S, int j) {

@@ -304,7 +304,94 @@ __device__ __forceinline__ T co_recursion(T (&J)[N - 1][N - 1][4], const T (&Sp)
   return amp;
 }
 
-template <int N, typename T, bool SUMHEL>
+// Tensor form of the bracket (Eqs. 2.23-2.26): the four-gluon vertex is
+// replaced by the auxiliary antisymmetric tensor field.  With unit vertex
+// factors (the paper's 1/sqrt2 at the creation and at the absorption of the
+// tensor combine to the 1/2 of the four-vertex, collected with the other
+// couplings at the end):
+//   T(i..j)  = sum_s J(i..s) ^ J(s+1..j),
+//   br(i..j) = sum_s [ V3 terms + T(s+1..j) J(i..s) + J(s+1..j) T(i..s) ],
+// with (T X)^nu = T^{nu b} X_b and (Y T)^nu = Y_a T^{a nu}; single gluons
+// carry no tensor.  The V3 terms are those of co_bracket.  TT holds the
+// tensors of the shorter segments (6 upper components each); the tensor of
+// (i..j) is formed only if `need_t` (not for the full current).
+template <int N, typename T>
+__device__ __forceinline__ void co_bracket_tf(const T (&J)[N - 1][N - 1][4], const T (&TT)[N - 1][N - 1][6],
+                                              const T (&Sp)[N][4], const int i, const int j, const bool need_t,
+                                              T (&br)[4], T (&tt)[6]) {
+  constexpr int M = N - 1;
+  T P2[4];
+  sub4(Sp[j + 1], Sp[i], P2);
+  scale4(T(2), P2, P2);
+  T W[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) { br[m] = T(0); W[m] = T(0); }
+#pragma unroll
+  for (int m = 0; m < 6; ++m) tt[m] = T(0);
+  T sxy = T(0);
+  T cX[M], cR[M];
+#pragma unroll
+  for (int s = i; s < j; ++s) {
+    const T xy = mdot(J[i][s], J[s + 1][j]);
+    const T px = mdot(P2, J[i][s]);
+    const T py = mdot(P2, J[s + 1][j]);
+    sxy += xy;
+    axpy4(xy, Sp[s + 1], W);
+    cX[s] = -py;
+    cR[s] = px;
+  }
+#pragma unroll
+  for (int s = i; s < j; ++s) {
+    axpy4(cR[s], J[s + 1][j], br);
+    axpy4(cX[s], J[i][s], br);
+    if (s + 1 < j) ten_vec_acc(TT[s + 1][j], J[i][s], br);
+    if (s > i) vec_ten_acc(J[s + 1][j], TT[i][s], br);
+    if (need_t) {
+      const T* X = J[i][s];
+      const T* Y = J[s + 1][j];
+      tt[0] += X[0] * Y[1] - X[1] * Y[0];
+      tt[1] += X[0] * Y[2] - X[2] * Y[0];
+      tt[2] += X[0] * Y[3] - X[3] * Y[0];
+      tt[3] += X[1] * Y[2] - X[2] * Y[1];
+      tt[4] += X[1] * Y[3] - X[3] * Y[1];
+      tt[5] += X[2] * Y[3] - X[3] * Y[2];
+    }
+  }
+  T t[4], u[4];
+  add4(W, W, t);
+  add4(Sp[i], Sp[j + 1], u);
+  axpy4(-sxy, u, t);
+  add4(br, t, br);
+}
+
+// co_recursion with the tensor form of the bracket.
+template <int N, typename T>
+__device__ __forceinline__ T co_recursion_tf(T (&J)[N - 1][N - 1][4], const T (&Sp)[N][4], const int (&msk)[N],
+                                             const T* __restrict__ inv, const T (&en)[4]) {
+  constexpr int M = N - 1;
+  T TT[M][M][6];
+  T amp = T(0);
+#pragma unroll
+  for (int len = 2; len <= M; ++len) {
+#pragma unroll
+    for (int i = 0; i + len - 1 < M; ++i) {
+      const int j = i + len - 1;
+      T br[4], tt[6];
+      co_bracket_tf<N, T>(J, TT, Sp, i, j, len < M, br, tt);
+      if (len < M) {
+        const T ip = inv[msk[j + 1] ^ msk[i]];
+        scale4(ip, br, J[i][j]);
+#pragma unroll
+        for (int m = 0; m < 6; ++m) TT[i][j][m] = tt[m];
+      } else {
+        amp = mdot(en, br);
+      }
+    }
+  }
+  return amp;
+}
+
+template <int N, typename T, bool SUMHEL, bool TF = false>
 __global__ void __launch_bounds__(256) co_kernel(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
                                                  const double* __restrict__ p, const int8_t* __restrict__ hel,
                                                  PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
@@ -442,17 +529,21 @@ __global__ void __launch_bounds__(256) co_kernel(int64_t S_, const int64_t* __re
 #pragma unroll
       for (int m = 0; m < 4; ++m) en[m] = ev[m];
     }
-    const T a = co_recursion<N, T>(J, Sp, msk, s_inv + el * S::NMASK, en);
+    T a;
+    if constexpr (TF)
+      a = co_recursion_tf<N, T>(J, Sp, msk, s_inv + el * S::NMASK, en);
+    else
+      a = co_recursion<N, T>(J, Sp, msk, s_inv + el * S::NMASK, en);
     amps[(e * H + h) * (int64_t)K + r] = a * vfac;
   }
 }
 
-template <int N, typename T, bool SUMHEL>
+template <int N, typename T, bool SUMHEL, bool TF = false>
 cudaError_t launch_co_n(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
                         int* status, cudaStream_t s, const int64_t* dB) {
   using S = CoShape<N, SUMHEL>;
   using L = CoSmem<N, T, SUMHEL>;
-  auto kern = co_kernel<N, T, SUMHEL>;
+  auto kern = co_kernel<N, T, SUMHEL, TF>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (err != cudaSuccess) return err;
   const PolFrame F = make_pol_frame(q);
@@ -730,6 +821,28 @@ cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const 
     default: return cudaErrorInvalidValue;
   }
 #undef BG_CO_CASE
+}
+
+// The tensor form (Eqs. 2.23-2.26) in the one-thread-per-ordering kernel,
+// sampled or summed helicities, 4 <= n <= 9.
+template <typename T>
+cudaError_t launch_co_tensor_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
+                               T* amps, int* status, cudaStream_t s) {
+  const bool sum = (hel == nullptr);
+#define BG_COT_CASE(NN)                                                                      \
+  case NN:                                                                                   \
+    if (sum) return launch_co_n<NN, T, true, true>(B, sqrt_s, p, hel, q, amps, status, s, nullptr); \
+    return launch_co_n<NN, T, false, true>(B, sqrt_s, p, hel, q, amps, status, s, nullptr);
+  switch (n) {
+    BG_COT_CASE(4)
+    BG_COT_CASE(5)
+    BG_COT_CASE(6)
+    BG_COT_CASE(7)
+    BG_COT_CASE(8)
+    BG_COT_CASE(9)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BG_COT_CASE
 }
 
 }  // namespace bg

@@ -72,6 +72,15 @@ def test_canonical_flop_model():
     assert bench.colour_sum_flops(8) == 2 * 720 * 720 + 2 * 720
 
 
+def test_tensor_form_flop_model():
+    # n = 4 by hand: segments of length 2 (two of them): V3 65 + wedge 24 +
+    # propagator 12; the full current (length 3): two splits of V3 (130) and
+    # one contraction on each side (2 x 24); final contraction 7; 2 orderings
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.tensor_form_flops(4) == 2 * (7 + 2 * (65 + 24 + 12) + (130 + 48))
+
+
 def test_flow_order_counts_brute_force():
     # the bench's count of closing colour-flow orders (by colour types) against
     # the direct enumeration of the (n-1)! orders

@@ -38,6 +38,15 @@ def test_library_exports_every_declared_symbol(libbg):
     assert not missing, missing
 
 
+def test_binding_loads_without_gpu(libbg):
+    # the ctypes binding resolves every entry point it declares (a stale name
+    # would fail here, on the CPU, rather than on the GPU machine)
+    from paper_2106_06507_gb300 import bg
+    L = bg.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
 def test_probe_library_is_separate(libbg):
     # the FMA probe is a measurement utility in its own library, not part of
     # the product ABI
