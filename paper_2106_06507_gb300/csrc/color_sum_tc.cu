@@ -12,21 +12,29 @@
 // (24 significant bits), so that D is accurate to FP32 rounding; the MMA
 // accumulates in FP32 in tensor memory.
 //
-// Roles (10 warps):
+// Roles (10 warps, 11 with the staged amplitude path):
 //   warp 0      one thread: bulk copies of C tiles (mbarrier complete_tx)
 //   warp 1      allocates tensor memory; one thread issues tcgen05.mma and
 //               tcgen05.commit
 //   warps 2..5  converters: FP32 amplitudes -> 3 BF16 planes in shared memory
 //   warps 6..9  epilogue: tcgen05.ld of D rows (one event per thread),
 //               contraction with the FP32 amplitudes, FP64 accumulation
-// Two pipeline stages for the operands and two accumulator buffers in
+//   warp 10     (staged path) one thread: tensor-map bulk copies of the
+//               amplitude tile, 128 events x 64 orderings of FP32 per K chunk
+//               as two 128 x 32 boxes with 128-byte swizzle, into a ring of
+//               2-3 staging buffers ahead of the converters
+// Two pipeline stages for the BF16 operands and two accumulator buffers in
 // tensor memory, so that the epilogue of one ordering tile overlaps the
-// MMAs of the next.  Every mbarrier wait is bounded (about 2 s of SM
-// clocks); on expiry the kernel records BG_ETIMEOUT in the status word and
-// the CTA drains and exits.
+// MMAs of the next.  In the staged path the converters read their rows from
+// shared memory (the swizzle makes the 32 rows of a warp hit distinct banks)
+// instead of loading them from global memory row by row.  Every mbarrier
+// wait is bounded (about 2 s of SM clocks); on expiry the kernel records
+// BG_ETIMEOUT in the status word and the CTA drains and exits.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "bg_internal.h"
@@ -39,6 +47,9 @@ constexpr int TC_M = 128;         // events per CTA
 constexpr int TC_KC = 64;         // K elements per pipeline stage
 constexpr int TC_STAGES = 2;
 constexpr int TC_THREADS = 320;
+constexpr int TC_THREADS_STAGED = 352;
+constexpr int TC_AF_BYTES = TC_M * TC_KC * 4;  // one FP32 amplitude stage: two 16 KB boxes
+constexpr int TC_AF_MAX = 3;                   // FP32 staging buffers at most
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -82,6 +93,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
   return true;
 }
 
+// After a producer stops (normally or because a wait gave up), it waits, with
+// the same bound, for the bulk copies it issued into the last `depth` stages
+// (iterations it_end-depth .. it_end-1 of a ring of `depth` stages), so that
+// no copy is still writing shared memory when the CTA exits.  Returns at once
+// when the consumers have already seen those copies complete.
+__device__ __forceinline__ void drain_copies(uint64_t* full, int depth, int it_end) {
+  for (int it = it_end - depth; it < it_end; ++it) {
+    if (it < 0) continue;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(&full[it % depth], (uint32_t)(it / depth) & 1))
+      if (clock64() - t0 > kWaitCycles) break;
+  }
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -91,6 +116,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 2-D tensor-map bulk copy of the box at (x, y) into shared memory.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -151,7 +185,9 @@ __device__ __forceinline__ void tc_load16(const TIn* row, bool live, int m0, int
 #pragma unroll
   for (int j = 0; j < 16; ++j) x[j] = 0.0f;
   if (!live || m0 >= k) return;
-  if (sizeof(TIn) == 4 && m0 + 16 <= k && (k & 3) == 0) {
+  // vector loads only from 16-byte aligned addresses (the interface admits
+  // amplitude arrays that are merely 4-byte aligned)
+  if (sizeof(TIn) == 4 && m0 + 16 <= k && (reinterpret_cast<uintptr_t>(row + m0) & 15) == 0) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const float4 f = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(row) + m0 + 4 * v);
@@ -185,6 +221,7 @@ struct TcParams {
   int kchunks;  // K chunks of TC_KC
   double scale; // includes the gcd of C
   float g;      // gcd of C (Y = g D)
+  int af_stages;  // staged path: FP32 staging buffers (2..TC_AF_MAX)
 };
 
 // Converter step `it` for row r: wait for stage it % 2 to be free, split the
@@ -222,11 +259,11 @@ __device__ __forceinline__ bool tc_convert_chunk(const float (&x)[TC_KC], int it
   return true;
 }
 
-template <typename TIn, int CPL>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <typename TIn, int CPL, bool STAGED>
+__global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     color_sum_tc_kernel(TcParams P, const TIn* __restrict__ A, const __nv_bfloat16* __restrict__ Ct,
                         const uint8_t* __restrict__ accept, double* __restrict__ me2, int* __restrict__ status,
-                        TIn* __restrict__ Y) {
+                        TIn* __restrict__ Y, const __grid_constant__ CUtensorMap amap) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned carve-up
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -235,14 +272,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t c_plane_bytes = (uint32_t)P.nt * TC_KC * 2;
   const uint32_t stage_bytes = 3 * a_plane_bytes + ((c_tile_bytes + 1023) & ~1023u);
   unsigned char* stage_base = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_STAGES * stage_bytes);
+  // staged path: FP32 amplitude staging ring (1024-byte aligned for the swizzle)
+  unsigned char* af_base = smem + TC_STAGES * stage_bytes;
+  const int af_stages = STAGED ? P.af_stages : 0;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(af_base + (size_t)af_stages * TC_AF_BYTES);
   uint64_t* full_c = bars;                  // [2]
   uint64_t* full_a = bars + 2;              // [2]
   uint64_t* empty = bars + 4;               // [2]
   uint64_t* dfull = bars + 6;               // [2]
   uint64_t* dempty = bars + 8;              // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11);
+  uint64_t* full_af = bars + 10;            // [TC_AF_MAX]
+  uint64_t* empty_af = bars + 10 + TC_AF_MAX;  // [TC_AF_MAX]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10 + 2 * TC_AF_MAX);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 11 + 2 * TC_AF_MAX);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -264,6 +306,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&dfull[s], 1);
       mbar_init(&dempty[s], 128);
     }
+    for (int s = 0; s < af_stages; ++s) {
+      mbar_init(&full_af[s], 1);
+      mbar_init(&empty_af[s], 128);
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -281,7 +327,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ---------------- C tile producer ----------------
     if (lane == 0) {
-      for (int it = 0; it < total; ++it) {
+      int it = 0;
+      for (; it < total; ++it) {
         const int s = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
         if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) break;
@@ -292,6 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_arrive_expect_tx(&full_c[s], c_tile_bytes);
         bulk_g2s(dst, src, c_tile_bytes, &full_c[s]);
       }
+      drain_copies(full_c, TC_STAGES, it);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -332,6 +380,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (ok) mma_commit(&dfull[b]);  // accumulator b complete
       }
+    }
+  } else if (warp < 6 && STAGED) {
+    // ---------------- converters, staged path ----------------
+    // Row r of the chunk sits in the two swizzled boxes of the staging
+    // buffer: element j of box b at byte r*128 + ((j/4) ^ (r%8))*16 + (j%4)*4.
+    const int r = threadIdx.x - 64;
+    for (int it = 0; it < total; ++it) {
+      const int sa = it % af_stages;
+      const uint32_t ua = (uint32_t)(it / af_stages);
+      if (!mbar_wait(&full_af[sa], ua & 1, status, abort_flag)) break;
+      const unsigned char* box = af_base + (size_t)sa * TC_AF_BYTES + r * 128;
+      float x[TC_KC];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(box + b * (TC_AF_BYTES / 2) + ((c ^ (r & 7)) << 4));
+          x[b * 32 + 4 * c] = v.x, x[b * 32 + 4 * c + 1] = v.y, x[b * 32 + 4 * c + 2] = v.z,
+                         x[b * 32 + 4 * c + 3] = v.w;
+        }
+      }
+      const bool ok =
+          tc_convert_chunk(x, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag);
+      mbar_arrive(&empty_af[sa]);  // the staging buffer's rows are in registers and converted
+      if (!ok) break;
+    }
+  } else if (warp == 10) {
+    // ---------------- staged path: amplitude tile producer ----------------
+    if (STAGED && lane == 0) {
+      int it = 0;
+      for (; it < total; ++it) {
+        const int sa = it % af_stages;
+        const uint32_t ua = (uint32_t)(it / af_stages);
+        if (it >= af_stages && !mbar_wait(&empty_af[sa], (ua - 1) & 1, status, abort_flag)) break;
+        const int kc = it % P.kchunks;
+        unsigned char* dst = af_base + (size_t)sa * TC_AF_BYTES;
+        mbar_arrive_expect_tx(&full_af[sa], TC_AF_BYTES);
+        tma_load_2d(dst, &amap, kc * TC_KC, (int)e0, &full_af[sa]);
+        tma_load_2d(dst + TC_AF_BYTES / 2, &amap, kc * TC_KC + 32, (int)e0, &full_af[sa]);
+      }
+      drain_copies(full_af, af_stages, it);
     }
   } else if (warp < 6) {
     // ---------------- converters: FP32 -> hi/mid/lo BF16 planes ----------------
@@ -466,11 +555,51 @@ bool build_tc_tiles(int n, const std::vector<double>& dense, int k, std::vector<
   return true;
 }
 
-size_t tc_smem_bytes(int nt, int cpl) {
+size_t tc_smem_bytes(int nt, int cpl, int af_stages) {
   const size_t a_plane = TC_M * TC_KC * 2;
   const size_t c_tile = ((size_t)nt * TC_KC * 2 * cpl + 1023) & ~size_t(1023);
-  return 1024 + TC_STAGES * (3 * a_plane + c_tile) + 128;
+  return 1024 + TC_STAGES * (3 * a_plane + c_tile) + (size_t)af_stages * TC_AF_BYTES + 256;
 }
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of the FP32 amplitudes A [B][k] (row stride k): boxes of 32
+// orderings x 128 events with 128-byte swizzle; out-of-range boxes are
+// zero-filled.  False if the layout does not allow it (base or row stride
+// not a multiple of 16 bytes, sizes out of range).
+bool amp_tensor_map(const float* A, int64_t B, int k, CUtensorMap* map) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(A) & 15) || ((size_t)k * 4) % 16 || B < 1 || B > (int64_t(1) << 31))
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)B};
+  const cuuint64_t strides[1] = {(cuuint64_t)k * 4};
+  const cuuint32_t box[2] = {32, (cuuint32_t)TC_M};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr size_t kSmemOptIn = 232448;  // shared memory per block (opt-in)
 
 cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, int* status, cudaStream_t s) {
   TcParams P;
@@ -482,20 +611,34 @@ cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, in
   P.kchunks = C->tc_kchunks;
   P.scale = a.scale * C->tc_g;
   P.g = (float)C->tc_g;
-  const size_t smem = tc_smem_bytes(P.nt, C->tc_cpl);
+  P.af_stages = 0;
   const unsigned blocks = (unsigned)((a.B + TC_M - 1) / TC_M);
-#define BG_TC_LAUNCH(TIN, CPL)                                                                                 \
+  // The staged amplitude path: FP32 amplitudes, one BF16 plane of C, a
+  // tensor map for A, and room for at least two staging buffers.
+  CUtensorMap amap;
+  std::memset(&amap, 0, sizeof amap);
+  if (a.amps_f32 && C->tc_cpl == 1) {
+    int st = TC_AF_MAX;
+    while (st >= 2 && tc_smem_bytes(P.nt, 1, st) > kSmemOptIn) --st;
+    if (st >= 2 && amp_tensor_map(static_cast<const float*>(a.amps), a.B, a.k, &amap)) P.af_stages = st;
+  }
+  const size_t smem = tc_smem_bytes(P.nt, C->tc_cpl, P.af_stages);
+#define BG_TC_LAUNCH(TIN, CPL, STG)                                                                            \
   {                                                                                                            \
-    auto kern = color_sum_tc_kernel<TIN, CPL>;                                                                 \
+    auto kern = color_sum_tc_kernel<TIN, CPL, STG>;                                                            \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
     if (e != cudaSuccess) return e;                                                                            \
-    kern<<<blocks, TC_THREADS, smem, s>>>(P, static_cast<const TIN*>(a.amps), C->tc_tiles, a.accept, a.me2,    \
-                                          status, static_cast<TIN*>(a.Y));                                     \
+    kern<<<blocks, STG ? TC_THREADS_STAGED : TC_THREADS, smem, s>>>(                                           \
+        P, static_cast<const TIN*>(a.amps), C->tc_tiles, a.accept, a.me2, status, static_cast<TIN*>(a.Y), amap); \
   }
   if (a.amps_f32) {
-    if (C->tc_cpl == 1) BG_TC_LAUNCH(float, 1) else BG_TC_LAUNCH(float, 2)
+    if (C->tc_cpl == 1) {
+      if (P.af_stages) BG_TC_LAUNCH(float, 1, true) else BG_TC_LAUNCH(float, 1, false)
+    } else {
+      BG_TC_LAUNCH(float, 2, false)
+    }
   } else {
-    if (C->tc_cpl == 1) BG_TC_LAUNCH(double, 1) else BG_TC_LAUNCH(double, 2)
+    if (C->tc_cpl == 1) BG_TC_LAUNCH(double, 1, false) else BG_TC_LAUNCH(double, 2, false)
   }
 #undef BG_TC_LAUNCH
   return cudaGetLastError();

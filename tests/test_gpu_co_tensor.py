@@ -8,7 +8,8 @@ form, under the tolerances of test_gpu_co.py:
   FP64 amplitudes: element-wise within 1e-11 of the event's largest ordering
   amplitude (n = 4..8, and n = 9 for a few events);
   FP64 helicity-summed |M|^2 at n = 4 (all 16 configurations): the FP64
-  parity rule against the extended-precision oracle;
+  parity rule against the extended-precision oracle, with the rounding floor
+  of the oracle's two FP64 evaluations (four-vertex and tensor form);
   FP32 |M|^2 with the exact colour sum (FP64 CUDA cores): median relative
   error below 2e-6, all below 1e-3."""
 import numpy as np
@@ -16,7 +17,6 @@ import pytest
 
 from paper_2106_06507_gb300 import inputs
 
-from test_gpu_co import assert_fp64_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -62,14 +62,26 @@ def test_tensor_form_amplitudes_fp64(bg, oracle, n, B):
 
 
 def test_tensor_form_helicity_sum_n4(bg, oracle):
+    # The FP64 rule of test_gpu_co.py with the rounding floor of both FP64
+    # evaluations of the definition in the oracle, the four-vertex and the
+    # tensor form: the GPU tensor form sums in the latter's order.
     n, B = 4, 2000
     u = inputs.rambo_uniforms(n, B, seed=140)
     C = bg.ColourMatrix(n)
     p, _ = bg.momenta_rambo(n, dev_arr(u), SQRT_S)
     amps = bg.currents_co(n, p, None, prec=bg.BG_F64, sqrt_s=SQRT_S, tensor_form=True)
-    me2 = bg.color_sum(C, amps, hel_sampled=False, mode=bg.BG_CS_F64, sqrt_s=SQRT_S).cpu().numpy()
-    assert_fp64_parity(oracle, me2, n, u, None)
+    got = bg.color_sum(C, amps, hel_sampled=False, mode=bg.BG_CS_F64, sqrt_s=SQRT_S).cpu().numpy()
     C.close()
+    ext = oracle.me2_co_ext(n, u, sqrt_s=SQRT_S)
+    f64 = oracle.me2_co(n, u, sqrt_s=SQRT_S)
+    f64t = oracle.me2_co(n, u, sqrt_s=SQRT_S, tensor_form=True)
+    assert np.array_equal(got == 0, ext == 0)
+    nz = ext != 0
+    rel = np.abs(got[nz] / ext[nz] - 1.0)
+    floor = np.maximum(np.abs(f64[nz] / ext[nz] - 1.0), np.abs(f64t[nz] / ext[nz] - 1.0))
+    assert np.median(rel) <= max(1e-13, 8.0 * np.median(floor))
+    assert np.sum(rel > 1e-12) <= 2 + 2 * np.sum(floor > 1e-12)
+    assert rel.max() <= max(5e-11, 8.0 * floor.max())
 
 
 @pytest.mark.parametrize("n,B", [(6, 1001), (7, 301), (8, 67)])

@@ -88,6 +88,28 @@ def test_tc_repeated_calls_are_deterministic(bg):
     C.close()
 
 
+@pytest.mark.parametrize("n,B", [(6, 1000), (7, 300), (8, 129), (8, 1500)])
+def test_tc_staged_path_matches_register_path(bg, n, B):
+    # FP32 amplitudes at a 16-byte aligned address go through the staged
+    # path (tensor-map copies of the amplitude tile into shared memory); the
+    # same amplitudes at an address that is only 4-byte aligned go through
+    # the per-thread loads.  Both convert and multiply the same numbers in the
+    # same order: the results must be bit for bit equal.
+    import torch
+    C = bg.ColourMatrix(n)
+    _, _, acc, amps = amps_for(bg, n, B, 60 + n, bg.BG_F32)
+    k = amps.shape[2]
+    flat = torch.empty((B * k + 4,), dtype=torch.float32, device=amps.device)
+    shifted = flat[1:1 + B * k].view(B, 1, k)
+    shifted.copy_(amps)
+    assert shifted.data_ptr() % 16 != 0 and amps.data_ptr() % 16 == 0
+    a = bg.color_sum(C, amps, True, mode=bg.BG_CS_TC_BF16, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    b = bg.color_sum(C, shifted, True, mode=bg.BG_CS_TC_BF16, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    assert bg.device_status() == 0
+    assert np.array_equal(a, b)
+    C.close()
+
+
 def test_tc_unsupported_cases(bg):
     import torch
     for n in (5,):
