@@ -472,7 +472,8 @@ bg_status bg_mixed_counts(bg_mixed* plan, int64_t* counts);
  *   BG_ALGO_CO (sampled helicities, n >= 6): 0 = one thread per ordering,
  *     1 = depth-first groups of six orderings sharing prefix currents in
  *     blocks of 256 threads, 2 = the same in blocks of 128, 3 = blocks of
- *     128 with registers capped for three blocks per SM (defaults: 2 for
+ *     128 with registers capped for three blocks per SM, 4 and 5 = blocks
+ *     of 64 with at most 200 and 184 registers per thread (defaults: 2 for
  *     n = 6, 7; 1 for n = 8, 9);
  *     helicity sums and n < 6 have one variant;
  *   BG_ALGO_CD: (threads per event, unrolling of the partition loop):

@@ -584,10 +584,10 @@ struct CoDfsSmem {
   static constexpr size_t bytes = off_p2 + sizeof(double) * S::EB * S::NMASK;
 };
 
-template <int N, typename T, int NT_, int MINB_ = 1>
-__global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
-                                                     const double* __restrict__ p, const int8_t* __restrict__ hel,
-                                                     PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
+template <int N, typename T, int NT_>
+__device__ __forceinline__ void co_dfs_body(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
+                                            const double* __restrict__ p, const int8_t* __restrict__ hel,
+                                            const PolFrame& F, T* __restrict__ amps, int* __restrict__ status) {
   // S_: capacity (row stride of p and hel); dB: device-side event count (NULL: S_)
   const int64_t B = dB ? (*dB < S_ ? *dB : S_) : S_;
   using S = CoDfsShape<N, NT_>;
@@ -776,12 +776,39 @@ __global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const in
   }
 }
 
+// Kernels of the depth-first variant: a block size with a minimum number of
+// resident blocks (the register budget follows from it), or a block size
+// with an explicit register cap MAXREG (the compiler spills what does not
+// fit).  Both run co_dfs_body: the same arithmetic, bitwise identical.
+template <int N, typename T, int NT_, int MINB_ = 1>
+__global__ void __launch_bounds__(NT_, MINB_) co_kernel_dfs(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s,
+                                                     const double* __restrict__ p, const int8_t* __restrict__ hel,
+                                                     PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
+  co_dfs_body<N, T, NT_>(S_, dB, inv_sqrt_s, p, hel, F, amps, status);
+}
+template <int N, typename T, int NT_, int MAXREG_>
+__global__ void __launch_bounds__(NT_) __maxnreg__(MAXREG_)
+    co_kernel_dfs_r(int64_t S_, const int64_t* __restrict__ dB, double inv_sqrt_s, const double* __restrict__ p,
+                    const int8_t* __restrict__ hel, PolFrame F, T* __restrict__ amps, int* __restrict__ status) {
+  co_dfs_body<N, T, NT_>(S_, dB, inv_sqrt_s, p, hel, F, amps, status);
+}
+
+// MINB > 0: co_kernel_dfs<.., NT, MINB>; MINB < 0: co_kernel_dfs_r with at
+// most -MINB registers per thread.
+template <int N, typename T, int NT, int MINB>
+constexpr auto co_dfs_kernel_ptr() {
+  if constexpr (MINB > 0)
+    return co_kernel_dfs<N, T, NT, MINB>;
+  else
+    return co_kernel_dfs_r<N, T, NT, -MINB>;
+}
+
 template <int N, typename T, int NT, int MINB = 1>
 cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q, T* amps,
                           int* status, cudaStream_t s, const int64_t* dB) {
   using S = CoDfsShape<N, NT>;
   using L = CoDfsSmem<N, T, NT>;
-  auto kern = co_kernel_dfs<N, T, NT, MINB>;
+  auto kern = co_dfs_kernel_ptr<N, T, NT, MINB>();
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (err != cudaSuccess) return err;
   const PolFrame F = make_pol_frame(q);
@@ -794,22 +821,26 @@ cudaError_t launch_co_dfs(int64_t B, double sqrt_s, const double* p, const int8_
 // 1 = depth-first groups of six orderings in blocks of 256 threads, 2 = the
 // same in blocks of 128 threads (more resident blocks: the FP64 prologue of
 // one block overlaps the recursion of another), 3 = 128-thread blocks with
-// registers capped for three resident blocks per SM.  Defaults (GB300
-// timings): 2 for n = 6, 7; 1 for n = 8, 9.  The helicity sum and n < 6 have
-// one variant.
-inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 4 : 1; }
+// registers capped for three resident blocks per SM, 4 and 5 = 64-thread
+// blocks with at most 200 and 184 registers per thread (10 and 11 resident
+// warps per SM at n = 8, where the uncapped kernel takes 219 and allows 8).
+// Defaults (GB300 timings): 2 for n = 6, 7; 1 for n = 8, 9.  The helicity
+// sum and n < 6 have one variant.
+inline int co_num_variants(int n, bool sum) { return (!sum && n >= 6) ? 6 : 1; }
 
 template <typename T>
 cudaError_t launch_co_t(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,
                         T* amps, int* status, cudaStream_t s, const int64_t* dB, int variant) {
   const bool sum = (hel == nullptr);
-  const int v = (sum || n < 6) ? 0 : (variant < 0 || variant > 3 ? (n <= 7 ? 2 : 1) : variant);
+  const int v = (sum || n < 6) ? 0 : (variant < 0 || variant > 5 ? (n <= 7 ? 2 : 1) : variant);
 #define BG_CO_CASE(NN)                                                                                   \
   case NN:                                                                                               \
     if (sum) return launch_co_n<NN, T, true>(B, sqrt_s, p, hel, q, amps, status, s, dB);                \
     if (v == 1) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 256>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
     if (v == 2) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 128>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
     if (v == 3) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 128, 3>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
+    if (v == 4) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 64, -200>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
+    if (v == 5) return launch_co_dfs<(NN >= 6 ? NN : 6), T, 64, -184>(B, sqrt_s, p, hel, q, amps, status, s, dB); \
     return launch_co_n<NN, T, false>(B, sqrt_s, p, hel, q, amps, status, s, dB);
   switch (n) {
     BG_CO_CASE(4)

@@ -5,7 +5,8 @@
 //   colour-ordered recursion, sampled helicities, n >= 6:
 //     0 = one thread per ordering, 1 / 2 / 3 = depth-first groups of six
 //     orderings in blocks of 256 / 128 / 128 threads (3: registers capped
-//     for three resident blocks);
+//     for three resident blocks), 4 / 5 = blocks of 64 threads with at most
+//     200 / 184 registers per thread;
 //   colour-dressed recursion: threads per event (CTA size) and unrolling of
 //     the partition loop, see cd_variant_threads() in cd_recursion.cuh.
 // bg_autotune times every variant on a synthetic probe batch (Rambo points

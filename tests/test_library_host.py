@@ -108,7 +108,7 @@ def test_tune_variant_counts_without_gpu(libbg):
     # dressed: four (CTA size, unrolling) pairs up to n = 9, five above;
     # out of range: 0
     CO, CD = 0, 1
-    assert [libbg.bg_tune_num_variants(CO, n) for n in range(4, 10)] == [1, 1, 4, 4, 4, 4]
+    assert [libbg.bg_tune_num_variants(CO, n) for n in range(4, 10)] == [1, 1, 6, 6, 6, 6]
     assert [libbg.bg_tune_num_variants(CD, n) for n in range(4, 13)] == [4] * 6 + [5] * 3
     assert libbg.bg_tune_num_variants(CO, 10) == 0
     assert libbg.bg_tune_num_variants(CD, 3) == 0
