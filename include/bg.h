@@ -173,7 +173,11 @@ bg_status bg_currents_co_tensor(int n, int64_t B, double sqrt_s, const double* p
  *   me2     [B] double   output in GeV^(8-2n).
  * mode BG_CS_F64 accumulates in FP64; BG_CS_F32 forms C A in FP32 (C's
  * integer entries are exact in FP32) and accumulates the quadratic form
- * per event in FP64.
+ * per event in FP64.  BG_CS_TC_BF16: every wait of the tensor-core kernel
+ * on its pipeline is bounded (~2 s); if one runs out, the kernel records
+ * BG_ETIMEOUT in the device status word and writes 0 for its events.  (The
+ * environment variable BG_TC_TEST_STALL=1 makes the waits run out on purpose
+ * after ~1 ms; it exists for the tests of that path.)
  * Errors: BG_EINVAL (NULL C/amps/me2, B < 0, H < 1), BG_ECUDA.
  * ------------------------------------------------------------------------- */
 bg_status bg_color_sum(const bg_colormat* C, int64_t B, int H, const void* amps, bg_prec amp_prec,

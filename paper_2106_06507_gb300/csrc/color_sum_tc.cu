@@ -33,6 +33,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -51,6 +52,7 @@ constexpr int TC_THREADS_STAGED = 352;
 constexpr int TC_AF_BYTES = TC_M * TC_KC * 4;  // one FP32 amplitude stage: two 16 KB boxes
 constexpr int TC_AF_MAX = 3;                   // FP32 staging buffers at most
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr long long kTestWaitCycles = 2000000LL;  // ~1 ms: the stall test's limit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -79,12 +81,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; returns false (and records BG_ETIMEOUT) if the phase does not
-// complete within kWaitCycles, or if another thread has already given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort_flag) {
+// complete within `limit` SM clocks, or if another thread has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort_flag,
+                                          long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       flag_status(status, BG_ETIMEOUT);
       return false;
@@ -222,6 +225,8 @@ struct TcParams {
   double scale; // includes the gcd of C
   float g;      // gcd of C (Y = g D)
   int af_stages;  // staged path: FP32 staging buffers (2..TC_AF_MAX)
+  long long wait_cycles;  // limit of every bounded wait (SM clocks)
+  int stall_c;    // test hook: the C-tile producer issues nothing, so the waits run out
 };
 
 // Converter step `it` for row r: wait for stage it % 2 to be free, split the
@@ -229,10 +234,11 @@ struct TcParams {
 // layout, signal full_a.  Returns false if a wait gave up.
 __device__ __forceinline__ bool tc_convert_chunk(const float (&x)[TC_KC], int it, int r, unsigned char* stage_base,
                                                  uint32_t stage_bytes, uint32_t a_plane_bytes, uint64_t* empty,
-                                                 uint64_t* full_a, int* status, volatile int* abort_flag) {
+                                                 uint64_t* full_a, int* status, volatile int* abort_flag,
+                                                 long long limit) {
   const int s = it & 1;
   const uint32_t use = (uint32_t)(it >> 1);
-  if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) return false;
+  if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag, limit)) return false;
   unsigned char* st = stage_base + s * stage_bytes;
 #pragma unroll
   for (int g = 0; g < TC_KC / 8; ++g) {
@@ -326,12 +332,12 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
 
   if (warp == 0) {
     // ---------------- C tile producer ----------------
-    if (lane == 0) {
+    if (lane == 0 && !P.stall_c) {
       int it = 0;
       for (; it < total; ++it) {
         const int s = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
-        if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag)) break;
+        if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag, P.wait_cycles)) break;
         const int ntile = it / P.kchunks, kc = it % P.kchunks;
         unsigned char* dst = stage_base + s * stage_bytes + 3 * a_plane_bytes;
         const unsigned char* src = reinterpret_cast<const unsigned char*>(Ct) +
@@ -349,15 +355,15 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
       for (int ntile = 0; ntile < P.ntiles && ok; ++ntile) {
         const int b = ntile & 1;
         const uint32_t buse = (uint32_t)(ntile >> 1);
-        if (ntile >= 2 && !mbar_wait(&dempty[b], (buse - 1) & 1, status, abort_flag)) { ok = false; break; }
+        if (ntile >= 2 && !mbar_wait(&dempty[b], (buse - 1) & 1, status, abort_flag, P.wait_cycles)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * P.nt);
         for (int kc = 0; kc < P.kchunks; ++kc) {
           const int it = ntile * P.kchunks + kc;
           const int s = it & 1;
           const uint32_t use = (uint32_t)(it >> 1);
-          if (!mbar_wait(&full_c[s], use & 1, status, abort_flag) ||
-              !mbar_wait(&full_a[s], use & 1, status, abort_flag)) {
+          if (!mbar_wait(&full_c[s], use & 1, status, abort_flag, P.wait_cycles) ||
+              !mbar_wait(&full_a[s], use & 1, status, abort_flag, P.wait_cycles)) {
             ok = false;
             break;
           }
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     for (int it = 0; it < total; ++it) {
       const int sa = it % af_stages;
       const uint32_t ua = (uint32_t)(it / af_stages);
-      if (!mbar_wait(&full_af[sa], ua & 1, status, abort_flag)) break;
+      if (!mbar_wait(&full_af[sa], ua & 1, status, abort_flag, P.wait_cycles)) break;
       const unsigned char* box = af_base + (size_t)sa * TC_AF_BYTES + r * 128;
       float x[TC_KC];
 #pragma unroll
@@ -402,7 +408,8 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
         }
       }
       const bool ok =
-          tc_convert_chunk(x, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag);
+          tc_convert_chunk(x, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag,
+                           P.wait_cycles);
       mbar_arrive(&empty_af[sa]);  // the staging buffer's rows are in registers and converted
       if (!ok) break;
     }
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
       for (; it < total; ++it) {
         const int sa = it % af_stages;
         const uint32_t ua = (uint32_t)(it / af_stages);
-        if (it >= af_stages && !mbar_wait(&empty_af[sa], (ua - 1) & 1, status, abort_flag)) break;
+        if (it >= af_stages && !mbar_wait(&empty_af[sa], (ua - 1) & 1, status, abort_flag, P.wait_cycles)) break;
         const int kc = it % P.kchunks;
         unsigned char* dst = af_base + (size_t)sa * TC_AF_BYTES;
         mbar_arrive_expect_tx(&full_af[sa], TC_AF_BYTES);
@@ -434,12 +441,13 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     tc_load_chunk<TIn>(row, e < P.B, 0, P.k, xa);
     for (int it = 0; it < total; it += 2) {
       if (it + 1 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 1) % P.kchunks, P.k, xb);
-      if (!tc_convert_chunk(xa, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag))
+      if (!tc_convert_chunk(xa, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag,
+                            P.wait_cycles))
         break;
       if (it + 1 >= total) break;
       if (it + 2 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 2) % P.kchunks, P.k, xa);
       if (!tc_convert_chunk(xb, it + 1, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status,
-                            abort_flag))
+                            abort_flag, P.wait_cycles))
         break;
     }
   } else {
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
       const int b = ntile & 1;
       const uint32_t buse = (uint32_t)(ntile >> 1);
       // warp-uniform decision: tcgen05.ld below is .sync.aligned
-      const bool ready = mbar_wait(&dfull[b], buse & 1, status, abort_flag);
+      const bool ready = mbar_wait(&dfull[b], buse & 1, status, abort_flag, P.wait_cycles);
       if (!__all_sync(0xffffffffu, ready)) break;
       tc_fence_after();
       float part = 0.0f;
@@ -612,6 +620,11 @@ cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, in
   P.scale = a.scale * C->tc_g;
   P.g = (float)C->tc_g;
   P.af_stages = 0;
+  // BG_TC_TEST_STALL (tests only): the C tiles are never copied, every wait
+  // runs out after ~1 ms, the kernel records BG_ETIMEOUT and writes 0.
+  const char* stall = std::getenv("BG_TC_TEST_STALL");
+  P.stall_c = (stall && stall[0] == '1') ? 1 : 0;
+  P.wait_cycles = P.stall_c ? kTestWaitCycles : kWaitCycles;
   const unsigned blocks = (unsigned)((a.B + TC_M - 1) / TC_M);
   // The staged amplitude path: FP32 amplitudes, one BF16 plane of C, a
   // tensor map for A, and room for at least two staging buffers.

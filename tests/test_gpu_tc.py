@@ -110,6 +110,35 @@ def test_tc_staged_path_matches_register_path(bg, n, B):
     C.close()
 
 
+@pytest.mark.parametrize("staged", [True, False])
+def test_tc_bounded_wait_runs_out(bg, monkeypatch, staged):
+    # BG_TC_TEST_STALL=1 makes the colour-matrix tile producer issue no copy,
+    # so the MMA issuer's wait for the first tile (and then every other wait)
+    # runs out after ~1 ms: the kernel must record BG_ETIMEOUT in the device
+    # status word, write |M|^2 = 0, leave no copy or MMA in flight, and the
+    # device must stay usable (the next call gives the normal result).
+    import torch
+    n, B = 8, 300
+    C = bg.ColourMatrix(n)
+    _, _, acc, amps = amps_for(bg, n, B, 70, bg.BG_F32)
+    if not staged:  # a 4-byte aligned copy takes the per-thread load path
+        flat = torch.empty((B * 720 + 4,), dtype=torch.float32, device=amps.device)
+        amps = flat[1:1 + B * 720].view(B, 1, 720).copy_(amps)
+    bg.device_status_reset()
+    ref = bg.color_sum(C, amps, True, mode=bg.BG_CS_TC_BF16, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    assert bg.device_status() == 0 and (ref > 0).any()
+    monkeypatch.setenv("BG_TC_TEST_STALL", "1")
+    got = bg.color_sum(C, amps, True, mode=bg.BG_CS_TC_BF16, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    assert bg.device_status() == bg.BG_ETIMEOUT
+    assert np.all(got == 0.0)
+    monkeypatch.delenv("BG_TC_TEST_STALL")
+    bg.device_status_reset()
+    again = bg.color_sum(C, amps, True, mode=bg.BG_CS_TC_BF16, sqrt_s=SQRT_S, accept=acc).cpu().numpy()
+    assert bg.device_status() == 0
+    assert np.array_equal(again, ref)
+    C.close()
+
+
 def test_tc_unsupported_cases(bg):
     import torch
     for n in (5,):

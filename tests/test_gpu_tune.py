@@ -62,7 +62,7 @@ def test_co_variants_bitwise_identical(bg, n, prec):
         bg.tune_set(bg.BG_ALGO_CO, n, prec, v)
         outs.append(bg.currents_co(n, p, hel, prec=prec, sqrt_s=SQRT_S).cpu().numpy())
     bg.tune_set(bg.BG_ALGO_CO, n, prec, -1)
-    assert len(outs) == 4
+    assert len(outs) == 6
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
 
@@ -73,7 +73,7 @@ def test_autotune_table_and_cache(bg, tmp_path):
     assert ms_cd[best_cd] == min(ms_cd)
     assert bg.tune_get(bg.BG_ALGO_CD, 10, bg.BG_F32) == best_cd
     best_co, ms_co = bg.autotune(bg.BG_ALGO_CO, 7, bg.BG_F32)
-    assert best_co in (0, 1, 2, 3) and len(ms_co) == 4
+    assert best_co in range(6) and len(ms_co) == 6
     path = str(tmp_path / "tune.txt")
     bg.tune_save(path)
     bg.tune_set(bg.BG_ALGO_CD, 10, bg.BG_F32, -1)
