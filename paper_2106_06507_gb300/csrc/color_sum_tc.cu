@@ -23,9 +23,10 @@
 //               amplitude tile, 128 events x 64 orderings of FP32 per K chunk
 //               as two 128 x 32 boxes with 128-byte swizzle, into a ring of
 //               2-3 staging buffers ahead of the converters
-// Two pipeline stages for the BF16 operands and two accumulator buffers in
-// tensor memory, so that the epilogue of one ordering tile overlaps the
-// MMAs of the next.  In the staged path the converters read their rows from
+// The CTAs are persistent (one per SM, each looping over tiles of 128
+// events).  Two pipeline stages for the BF16 operands and two accumulator
+// buffers in tensor memory, so that the epilogue of one ordering tile
+// overlaps the MMAs of the next -- also across the CTA's event tiles.  In the staged path the converters read their rows from
 // shared memory (the swizzle makes the 32 rows of a warp hit distinct banks)
 // instead of loading them from global memory row by row.  Every mbarrier
 // wait is bounded (about 2 s of SM clocks); on expiry the kernel records
@@ -245,15 +246,18 @@ __device__ __forceinline__ bool tc_convert_chunk(const float (&x)[TC_KC], int it
     uint32_t hi[4], mid[4], lo[4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
+      // pairs of elements converted by one packed instruction each (the same
+      // round-to-nearest-even of each element as the scalar conversion)
       const float x0 = x[g * 8 + j], x1 = x[g * 8 + j + 1];
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-      const float r0 = x0 - __bfloat162float(h0), r1 = x1 - __bfloat162float(h1);
-      const __nv_bfloat16 m0 = __float2bfloat16_rn(r0), m1 = __float2bfloat16_rn(r1);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(r0 - __bfloat162float(m0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(r1 - __bfloat162float(m1));
-      hi[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-      mid[j / 2] = (uint32_t)__bfloat16_as_ushort(m0) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
-      lo[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      const float2 hf = __bfloat1622float2(h);
+      const float r0 = x0 - hf.x, r1 = x1 - hf.y;
+      const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+      const float2 mf = __bfloat1622float2(m);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+      hi[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+      mid[j / 2] = *reinterpret_cast<const uint32_t*>(&m);
+      lo[j / 2] = *reinterpret_cast<const uint32_t*>(&l);
     }
     const uint32_t off = tile_off(r, g * 8);
     *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -294,13 +298,19 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t e0 = (int64_t)blockIdx.x * TC_M;
-  if (P.dB) {
-    const int64_t cnt = *P.dB < P.B ? *P.dB : P.B;
-    if (e0 >= cnt) return;  // whole CTA beyond the events of this launch
-    P.B = cnt;
-  }
-  const int total = P.ntiles * P.kchunks;  // pipeline iterations
+  // Persistent CTAs: this CTA takes the event tiles blockIdx.x, + gridDim.x,
+  // ...; the pipeline iterations (it) and the accumulator uses (g) count on
+  // across its tiles, so that the epilogue of one tile overlaps the MMAs of
+  // the next.
+  int64_t nev = P.B;
+  if (P.dB) nev = *P.dB < P.B ? *P.dB : P.B;
+  const int64_t ntev = (nev + TC_M - 1) / TC_M;
+  const int my_tiles = (int64_t)blockIdx.x < ntev ? (int)((ntev - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  if (my_tiles == 0) return;  // whole CTA without events in this launch
+  P.B = nev;
+  const int total = P.ntiles * P.kchunks;  // pipeline iterations per event tile
+  const int all_it = my_tiles * total;
+  const int all_g = my_tiles * P.ntiles;
   const uint32_t tmem_cols = (2 * P.nt <= 32) ? 32 : (2 * P.nt <= 64) ? 64 : (2 * P.nt <= 128) ? 128
                            : (2 * P.nt <= 256) ? 256 : 512;
 
@@ -334,11 +344,12 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     // ---------------- C tile producer ----------------
     if (lane == 0 && !P.stall_c) {
       int it = 0;
-      for (; it < total; ++it) {
+      for (; it < all_it; ++it) {
         const int s = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
         if (it >= TC_STAGES && !mbar_wait(&empty[s], (use - 1) & 1, status, abort_flag, P.wait_cycles)) break;
-        const int ntile = it / P.kchunks, kc = it % P.kchunks;
+        const int local = it % total;
+        const int ntile = local / P.kchunks, kc = local % P.kchunks;
         unsigned char* dst = stage_base + s * stage_bytes + 3 * a_plane_bytes;
         const unsigned char* src = reinterpret_cast<const unsigned char*>(Ct) +
                                    ((size_t)ntile * P.kchunks + kc) * (size_t)c_tile_bytes;
@@ -352,14 +363,14 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(TC_M, P.nt);
       bool ok = true;
-      for (int ntile = 0; ntile < P.ntiles && ok; ++ntile) {
-        const int b = ntile & 1;
-        const uint32_t buse = (uint32_t)(ntile >> 1);
-        if (ntile >= 2 && !mbar_wait(&dempty[b], (buse - 1) & 1, status, abort_flag, P.wait_cycles)) { ok = false; break; }
+      for (int g = 0; g < all_g && ok; ++g) {
+        const int b = g & 1;
+        const uint32_t buse = (uint32_t)(g >> 1);
+        if (g >= 2 && !mbar_wait(&dempty[b], (buse - 1) & 1, status, abort_flag, P.wait_cycles)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * P.nt);
         for (int kc = 0; kc < P.kchunks; ++kc) {
-          const int it = ntile * P.kchunks + kc;
+          const int it = g * P.kchunks + kc;
           const int s = it & 1;
           const uint32_t use = (uint32_t)(it >> 1);
           if (!mbar_wait(&full_c[s], use & 1, status, abort_flag, P.wait_cycles) ||
@@ -392,7 +403,7 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     // Row r of the chunk sits in the two swizzled boxes of the staging
     // buffer: element j of box b at byte r*128 + ((j/4) ^ (r%8))*16 + (j%4)*4.
     const int r = threadIdx.x - 64;
-    for (int it = 0; it < total; ++it) {
+    for (int it = 0; it < all_it; ++it) {
       const int sa = it % af_stages;
       const uint32_t ua = (uint32_t)(it / af_stages);
       if (!mbar_wait(&full_af[sa], ua & 1, status, abort_flag, P.wait_cycles)) break;
@@ -417,11 +428,12 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     // ---------------- staged path: amplitude tile producer ----------------
     if (STAGED && lane == 0) {
       int it = 0;
-      for (; it < total; ++it) {
+      for (; it < all_it; ++it) {
         const int sa = it % af_stages;
         const uint32_t ua = (uint32_t)(it / af_stages);
         if (it >= af_stages && !mbar_wait(&empty_af[sa], (ua - 1) & 1, status, abort_flag, P.wait_cycles)) break;
-        const int kc = it % P.kchunks;
+        const int64_t e0 = ((int64_t)blockIdx.x + (int64_t)(it / total) * gridDim.x) * TC_M;
+        const int kc = (it % total) % P.kchunks;
         unsigned char* dst = af_base + (size_t)sa * TC_AF_BYTES;
         mbar_arrive_expect_tx(&full_af[sa], TC_AF_BYTES);
         tma_load_2d(dst, &amap, kc * TC_KC, (int)e0, &full_af[sa]);
@@ -435,61 +447,83 @@ __global__ void __launch_bounds__(STAGED ? TC_THREADS_STAGED : TC_THREADS, 1)
     // current chunk is converted (and before waiting for a free stage), so
     // the loads' latency overlaps the conversion and the MMAs.
     const int r = threadIdx.x - 64;  // row (event) of the tile, 0..127
-    const int64_t e = e0 + r;
-    const TIn* row = A + e * (int64_t)P.k;
-    float xa[TC_KC], xb[TC_KC];
-    tc_load_chunk<TIn>(row, e < P.B, 0, P.k, xa);
-    for (int it = 0; it < total; it += 2) {
-      if (it + 1 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 1) % P.kchunks, P.k, xb);
-      if (!tc_convert_chunk(xa, it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status, abort_flag,
-                            P.wait_cycles))
-        break;
-      if (it + 1 >= total) break;
-      if (it + 2 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 2) % P.kchunks, P.k, xa);
-      if (!tc_convert_chunk(xb, it + 1, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status,
-                            abort_flag, P.wait_cycles))
-        break;
+    bool ok = true;
+    for (int t = 0; t < my_tiles && ok; ++t) {
+      const int64_t e = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * TC_M + r;
+      const TIn* row = A + e * (int64_t)P.k;
+      const int ib = t * total;
+      float xa[TC_KC], xb[TC_KC];
+      tc_load_chunk<TIn>(row, e < P.B, 0, P.k, xa);
+      for (int it = 0; it < total; it += 2) {
+        if (it + 1 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 1) % P.kchunks, P.k, xb);
+        if (!tc_convert_chunk(xa, ib + it, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status,
+                              abort_flag, P.wait_cycles)) {
+          ok = false;
+          break;
+        }
+        if (it + 1 >= total) break;
+        if (it + 2 < total) tc_load_chunk<TIn>(row, e < P.B, (it + 2) % P.kchunks, P.k, xa);
+        if (!tc_convert_chunk(xb, ib + it + 1, r, stage_base, stage_bytes, a_plane_bytes, empty, full_a, status,
+                              abort_flag, P.wait_cycles)) {
+          ok = false;
+          break;
+        }
+      }
     }
   } else {
     // ---------------- epilogue: one event per thread ----------------
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
     const int r = q * 32 + lane;
-    const int64_t e = e0 + r;
-    const TIn* row = A + e * (int64_t)P.k;
-    double acc = 0.0;
-    for (int ntile = 0; ntile < P.ntiles; ++ntile) {
-      const int b = ntile & 1;
-      const uint32_t buse = (uint32_t)(ntile >> 1);
-      // warp-uniform decision: tcgen05.ld below is .sync.aligned
-      const bool ready = mbar_wait(&dfull[b], buse & 1, status, abort_flag, P.wait_cycles);
-      if (!__all_sync(0xffffffffu, ready)) break;
-      tc_fence_after();
-      float part = 0.0f;
-      float an[16];
-      tc_load16<TIn>(row, e < P.B, ntile * P.nt, P.k, an);
-      for (int c0 = 0; c0 < P.nt; c0 += 16) {
-        float ac[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) ac[j] = an[j];
-        if (c0 + 16 < P.nt) tc_load16<TIn>(row, e < P.B, ntile * P.nt + c0 + 16, P.k, an);
-        float d[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.nt + c0), d);
-        const int m0 = ntile * P.nt + c0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) part = fmaf(ac[j], d[j], part);  // ac is 0 beyond k and B
-        if (Y && e < P.B) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (m0 + j < P.k) Y[e * (int64_t)P.k + m0 + j] = (TIn)(P.g * d[j]);
+    bool ok = true;
+    for (int t = 0; t < my_tiles && ok; ++t) {
+      const int64_t e = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * TC_M + r;
+      const TIn* row = A + e * (int64_t)P.k;
+      double acc = 0.0;
+      for (int ntile = 0; ntile < P.ntiles; ++ntile) {
+        const int g = t * P.ntiles + ntile;
+        const int b = g & 1;
+        const uint32_t buse = (uint32_t)(g >> 1);
+        // warp-uniform decision: tcgen05.ld below is .sync.aligned
+        const bool ready = mbar_wait(&dfull[b], buse & 1, status, abort_flag, P.wait_cycles);
+        if (!__all_sync(0xffffffffu, ready)) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        float part = 0.0f;
+        float an[16];
+        tc_load16<TIn>(row, e < P.B, ntile * P.nt, P.k, an);
+        for (int c0 = 0; c0 < P.nt; c0 += 16) {
+          float ac[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) ac[j] = an[j];
+          if (c0 + 16 < P.nt) tc_load16<TIn>(row, e < P.B, ntile * P.nt + c0 + 16, P.k, an);
+          float d[16];
+          tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * P.nt + c0), d);
+          const int m0 = ntile * P.nt + c0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) part = fmaf(ac[j], d[j], part);  // ac is 0 beyond k and B
+          if (Y && e < P.B) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (m0 + j < P.k) Y[e * (int64_t)P.k + m0 + j] = (TIn)(P.g * d[j]);
+          }
+        }
+        acc += (double)part;
+        tc_fence_before();
+        mbar_arrive(&dempty[b]);
       }
-      acc += (double)part;
-      tc_fence_before();
-      mbar_arrive(&dempty[b]);
+      if (e < P.B) {
+        const bool keep = ok && ((accept == nullptr) || (accept[e] != 0));
+        me2[e] = (keep && !*abort_flag) ? P.scale * acc : 0.0;
+      }
     }
-    if (e < P.B) {
-      const bool ok = (accept == nullptr) || (accept[e] != 0);
-      me2[e] = (ok && !*abort_flag) ? P.scale * acc : 0.0;
+    if (!ok) {
+      // the events of this CTA's remaining tiles get 0 (a wait gave up)
+      for (int t = 0; t < my_tiles; ++t) {
+        const int64_t e = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * TC_M + r;
+        if (e < P.B) me2[e] = 0.0;
+      }
     }
   }
 
@@ -625,7 +659,12 @@ cudaError_t launch_color_sum_tc(const ColourSumArgs& a, const bg_colormat* C, in
   const char* stall = std::getenv("BG_TC_TEST_STALL");
   P.stall_c = (stall && stall[0] == '1') ? 1 : 0;
   P.wait_cycles = P.stall_c ? kTestWaitCycles : kWaitCycles;
-  const unsigned blocks = (unsigned)((a.B + TC_M - 1) / TC_M);
+  // persistent CTAs: one per SM (a CTA fills the SM's shared memory), each
+  // looping over event tiles of 128
+  const int64_t tiles = (a.B + TC_M - 1) / TC_M;
+  if (tiles == 0) return cudaSuccess;
+  const int sms = device_sms();
+  const unsigned blocks = (unsigned)(sms > 0 && tiles > sms ? sms : tiles);
   // The staged amplitude path: FP32 amplitudes, one BF16 plane of C, a
   // tensor map for A, and room for at least two staging buffers.
   CUtensorMap amap;

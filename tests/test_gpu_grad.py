@@ -5,8 +5,11 @@ own |M|^2.
 Tolerances: FP64 path, per-event relative error of the gradient vector
 (Euclidean norm) below 1e-9 (the dual-number oracle is exact to rounding;
 the reverse sweep re-associates sums over up to 8! terms).  FP32 path:
-median below 1e-4 and 95 % below 1e-2 (the gradient is a difference of
-large contributions; its FP32 error is larger than that of |M|^2).
+median below 1e-5, 95 % below 1e-4, 99 % below 1e-3 and every event below
+5e-3, on 400 (n = 6) and 200 (n = 8) events (the gradient is a difference of
+large contributions, so its FP32 error is larger than that of |M|^2; measured
+at n = 6 / 8: median 7.8e-7 / 1.9e-6, 99 % 1.1e-4 / 2.8e-5, worst 5.0e-4 /
+4.5e-5).
 Central differences (h = 1e-6, FP64): agreement to 1e-6 of the gradient
 norm.  The per-event sums over orderings are taken in a fixed order, so
 repeated calls agree bit for bit; an upstream weight w changes the result
@@ -60,19 +63,23 @@ def test_grad_fp64_matches_dual_numbers(bg, oracle, n, B):
     plan.close()
 
 
-@pytest.mark.parametrize("n,B", [(6, 16), (8, 6)])
+@pytest.mark.parametrize("n,B", [(6, 400), (8, 200)])
 def test_grad_fp32_matches_dual_numbers(bg, oracle, n, B):
+    # the oracle's dual-number gradients on all host cores (each call is one
+    # event; ctypes releases the interpreter lock)
+    from concurrent.futures import ThreadPoolExecutor
     u, hel, ut, ht = dev_inputs(n, B, 110 + n)
     plan = plan_for(bg, n, B, bg.BG_F32, pt_min=-1.0)
     g = plan.grad(ut, ht).cpu().numpy()
-    rel = []
-    for e in range(B):
-        _, ref = oracle.me2_co_grad(n, u[e], hel[e], sqrt_s=SQRT_S)
-        rel.append(np.linalg.norm(g[e] - ref) / np.linalg.norm(ref))
-    rel = np.array(rel)
-    assert np.median(rel) < 1e-4
-    assert np.quantile(rel, 0.95) < 1e-2
     plan.close()
+    oracle.colour_matrix(n)
+    with ThreadPoolExecutor(oracle.n_cores()) as ex:
+        refs = list(ex.map(lambda e: oracle.me2_co_grad(n, u[e], hel[e], sqrt_s=SQRT_S)[1], range(B)))
+    rel = np.array([np.linalg.norm(g[e] - refs[e]) / np.linalg.norm(refs[e]) for e in range(B)])
+    assert np.median(rel) < 1e-5
+    assert np.quantile(rel, 0.95) < 1e-4
+    assert np.quantile(rel, 0.99) < 1e-3
+    assert rel.max() < 5e-3
 
 
 def test_grad_central_differences_fp64(bg):
