@@ -116,8 +116,8 @@ def device_sms(dev) -> int:
 
 def cs_mode_for(bg, n: int) -> int:
     """Colour-sum arithmetic per multiplicity: tensor cores (tcgen05) where
-    available (6 <= n <= 8), FP32 CUDA cores for the 6x6 matrix of n = 5."""
-    return bg.BG_CS_TC_BF16 if 6 <= n <= 8 else bg.BG_CS_F32
+    available (6 <= n <= 9), FP32 CUDA cores for the 6x6 matrix of n = 5."""
+    return bg.BG_CS_TC_BF16 if 6 <= n <= 9 else bg.BG_CS_F32
 
 
 def canonical_recursion_flops(n: int) -> int:
@@ -338,24 +338,6 @@ def run_ours(args) -> None:
 
     ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(4)] for n in NS}
     launches_per_step = 3 * len(NS)
-    # Rambo (FP64 pipe) runs on a side stream ahead of the recursions (FP32
-    # pipe), so that it overlaps them; the step still does all the work.
-    side = torch.cuda.Stream(dev)
-    ev_r = {n: torch.cuda.Event() for n in NS}
-    ev_end = torch.cuda.Event()
-
-    def step_overlap():
-        side.wait_event(ev_end)  # the previous step has consumed the momenta
-        for n in NS:
-            bg.momenta_rambo(n, U[n], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=side)
-            ev_r[n].record(side)
-        for n in NS:
-            stream.wait_event(ev_r[n])
-            bg.currents_co(n, P[n], HEL[n], prec=prec, sqrt_s=SQRT_S, amps=AMPS[n], stream=stream)
-            bg.color_sum(CM[n], AMPS[n], True, mode=csm(n), sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
-                         stream=stream)
-        ev_end.record(stream)
-
     def step(record: bool):
         for n in NS:
             if record:
@@ -380,7 +362,7 @@ def run_ours(args) -> None:
     tuned = {n: bg.autotune(bg.BG_ALGO_CO, n, prec, probe_batch=probe_batch, stream=stream)[0] for n in NS if n >= 6}
 
     for _ in range(args.warmup):
-        step_overlap()
+        step(False)
     torch.cuda.synchronize(dev)
     barrier()
 
@@ -391,9 +373,8 @@ def run_ours(args) -> None:
     kernel_ms = {n: [0.0, 0.0, 0.0] for n in NS}
     torch.cuda.synchronize(dev)
     t0.record(stream)
-    side.wait_event(t0)
     for _ in range(args.steps):
-        step_overlap()
+        step(False)
     t1.record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
@@ -522,8 +503,8 @@ def run_ours(args) -> None:
                 "tuned_variants": {str(n): v for n, v in tuned.items()}},
             "per_n": per_n,
             "kernel_ms_per_step": {f"n{n}": [round(x / args.steps, 4) for x in kernel_ms[n]] for n in NS},
-            "schedule": ("Rambo for all n on a side stream ahead of the recursions and colour sums (FP64 and FP32 "
-                         "pipes overlap); kernel_ms_per_step and kernel_share from the same step serialised"),
+            "schedule": ("one stream: Rambo, recursion, colour sum per n in turn; kernel_ms_per_step and "
+                         "kernel_share from the same step with CUDA events between the kernels"),
             "kernel_share": {k: round(v, 4) for k, v in shares.items()},
             "roofline": roof,
             "cpu_baseline": None,
