@@ -392,40 +392,52 @@ def run_ours(args) -> None:
             for j in range(3):
                 kernel_ms[n][j] += ev[n][j].elapsed_time(ev[n][j + 1])
 
-    # e2e: the public plan API with HOST buffers, copies inside the timed region
-    plans = {n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=prec, cs_mode=csm(n), hel_sampled=True)
-             for n in NS}
+    # e2e: the public plan API with HOST buffers, copies inside the timed region.
+    # Two sets of plans (and pinned output buffers) alternate between steps,
+    # one stream per multiplicity and set: the calls of step s+1 are issued
+    # before the host waits for the results of step s, so that the
+    # host-to-device copies of one step overlap the kernels of the other.
+    # Every step copies its inputs in and its |M|^2 out, and the host has
+    # every step's results before the clock stops.
+    plan_sets = [{n: bg.Plan(n, BATCH, SQRT_S, PT_MIN, prec=prec, cs_mode=csm(n), hel_sampled=True) for n in NS}
+                 for _ in range(2)]
     host_u = {n: U[n].cpu().pin_memory() for n in NS}
     host_h = {n: HEL[n].cpu().pin_memory() for n in NS}
-    host_m = {n: torch.empty((BATCH,), dtype=torch.float64).pin_memory() for n in NS}
-    d2h = sum(host_m[n].numel() * 8 for n in NS)
-    # one stream per multiplicity: the asynchronous calls overlap each plan's
-    # host<->device copies with the other plans' kernels; the host waits for
-    # every result at the end of each step
-    e2e_streams = {n: torch.cuda.Stream(dev) for n in NS}
+    host_m = [{n: torch.empty((BATCH,), dtype=torch.float64).pin_memory() for n in NS} for _ in range(2)]
+    d2h = sum(host_m[0][n].numel() * 8 for n in NS)
+    e2e_streams = [{n: torch.cuda.Stream(dev) for n in NS} for _ in range(2)]
 
-    def e2e_step():
-        for n in NS:
-            plans[n].me2(host_u[n], host_h[n], out=host_m[n], stream=e2e_streams[n], wait=False)
-        for n in NS:
-            e2e_streams[n].synchronize()
+    def e2e_issue(b):
+        for n in reversed(NS):  # the longest recursion first
+            plan_sets[b][n].me2(host_u[n], host_h[n], out=host_m[b][n], stream=e2e_streams[b][n], wait=False)
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+    def e2e_wait(b):
+        for n in NS:
+            e2e_streams[b][n].synchronize()
+
+    def e2e_run(steps):
+        for i in range(steps):
+            e2e_issue(i & 1)
+            if i > 0:
+                e2e_wait((i - 1) & 1)
+        e2e_wait((steps - 1) & 1)
+
+    e2e_run(max(2, args.warmup))
     torch.cuda.synchronize(dev)
     barrier()
     w0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    e2e_run(args.steps)
     torch.cuda.synchronize(dev)
     e2e_elapsed = max_over_ranks(time.perf_counter() - w0, dev)
     e2e_value = world * len(NS) * BATCH * args.steps / e2e_elapsed
     # the e2e results must equal the device-resident results
-    for n in NS:
-        if not torch.equal(host_m[n], ME2[n].cpu()):
-            raise RuntimeError(f"e2e |M|^2 differs from the device-resident run at n={n}")
-    for n in NS:
-        plans[n].close()
+    for b in range(2):
+        for n in NS:
+            if not torch.equal(host_m[b][n], ME2[n].cpu()):
+                raise RuntimeError(f"e2e |M|^2 differs from the device-resident run at n={n}")
+    for b in range(2):
+        for n in NS:
+            plan_sets[b][n].close()
     del host_u, host_h, host_m
 
     # roofline of the dominant kernel (the colour-ordered recursion at n = 8)
