@@ -6,6 +6,7 @@
 // row tiles of C, so each event's quadratic form is finished in registers
 // and written once (no atomics, no scratch memory, deterministic order).
 // TC is the arithmetic type of C A; the per-event sum is accumulated in FP64.
+// Colour matrices with k <= 24 take a one-thread-per-event kernel instead.
 #include "bg_internal.h"
 #include "device_common.cuh"
 
@@ -107,8 +108,59 @@ __global__ void __launch_bounds__(NT) color_sum_kernel(int64_t Bcap, const int64
   }
 }
 
+// Small colour matrices (k = 2, 6, 24: n = 4, 5, 6): one thread per event,
+// C in shared memory, the event's k amplitudes in registers.  The same
+// arithmetic per element as the tiled kernel: (C A)_a accumulated over b in
+// increasing order in TC, then sum_a A_a (C A)_a in FP64 (over a in
+// increasing order).  Consecutive threads read consecutive amplitude rows,
+// so the loads are coalesced.
+template <typename TIn, typename TC, int K>
+__global__ void __launch_bounds__(128) color_sum_small_kernel(int64_t Bcap, const int64_t* __restrict__ dB, int H,
+                                                              const TIn* __restrict__ A, const TC* __restrict__ C,
+                                                              double scale, const uint8_t* __restrict__ accept,
+                                                              double* __restrict__ me2, TIn* __restrict__ Y) {
+  __shared__ TC Cs[K * K];
+  for (int i = threadIdx.x; i < K * K; i += blockDim.x) Cs[i] = C[i];
+  __syncthreads();
+  const int64_t B = dB ? (*dB < Bcap ? *dB : Bcap) : Bcap;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  double s = 0.0;
+  for (int h = 0; h < H; ++h) {
+    const TIn* a = A + (e * H + h) * (int64_t)K;
+    TC x[K];
+#pragma unroll
+    for (int b = 0; b < K; ++b) x[b] = TC(a[b]);
+#pragma unroll 2
+    for (int i = 0; i < K; ++i) {
+      TC acc = TC(0);
+#pragma unroll
+      for (int b = 0; b < K; ++b) acc = fma(Cs[b * K + i], x[b], acc);
+      s += (double)a[i] * (double)acc;
+      if (Y) Y[(e * H + h) * (int64_t)K + i] = (TIn)acc;
+    }
+  }
+  const bool ok = (accept == nullptr) || (accept[e] != 0);
+  me2[e] = ok ? scale * s : 0.0;
+}
+
 template <typename TIn, typename TC>
 cudaError_t launch_cs(const ColourSumArgs& a, const TC* C, cudaStream_t s) {
+  if (a.k == 2 || a.k == 6 || a.k == 24) {
+    const int64_t blocks = (a.B + 127) / 128;
+    const TIn* A = static_cast<const TIn*>(a.amps);
+    TIn* Y = static_cast<TIn*>(a.Y);
+    if (a.k == 2)
+      color_sum_small_kernel<TIn, TC, 2><<<(unsigned)blocks, 128, 0, s>>>(a.B, a.dB, a.H, A, C, a.scale, a.accept,
+                                                                         a.me2, Y);
+    else if (a.k == 6)
+      color_sum_small_kernel<TIn, TC, 6><<<(unsigned)blocks, 128, 0, s>>>(a.B, a.dB, a.H, A, C, a.scale, a.accept,
+                                                                         a.me2, Y);
+    else
+      color_sum_small_kernel<TIn, TC, 24><<<(unsigned)blocks, 128, 0, s>>>(a.B, a.dB, a.H, A, C, a.scale,
+                                                                          a.accept, a.me2, Y);
+    return cudaGetLastError();
+  }
   const int64_t blocks = (a.B + TE - 1) / TE;
   color_sum_kernel<TIn, TC><<<(unsigned)blocks, NT, 0, s>>>(a.B, a.dB, a.H, a.k, static_cast<const TIn*>(a.amps), C,
                                                            a.scale, a.accept, a.me2, static_cast<TIn*>(a.Y));
