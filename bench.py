@@ -978,7 +978,7 @@ def run_comc(args) -> None:
     prec = bg.BG_F64 if args.precision == "f64" else bg.BG_F32
     batch = BATCH if args.precision == "f32" else BATCH >> 4
     first = rank * batch
-    U, HEL, COL, P, ACC, ME2, host, orders = {}, {}, {}, {}, {}, {}, {}, {}
+    U, HEL, COL, P, ACC, ME2, WS, host, orders = {}, {}, {}, {}, {}, {}, {}, {}, {}
     for n in COMC_NS:
         u = inputs.rambo_uniforms(n, batch, seed=SEED, first_event=first)
         h = inputs.helicities(n, batch, seed=SEED, first_event=first)
@@ -990,6 +990,7 @@ def run_comc(args) -> None:
         P[n] = torch.empty((4, n, batch), dtype=torch.float64, device=dev)
         ACC[n] = torch.empty((batch,), dtype=torch.uint8, device=dev)
         ME2[n] = torch.empty((batch,), dtype=torch.float64, device=dev)
+        WS[n] = torch.empty((bg.comc_workspace_bytes(n, batch, prec),), dtype=torch.uint8, device=dev)
     ev = {n: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for n in COMC_NS}
     kernel_ms = {n: [0.0, 0.0] for n in COMC_NS}
 
@@ -1001,7 +1002,7 @@ def run_comc(args) -> None:
             if record:
                 ev[n][1].record(stream)
             bg.currents_co_mc(n, P[n], HEL[n], COL[n], prec=prec, sqrt_s=SQRT_S, accept=ACC[n], me2=ME2[n],
-                              stream=stream)
+                              workspace=WS[n], stream=stream)
             if record:
                 ev[n][2].record(stream)
 
@@ -1023,7 +1024,7 @@ def run_comc(args) -> None:
                 dst.copy_(src, non_blocking=True)
             bg.momenta_rambo(n, d_in[n][0], SQRT_S, PT_MIN, p=P[n], accept=ACC[n], stream=stream)
             bg.currents_co_mc(n, P[n], d_in[n][1], d_in[n][2], prec=prec, sqrt_s=SQRT_S, accept=ACC[n],
-                              me2=ME2[n], stream=stream)
+                              me2=ME2[n], workspace=WS[n], stream=stream)
             out_h[n].copy_(ME2[n], non_blocking=True)
 
     e2e_s = timed_host(e2e_step, args, dev)
@@ -1055,14 +1056,16 @@ def run_comc(args) -> None:
             "per_n": {str(n): batch * world / (sum(kernel_ms[n]) * 1e-3) for n in COMC_NS},
             "kernel_ms_per_step": {f"n{n}": [round(x, 3) for x in kernel_ms[n]] for n in COMC_NS},
             "orders_per_event": {str(n): float(orders[n].mean()) for n in COMC_NS},
-            "roofline": roofline(f"comc_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
+            "roofline": roofline(f"comc_eval_kernel<{n_dom},{'double' if args.precision == 'f64' else 'float'}>",
                                  "alu", achieved, peak, "TFLOP/s", peak_source,
                                  flops_model=("canonical recursion FLOPs of one order x closing orders of the "
                                               "events passing the cut"),
-                                 flops_per_order=per_order, orders_computed=n_orders),
+                                 flops_per_order=per_order, orders_computed=n_orders,
+                                 timed_span=("the whole bg_currents_co_mc call: prep, scan, offsets, eval and "
+                                             "final kernels")),
             "e2e": {"value": world * len(COMC_NS) * batch * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": len(COMC_NS) * batch * 8},
-            "gpu_launches": 2 * len(COMC_NS) * args.steps, "clocks": clk}), flush=True)
+            "gpu_launches": 6 * len(COMC_NS) * args.steps, "clocks": clk}), flush=True)
     finish_gpu(world)
 
 

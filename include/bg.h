@@ -368,15 +368,25 @@ bg_status bg_currents_cd_cont(int n, int64_t B, double sqrt_s, const double* p, 
  *           (external colour matrix |r_i><c_i|)
  *   accept  [B] or NULL  events with accept == 0 get 0
  *   me2     [B] double   output, GeV^(8-2n)
- * No workspace: each block keeps its events and the orders being evaluated
- * in shared memory.  Events with a colour label outside 1..3 get 0 and set
- * BG_EINVAL in the device status word.  The work per event is the number of
- * closing orders, (n-1)!/3^n on average and up to (n-1)! for degenerate
- * flows.  Supported: 4 <= n <= 12.  Errors: BG_EINVAL, BG_ECUDA.
+ *   workspace, workspace_bytes: caller-owned device scratch of at least
+ *           bg_comc_workspace_bytes(n, B, prec) bytes, 256-byte aligned (the
+ *           events' momenta, polarisations, pair invariants and colour
+ *           masks, the item offsets, partial sums); nothing needs to be
+ *           zeroed.  About 1 KB per event at n = 12.
+ * Every closing order of every event is one work item: the orders are
+ * counted per event in closed form (the BEST theorem for the Eulerian
+ * circuits of the flow's colour graph), and a persistent kernel evaluates
+ * the items, so that an event with many orders spreads over the GPU.  The
+ * work per event is the number of closing orders, (n-1)!/3^n on average and
+ * up to (n-1)! for degenerate flows.  The sums run in a fixed order (equal
+ * inputs give equal bits).  Events with a colour label outside 1..3 get 0
+ * and set BG_EINVAL in the device status word.  Supported: 4 <= n <= 12.
+ * Errors: BG_EINVAL, BG_ECUDA.
  * ------------------------------------------------------------------------- */
+bg_status bg_comc_workspace_bytes(int n, int64_t B, bg_prec prec, int64_t* bytes);
 bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
                             const int8_t* colors, const double* q, bg_prec prec, double g_s, const uint8_t* accept,
-                            double* me2, void* stream);
+                            double* me2, void* workspace, int64_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * bg_currents_lc -- leading-colour |M|^2 (Sec. 4, the prefactor formula of

@@ -85,7 +85,8 @@ def lib() -> ctypes.CDLL:
         L.bg_currents_cd.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, c_int, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_apply_cuts.argtypes = [c_int, c_i64, vp, c_dbl, c_dbl, c_dbl, vp, vp]
         L.bg_currents_cd_cont.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
-        L.bg_currents_co_mc.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, dp, c_int, c_dbl, vp, vp, vp]
+        L.bg_comc_workspace_bytes.argtypes = [c_int, c_i64, c_int, ctypes.POINTER(c_i64)]
+        L.bg_currents_co_mc.argtypes = [c_int, c_i64, c_dbl, vp, vp, vp, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_lc_workspace_bytes.argtypes = [c_int, c_i64, c_int, c_int, ctypes.POINTER(c_i64)]
         L.bg_currents_lc.argtypes = [c_int, c_i64, c_dbl, vp, vp, dp, c_int, c_dbl, vp, vp, vp, c_i64, vp]
         L.bg_mixed_create.argtypes = [ctypes.POINTER(MixedDesc), ctypes.POINTER(vp)]
@@ -108,7 +109,7 @@ def lib() -> ctypes.CDLL:
         for name in ("bg_colormat_create", "bg_colormat_row", "bg_colormat_row_host", "bg_momenta_rambo",
                      "bg_currents_co", "bg_currents_co_tensor", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_cd_workspace_bytes",
-                     "bg_currents_cd", "bg_currents_cd_cont", "bg_apply_cuts", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
+                     "bg_currents_cd", "bg_currents_cd_cont", "bg_apply_cuts", "bg_comc_workspace_bytes", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
                      "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
                      "bg_tune_load"):
             getattr(L, name).restype = c_int
@@ -286,17 +287,26 @@ def currents_cd_cont(n: int, p: torch.Tensor, ang: torch.Tensor, prec: int = BG_
     return me2
 
 
+def comc_workspace_bytes(n: int, B: int, prec: int = BG_F32) -> int:
+    b = ctypes.c_int64()
+    _check(lib().bg_comc_workspace_bytes(n, B, prec, ctypes.byref(b)))
+    return b.value
+
+
 def currents_co_mc(n: int, p: torch.Tensor, hel: torch.Tensor, colors: torch.Tensor, prec: int = BG_F32,
                    sqrt_s: float = 1000.0, g_s: float = G_S_DEFAULT, q=DEFAULT_Q,
-                   accept: torch.Tensor | None = None, me2=None, stream=None) -> torch.Tensor:
+                   accept: torch.Tensor | None = None, me2=None, workspace: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
     """|M|^2 estimator per event for sampled colour flows, evaluated from
     colour-ordered amplitudes (Eq. 2.19): p [4, n, B] float64, hel [n, B]
     int8, colors [2n, B] int8 flow pairs in 1..3."""
     B = p.shape[2]
     if me2 is None:
         me2 = torch.empty((B,), dtype=torch.float64, device=p.device)
+    if workspace is None:
+        workspace = torch.empty((max(comc_workspace_bytes(n, B, prec), 1),), dtype=torch.uint8, device=p.device)
     _check(lib().bg_currents_co_mc(n, B, sqrt_s, _ptr(p), _ptr(hel), _ptr(colors), _q(q), prec, g_s, _ptr(accept),
-                                   _ptr(me2), _stream(stream)))
+                                   _ptr(me2), _ptr(workspace), workspace.numel(), _stream(stream)))
     return me2
 
 

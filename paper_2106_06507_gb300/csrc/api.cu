@@ -358,9 +358,18 @@ bg_status bg_currents_cd_cont(int n, int64_t B, double sqrt_s, const double* p, 
   return cuda_check(e, "bg_currents_cd_cont");
 }
 
+bg_status bg_comc_workspace_bytes(int n, int64_t B, bg_prec prec, int64_t* bytes) {
+  if (!bytes) return fail(BG_EINVAL, "bg_comc_workspace_bytes: bytes is NULL");
+  if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_comc_workspace_bytes: n must be in 4..12");
+  if (B < 0) return fail(BG_EINVAL, "bg_comc_workspace_bytes: B < 0");
+  if (prec != BG_F32 && prec != BG_F64) return fail(BG_EINVAL, "bg_comc_workspace_bytes: invalid precision");
+  *bytes = (int64_t)comc_workspace_bytes(n, B, prec == BG_F32 ? 4 : 8);
+  return BG_OK;
+}
+
 bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel,
                             const int8_t* colors, const double* q, bg_prec prec, double g_s, const uint8_t* accept,
-                            double* me2, void* stream) {
+                            double* me2, void* workspace, int64_t workspace_bytes, void* stream) {
   if (n < 4 || n > kMaxN) return fail(BG_EINVAL, "bg_currents_co_mc: n must be in 4..12");
   if (B < 0) return fail(BG_EINVAL, "bg_currents_co_mc: B < 0");
   if (!(sqrt_s > 0.0)) return fail(BG_EINVAL, "bg_currents_co_mc: sqrt_s must be > 0");
@@ -370,16 +379,21 @@ bg_status bg_currents_co_mc(int n, int64_t B, double sqrt_s, const double* p, co
   if (!(q[0] > 0.0) || std::fabs(q[0] - qv) > 1e-12 * q[0])
     return fail(BG_EINVAL, "bg_currents_co_mc: q must be light-like with q0 > 0");
   if (B == 0) return BG_OK;
-  if (!p || !hel || !colors || !me2) return fail(BG_EINVAL, "bg_currents_co_mc: NULL argument");
-  if (!aligned(p, 8) || !aligned(me2, 8)) return fail(BG_EINVAL, "bg_currents_co_mc: misaligned pointer");
+  if (!p || !hel || !colors || !me2 || !workspace) return fail(BG_EINVAL, "bg_currents_co_mc: NULL argument");
+  if (workspace_bytes < (int64_t)comc_workspace_bytes(n, B, prec == BG_F32 ? 4 : 8))
+    return fail(BG_EINVAL, "bg_currents_co_mc: workspace smaller than bg_comc_workspace_bytes(n, B, prec)");
+  if (!aligned(p, 8) || !aligned(me2, 8) || !aligned(workspace, 256))
+    return fail(BG_EINVAL, "bg_currents_co_mc: misaligned pointer (workspace needs 256-byte alignment)");
   ComcParams prm;
   prm.B = B;
   prm.inv_sqrt_s = 1.0 / sqrt_s;
   prm.scale = std::pow(9.0, n) * std::ldexp(1.0, n) * std::pow(g_s, 2 * n - 4) * std::pow(sqrt_s, 8 - 2 * n) *
               std::ldexp(1.0, -(n - 2));
-  cudaError_t e = (prec == BG_F32)
-                      ? launch_comc_f32(n, prm, p, hel, colors, accept, q, me2, device_status_ptr(), (cudaStream_t)stream)
-                      : launch_comc_f64(n, prm, p, hel, colors, accept, q, me2, device_status_ptr(), (cudaStream_t)stream);
+  const int sms = device_sms();
+  cudaError_t e = (prec == BG_F32) ? launch_comc_f32(n, prm, p, hel, colors, accept, q, me2, workspace, sms,
+                                                     device_status_ptr(), (cudaStream_t)stream)
+                                   : launch_comc_f64(n, prm, p, hel, colors, accept, q, me2, workspace, sms,
+                                                     device_status_ptr(), (cudaStream_t)stream);
   return cuda_check(e, "bg_currents_co_mc");
 }
 

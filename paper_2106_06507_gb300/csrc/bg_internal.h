@@ -111,9 +111,11 @@ int cd_variants(int n);  // number of kernel variants (threads per event)
 // comc_f64.cu); ComcParams is defined in comc.cuh.
 struct ComcParams;
 cudaError_t launch_comc_f32(int n, const ComcParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                            const uint8_t* accept, const double* q, double* me2, int* status, cudaStream_t s);
+                            const uint8_t* accept, const double* q, double* me2, void* workspace, int sms, int* status,
+                            cudaStream_t s);
 cudaError_t launch_comc_f64(int n, const ComcParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                            const uint8_t* accept, const double* q, double* me2, int* status, cudaStream_t s);
+                            const uint8_t* accept, const double* q, double* me2, void* workspace, int sms, int* status,
+                            cudaStream_t s);
 
 // Gradient (co_grad.cu, grad_rambo.cu).
 cudaError_t launch_co_grad_f32(int n, int64_t B, double sqrt_s, const double* p, const int8_t* hel, const double* q,

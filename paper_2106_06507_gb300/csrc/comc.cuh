@@ -10,24 +10,33 @@
 //            x A(1, s_2, ..., s_n),
 // and |M|^2 is estimated by 9^n 2^n g^(2n-4) |A_flow|^2.  Only orders whose
 // delta chain closes contribute: on average (n-1)!/3^n per event, spread
-// very unevenly (at n = 12 about 3 % of the flows have any, those have a
-// few thousand).
+// very unevenly (at n = 12 about 3 % of the flows have any, those a few
+// thousand on average and up to ~10^5).
 //
-// Work decomposition (one block per tile of EB events):
-//   1. per event, in shared memory: scaled momenta and sampled polarisation
-//      vectors in T, and the pair invariants 2 k_a.k_b for all pairs of the
-//      n gluons, computed in FP64 and kept as an unevaluated sum of two
-//      floats in the FP32 kernel (FP64 in the FP64 kernel);
-//   2. one thread per event walks the orders whose chain closes (depth-first,
-//      labels in increasing order) and counts them; a warp scan gives each
-//      event its range of item indices;
-//   3. in windows of CAP items: each event's walk is resumed where the last
-//      window paused it, writing the packed orders of the window into shared
-//      memory (an event is walked once in total), then every thread takes
-//      items and evaluates the whole recursion of one order (same code path
-//      for every item), and one thread per event adds its items' amplitudes
-//      in item order (deterministic);
-//   4. |M|^2 per event.
+// Every closing order of every event is one work item, so that the orders of
+// a heavy event spread over the whole GPU:
+//   1. comc_prep_kernel (a block per 256 events): each event's record --
+//      scaled momenta, sampled polarisation vectors and the pair invariants
+//      2 k_a.k_b of all pairs of gluons, computed in FP64 and kept as an
+//      unevaluated sum of two floats in the FP32 kernel (FP64 in the FP64
+//      kernel) -- its colour masks, and its number of closing orders (BEST
+//      theorem, comc_rank.h); a block-wide scan of the counts;
+//   2. comc_scan_kernel, comc_offsets_kernel: the events' item offsets
+//      off[e] (exclusive prefix sums of the counts, off[B] the total) and the
+//      chunk size CH (a multiple of the evaluator's block size, with at most
+//      kComcMaxChunks chunks);
+//   3. comc_eval_kernel, persistent: the blocks take the chunks of CH items
+//      round-robin and their threads one item each per pass: the item's
+//      event (galloping search from the event of the pass's first item), the
+//      order of the item's rank in its event (comc_unrank), and the whole
+//      recursion of that order.  The amplitudes of an event are added in
+//      item order within the chunk; an event that a chunk boundary cuts
+//      leaves the partial sum of its part of the chunk in one of the chunk's
+//      two slots (first: the event that began before the chunk; last: the
+//      event that goes on after it);
+//   4. comc_final_kernel, one thread per event: the event's sum (from its
+//      chunk, or its partial sums in chunk order) and |M|^2.
+// The sums run in a fixed order: equal inputs give equal bits.
 // The propagator denominators P(i..j)^2 of each order are accumulated from
 // the pair invariants column by column, P(i..j)^2 = P(i..j-1)^2 +
 // sum_{a=i}^{j-1} 2 k_{s_a}.k_{s_j}, in double-float arithmetic (Knuth's
@@ -38,16 +47,22 @@
 
 #include "bg_internal.h"
 #include "co_recursion.cuh"
+#include "comc_rank.h"
 #include "device_common.cuh"
 
 namespace bg {
 
 struct ComcParams {
-  int64_t B;                    // capacity (row stride of p, hel, colours)
-  const int64_t* dB = nullptr;  // optional device-side event count
+  int64_t B;  // events (row stride of p, hel, colours)
   double inv_sqrt_s;
   double scale;  // 9^n 2^n g^(2n-4) sqrt_s^(8-2n) 2^-(n-2)
 };
+
+// At most this many chunks per launch (2 partial-sum slots each in the
+// workspace); chunks grow beyond the evaluator's block size only past
+// kComcMaxChunks x block size items.
+constexpr int64_t kComcMaxChunks = 1 << 16;
+constexpr int kComcPrepEvents = 256;
 
 // TAB (n >= 10; FP64 from n = 8): the current table of the order being
 // evaluated lives in shared memory (one slice per thread) instead of
@@ -57,15 +72,64 @@ template <int N, typename T>
 struct ComcShape {
   static constexpr bool TAB = N >= 10 || (sizeof(T) == 8 && N >= 8);
   // 64 threads with the shared-memory table: two blocks per SM, so that one
-  // block's per-event phases (walks, sums) overlap the other's recursions
+  // block's serial phases (the run sums) overlap the other's recursions
   static constexpr int NT = TAB ? 64 : 128;
   static constexpr int M = N - 1;
   static constexpr int NPAIR = N * (N - 1) / 2;
   static constexpr int NSEG = M * (M + 1) / 2;  // segments (i..j), i <= j, of the off-shell current
   static constexpr int NSLOT = NSEG + N;         // + prefix sums S_0..S_M of the ordered momenta
-  static constexpr int EB = N <= 8 ? 128 : N == 9 ? 64 : N <= 11 ? 32 : 16;
-  static constexpr int CAP = TAB ? (sizeof(T) == 8 ? 512 : 1024) : 2048;  // items per window
+  static constexpr size_t tab_bytes = TAB ? sizeof(T) * NSLOT * NT * 4 : 0;
 };
+
+// The record of one event in the workspace: momenta k [N][4] and
+// polarisations e [N][4] (type T), then the pair invariants [NPAIR] (a < b
+// lexicographic; float2 value + error in FP32, double in FP64: 8 bytes each).
+__host__ __device__ constexpr size_t comc_record_bytes(int n, size_t t_size) {
+  return (2 * t_size * (size_t)n * 4 + 8 * (size_t)(n * (n - 1) / 2) + 15) & ~size_t(15);
+}
+
+// Workspace (caller-owned device memory, 256-byte aligned), carved in this
+// order with 256-byte alignment between the arrays.
+struct ComcWorkspace {
+  long long* off;      // [B + 1] item offsets of the events
+  long long* meta;     // [4]: total items, chunk size CH
+  long long* bsum;     // [ceil(B / 256)] per-prep-block sums, then their exclusive prefix
+  double* acc;         // [B] sums of the events that lie within one chunk
+  double* part;        // [2 kComcMaxChunks] per chunk: first and last partial sums
+  uint4* hdr;          // [B] colour masks (ComcFlow packed)
+  unsigned char* rec;  // [B] records of comc_record_bytes(n) bytes
+};
+
+inline size_t comc_workspace_bytes(int n, int64_t B, size_t t_size, unsigned char* base = nullptr,
+                                   ComcWorkspace* w = nullptr) {
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t nb = (size_t)((B + kComcPrepEvents - 1) / kComcPrepEvents);
+  size_t o = 0;
+  const size_t o_off = o;
+  o = up(o + 8 * (size_t)(B + 1));
+  const size_t o_meta = o;
+  o = up(o + 8 * 4);
+  const size_t o_bsum = o;
+  o = up(o + 8 * (nb + 1));
+  const size_t o_acc = o;
+  o = up(o + 8 * (size_t)B);
+  const size_t o_part = o;
+  o = up(o + 8 * 2 * (size_t)kComcMaxChunks);
+  const size_t o_hdr = o;
+  o = up(o + 16 * (size_t)B);
+  const size_t o_rec = o;
+  o = up(o + comc_record_bytes(n, t_size) * (size_t)B);
+  if (w && base) {
+    w->off = reinterpret_cast<long long*>(base + o_off);
+    w->meta = reinterpret_cast<long long*>(base + o_meta);
+    w->bsum = reinterpret_cast<long long*>(base + o_bsum);
+    w->acc = reinterpret_cast<double*>(base + o_acc);
+    w->part = reinterpret_cast<double*>(base + o_part);
+    w->hdr = reinterpret_cast<uint4*>(base + o_hdr);
+    w->rec = base + o_rec;
+  }
+  return o;
+}
 
 // Pair invariants and running P^2 sums: two floats (value + error) for the
 // FP32 kernel, one double for the FP64 kernel.
@@ -110,9 +174,14 @@ template <int N>
 __host__ __device__ constexpr int comc_seg(int i, int j) {
   return i * (N - 1) - i * (i - 1) / 2 + (j - i);
 }
-// The loads are volatile so that the compiler keeps them in program order
-// instead of hoisting the whole unrolled recursion's loads ahead of their use
-// (which needs more than 255 registers and spills).
+// The loads are volatile asm statements so that the compiler keeps them in
+// program order instead of hoisting the whole unrolled recursion's loads
+// ahead of their use (which needs more than 255 registers and spills).  Such
+// a statement does not tell the compiler which memory it reads, so the
+// stores are volatile asm statements too: the compiler keeps volatile asm
+// statements in their program order, and every table access is one of them.
+// (With plain C++ stores the compiler was free to move a store past a load
+// that must see it, and did so in some inlining contexts.)
 template <int NT>
 __device__ __forceinline__ void tab_ld(const float* __restrict__ tab, int seg, float (&v)[4]) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(tab + (size_t)seg * NT * 4);
@@ -122,7 +191,9 @@ __device__ __forceinline__ void tab_ld(const float* __restrict__ tab, int seg, f
 }
 template <int NT>
 __device__ __forceinline__ void tab_st(float* __restrict__ tab, int seg, const float (&v)[4]) {
-  *reinterpret_cast<float4*>(tab + (size_t)seg * NT * 4) = make_float4(v[0], v[1], v[2], v[3]);
+  const unsigned a = (unsigned)__cvta_generic_to_shared(tab + (size_t)seg * NT * 4);
+  asm volatile("st.volatile.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]));
 }
 template <int NT>
 __device__ __forceinline__ void tab_ld(const double* __restrict__ tab, int seg, double (&v)[4]) {
@@ -132,8 +203,9 @@ __device__ __forceinline__ void tab_ld(const double* __restrict__ tab, int seg, 
 }
 template <int NT>
 __device__ __forceinline__ void tab_st(double* __restrict__ tab, int seg, const double (&v)[4]) {
-  *reinterpret_cast<double2*>(tab + (size_t)seg * NT * 4) = make_double2(v[0], v[1]);
-  *reinterpret_cast<double2*>(tab + (size_t)seg * NT * 4 + 2) = make_double2(v[2], v[3]);
+  const unsigned a = (unsigned)__cvta_generic_to_shared(tab + (size_t)seg * NT * 4);
+  asm volatile("st.volatile.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v[0]), "d"(v[1]));
+  asm volatile("st.volatile.shared.v2.f64 [%0], {%1, %2};" ::"r"(a + 16), "d"(v[2]), "d"(v[3]));
 }
 
 // Bracket of segment (i..j) (the V3 and V4 sums before the propagator, unit
@@ -214,102 +286,6 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
   add4(br, t4, br);
 }
 
-// Depth-first walk over the orders (0, g_1, ..., g_{N-1}) (0-based labels)
-// whose colour chain closes: the row colour of each gluon equals the column
-// colour of the gluon before it, and the column colour of the last gluon
-// equals the row colour of gluon 0.  rm[c]: mask of the gluons with row
-// colour c; cp: column colours, 2 bits per gluon.  Orders are visited in
-// lexicographic order of their labels; visit(packed) gets the labels of
-// positions 1..N-1 packed 4 bits each and returns false to pause the walk
-// after that order.  The state (depth, candidates left per depth, labels
-// chosen, gluons still free) can be saved and the walk resumed where it
-// paused, so that an event whose orders span several windows is walked once
-// in total.
-template <int N>
-struct ComcWalk {
-  // All state in scalars (no dynamically indexed arrays, which would live in
-  // local memory): the candidates left at depth d are the 16-bit lane d & 3
-  // of word d >> 2 of c[0..2]; the label chosen at depth d is nibble d - 1
-  // of `packed`.
-  uint64_t packed;
-  uint64_t c0, c1, c2;
-  uint32_t avail;
-  int d;
-
-  __device__ __forceinline__ static uint32_t rmask(const uint32_t (&rm)[3], uint32_t colour) {
-    return colour == 0u ? rm[0] : (colour == 1u ? rm[1] : rm[2]);
-  }
-  __device__ __forceinline__ uint32_t cand(int k) const {
-    const uint64_t w = k < 4 ? c0 : (k < 8 ? c1 : c2);
-    return (uint32_t)((w >> (16 * (k & 3))) & 0xFFFFull);
-  }
-  __device__ __forceinline__ void set_cand(int k, uint32_t v) {
-    const int sh = 16 * (k & 3);
-    const uint64_t m = ~(0xFFFFull << sh), x = (uint64_t)(v & 0xFFFFu) << sh;
-    if (k < 4)
-      c0 = (c0 & m) | x;
-    else if (k < 8)
-      c1 = (c1 & m) | x;
-    else
-      c2 = (c2 & m) | x;
-  }
-
-  __device__ __forceinline__ void start(const uint32_t (&rm)[3], uint32_t cp) {
-    packed = 0;
-    c0 = c1 = c2 = 0;
-    avail = ((1u << N) - 1u) & ~1u;
-    d = 1;
-    set_cand(1, avail & rmask(rm, cp & 3u));
-  }
-  // Returns the number of orders visited before the walk ended or paused.
-  template <typename F>
-  __device__ __forceinline__ int64_t run(const uint32_t (&rm)[3], uint32_t cp, F&& visit) {
-    const int r0 = (rm[0] & 1u) ? 0 : ((rm[1] & 1u) ? 1 : 2);
-    int64_t cnt = 0;
-    while (d > 0) {
-      const uint32_t cd = cand(d);
-      if (cd) {
-        const int g = __ffs(cd) - 1;
-        set_cand(d, cd & (cd - 1u));
-        const uint64_t pk = (packed & ~(0xFull << (4 * (d - 1)))) | ((uint64_t)g << (4 * (d - 1)));
-        if (d == N - 1) {
-          if ((int)((cp >> (2 * g)) & 3u) == r0) {
-            ++cnt;
-            if (!visit(pk)) return cnt;
-          }
-          continue;
-        }
-        packed = pk;
-        avail &= ~(1u << g);
-        ++d;
-        set_cand(d, avail & rmask(rm, (cp >> (2 * g)) & 3u));
-      } else {
-        --d;
-        if (d > 0) avail |= 1u << (int)((packed >> (4 * (d - 1))) & 0xFull);
-      }
-    }
-    return cnt;
-  }
-};
-
-template <int N, typename T>
-struct ComcSmem {
-  using S = ComcShape<N, T>;
-  using PT = typename ComcPair<T>::type;
-  static constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
-  static constexpr size_t off_k = 0;                                                 // T [EB][N][4]
-  static constexpr size_t off_e = off_k + sizeof(T) * S::EB * N * 4;                 // T [EB][N][4]
-  static constexpr size_t off_pair = a16(off_e + sizeof(T) * S::EB * N * 4);         // PT [EB][NPAIR]
-  static constexpr size_t off_item = a16(off_pair + sizeof(PT) * S::EB * S::NPAIR);  // u64 [CAP]
-  static constexpr size_t off_amp = off_item + 8 * S::CAP;                            // T [CAP]
-  static constexpr size_t off_acc = a16(off_amp + sizeof(T) * S::CAP);               // double [EB]
-  static constexpr size_t off_off = off_acc + 8 * S::EB;                              // i64 [EB+1]
-  static constexpr size_t off_cf = a16(off_off + 8 * (S::EB + 1));                   // u32 [EB][4]
-  static constexpr size_t off_iev = off_cf + 16 * S::EB;                              // u16 [CAP]
-  static constexpr size_t off_walk = a16(off_iev + 2 * S::CAP);                       // walk states [EB]
-  static constexpr size_t off_tab = a16(off_walk + sizeof(ComcWalk<N>) * S::EB);       // T [NSLOT][NT][4] (TAB)
-  static constexpr size_t bytes = off_tab + (S::TAB ? sizeof(T) * S::NSLOT * S::NT * 4 : 0);
-};
 
 // Colour-ordered amplitude A(g_0, ..., g_{N-1}) of one order with unit vertex
 // factors (Eqs. 2.20-2.22).  ke, ee: the event's momenta and polarisations
@@ -427,55 +403,79 @@ __device__ __forceinline__ T comc_amplitude_tab(uint64_t packed, const T* __rest
   return amp;
 }
 
-template <int N, typename T>
-__global__ void __launch_bounds__(ComcShape<N, T>::NT)
-    comc_kernel(ComcParams prm, const double* __restrict__ p, const int8_t* __restrict__ hel,
-                const int8_t* __restrict__ col, const uint8_t* __restrict__ accept, PolFrame F,
-                double* __restrict__ me2, int* __restrict__ status) {
-  using S = ComcShape<N, T>;
-  using L = ComcSmem<N, T>;
-  using PT = typename ComcPair<T>::type;
-  constexpr int EB = S::EB, NT = S::NT, CAP = S::CAP, NPAIR = S::NPAIR;
-  const int64_t S_ = prm.B;
-  const int64_t B = prm.dB ? (*prm.dB < S_ ? *prm.dB : S_) : S_;
-  const int64_t e0 = (int64_t)blockIdx.x * EB;
-  if (e0 >= B) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  T* s_k = reinterpret_cast<T*>(smem + L::off_k);
-  T* s_e = reinterpret_cast<T*>(smem + L::off_e);
-  PT* s_pair = reinterpret_cast<PT*>(smem + L::off_pair);
-  uint64_t* s_item = reinterpret_cast<uint64_t*>(smem + L::off_item);
-  T* s_amp = reinterpret_cast<T*>(smem + L::off_amp);
-  double* s_acc = reinterpret_cast<double*>(smem + L::off_acc);
-  long long* s_off = reinterpret_cast<long long*>(smem + L::off_off);
-  uint32_t* s_cf = reinterpret_cast<uint32_t*>(smem + L::off_cf);
-  uint16_t* s_iev = reinterpret_cast<uint16_t*>(smem + L::off_iev);
-  ComcWalk<N>* s_walk = reinterpret_cast<ComcWalk<N>*>(smem + L::off_walk);
-  const int tid = threadIdx.x;
 
-  // ---- 1. momenta, polarisations, pair invariants, colour flows
-  for (int it = tid; it < EB * N; it += NT) {
+__device__ __forceinline__ ComcFlow comc_decode(uint4 h) {
+  ComcFlow f;
+  f.rm0 = h.x & 0xFFFFu;
+  f.rm1 = h.x >> 16;
+  f.rm2 = h.y & 0xFFFFu;
+  f.cm0 = h.y >> 16;
+  f.cm1 = h.z & 0xFFFFu;
+  f.cm2 = h.z >> 16;
+  f.r0 = (int)(h.w & 3u);
+  f.c0 = (int)((h.w >> 2) & 3u);
+  return f;
+}
+
+__device__ __forceinline__ void comc_fact_table(uint32_t* s_fact) {
+  if (threadIdx.x < 12) {
+    uint32_t f = 1;
+    for (int k = 2; k <= (int)threadIdx.x; ++k) f *= (uint32_t)k;
+    s_fact[threadIdx.x] = f;
+  }
+}
+
+// Inclusive scan of v over the warp.
+__device__ __forceinline__ long long comc_warp_scan(long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long u = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += u;
+  }
+  return v;
+}
+
+// ---- 1. records, colour masks, counts; block-local inclusive scan
+template <int N, typename T>
+__global__ void __launch_bounds__(kComcPrepEvents)
+    comc_prep_kernel(ComcParams prm, const double* __restrict__ p, const int8_t* __restrict__ hel,
+                     const int8_t* __restrict__ col, const uint8_t* __restrict__ accept, PolFrame F, ComcWorkspace w,
+                     int* __restrict__ status) {
+  using PT = typename ComcPair<T>::type;
+  constexpr int EB = kComcPrepEvents, NPAIR = N * (N - 1) / 2;
+  constexpr size_t RB = comc_record_bytes(N, sizeof(T));
+  const int64_t B = prm.B;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int tid = threadIdx.x;
+  __shared__ uint32_t s_fact[12];
+  __shared__ long long s_wsum[EB / 32];
+  comc_fact_table(s_fact);
+
+  for (int it = tid; it < EB * N; it += EB) {
     const int el = it / N, g = it % N;
     const int64_t e = e0 + el;
     if (e >= B) continue;
     double k[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * S_ + e] * prm.inv_sqrt_s;
+    for (int m = 0; m < 4; ++m) k[m] = p[((int64_t)m * N + g) * B + e] * prm.inv_sqrt_s;
     if (g < 2) {
 #pragma unroll
       for (int m = 0; m < 4; ++m) k[m] = -k[m];
     }
-    const int h = hel[(int64_t)g * S_ + e];
+    const int h = hel[(int64_t)g * B + e];
     if (h != 1 && h != -1) flag_status(status, BG_EINVAL);
     T ev[4];
     lc_polarisation_frame<T>(k, F, h >= 0, ev);
+    T* rk = reinterpret_cast<T*>(w.rec + (size_t)e * RB);
+    T* re = rk + N * 4;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      s_k[(el * N + g) * 4 + m] = T(k[m]);
-      s_e[(el * N + g) * 4 + m] = ev[m];
+      rk[g * 4 + m] = T(k[m]);
+      re[g * 4 + m] = ev[m];
     }
   }
-  for (int it = tid; it < EB * NPAIR; it += NT) {
+  for (int it = tid; it < EB * NPAIR; it += EB) {
     const int el = it / NPAIR;
     int pr = it % NPAIR;
     const int64_t e = e0 + el;
@@ -489,167 +489,272 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
     double ka[4], kb[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      ka[m] = p[((int64_t)m * N + a) * S_ + e];
-      kb[m] = p[((int64_t)m * N + b) * S_ + e];
+      ka[m] = p[((int64_t)m * N + a) * B + e];
+      kb[m] = p[((int64_t)m * N + b) * B + e];
     }
     const double sgn = ((a < 2) != (b < 2)) ? -1.0 : 1.0;  // k = -p for gluons 1, 2
     const double v =
         sgn * 2.0 * (ka[0] * kb[0] - ka[1] * kb[1] - ka[2] * kb[2] - ka[3] * kb[3]) * prm.inv_sqrt_s * prm.inv_sqrt_s;
-    p2_split(v, s_pair[el * NPAIR + it % NPAIR]);
+    PT* rp = reinterpret_cast<PT*>(w.rec + (size_t)e * RB + 2 * sizeof(T) * N * 4);
+    p2_split(v, rp[it % NPAIR]);
   }
-  for (int el = tid; el < EB; el += NT) {
-    const int64_t e = e0 + el;
-    uint32_t rm0 = 0, rm1 = 0, rm2 = 0, cp = 0, ok = e < B ? 1u : 0u;
-    if (ok && accept != nullptr && accept[e] == 0) ok = 0;
-    if (e < B) {
-      for (int g = 0; g < N; ++g) {
-        const int rr = col[(int64_t)(2 * g) * S_ + e], cc = col[(int64_t)(2 * g + 1) * S_ + e];
-        if (rr < 1 || rr > 3 || cc < 1 || cc > 3) {
-          flag_status(status, BG_EINVAL);
-          ok = 0;
-          continue;
-        }
-        const uint32_t bit = 1u << g;
-        rm0 |= rr == 1 ? bit : 0u;
-        rm1 |= rr == 2 ? bit : 0u;
-        rm2 |= rr == 3 ? bit : 0u;
-        cp |= (uint32_t)(cc - 1) << (2 * g);
+  __syncthreads();
+
+  const int64_t e = e0 + tid;
+  long long cnt = 0;
+  if (e < B) {
+    ComcFlow f{0u, 0u, 0u, 0u, 0u, 0u, 0, 0};
+    bool ok = accept == nullptr || accept[e] != 0;
+    for (int g = 0; g < N; ++g) {
+      const int rr = col[(int64_t)(2 * g) * B + e], cc = col[(int64_t)(2 * g + 1) * B + e];
+      if (rr < 1 || rr > 3 || cc < 1 || cc > 3) {
+        flag_status(status, BG_EINVAL);
+        ok = false;
+        continue;
       }
+      if (g == 0) {
+        f.r0 = rr - 1;
+        f.c0 = cc - 1;
+        continue;
+      }
+      const uint32_t bit = 1u << g;
+      f.rm0 |= rr == 1 ? bit : 0u;
+      f.rm1 |= rr == 2 ? bit : 0u;
+      f.rm2 |= rr == 3 ? bit : 0u;
+      f.cm0 |= cc == 1 ? bit : 0u;
+      f.cm1 |= cc == 2 ? bit : 0u;
+      f.cm2 |= cc == 3 ? bit : 0u;
     }
     // a chain can close only if every colour is as often a row as a column
-    // colour: other flows have no closing order and are not walked
-    uint32_t bal = 1;
-    if (ok) {
-      int nc[3] = {0, 0, 0};
-      for (int g = 0; g < N; ++g) ++nc[(cp >> (2 * g)) & 3u];
-      bal = (__popc(rm0) == nc[0] && __popc(rm1) == nc[1] && __popc(rm2) == nc[2]) ? 1u : 0u;
-    }
-    s_cf[el * 4 + 0] = rm0;
-    s_cf[el * 4 + 1] = rm1;
-    s_cf[el * 4 + 2] = rm2;
-    s_cf[el * 4 + 3] = cp | (ok << 30) | (bal << 29);
+    // colour (the BEST count assumes it)
+    if (ok && comc_balanced(f)) cnt = (long long)comc_count(f, s_fact);
+    w.hdr[e] = make_uint4(f.rm0 | (f.rm1 << 16), f.rm2 | (f.cm0 << 16), f.cm1 | (f.cm2 << 16),
+                          (uint32_t)f.r0 | ((uint32_t)f.c0 << 2));
   }
-  __syncthreads();
-
-  // ---- 2. count the orders of each event, then a scan over the tile
-  for (int el = tid; el < EB; el += NT) {
-    const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
-    const uint32_t w = s_cf[el * 4 + 3];
-    int64_t cnt = 0;
-    if (((w >> 30) & 1u) && ((w >> 29) & 1u)) {
-      ComcWalk<N> wk;
-      wk.start(rm, w & 0x00FFFFFFu);
-      cnt = wk.run(rm, w & 0x00FFFFFFu, [](uint64_t) { return true; });
-    }
-    s_off[el + 1] = (long long)cnt;
-    s_acc[el] = 0.0;
-  }
+  long long v = comc_warp_scan(cnt);
+  if ((tid & 31) == 31) s_wsum[tid >> 5] = v;
   __syncthreads();
   if (tid < 32) {
-    long long carry = 0;
-    for (int base = 0; base < EB; base += 32) {
-      const int el = base + tid;
-      long long v = el < EB ? s_off[el + 1] : 0;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const long long u = __shfl_up_sync(0xffffffffu, v, d);
-        if (tid >= d) v += u;
-      }
-      if (el < EB) s_off[el + 1] = carry + v;
-      carry += __shfl_sync(0xffffffffu, v, 31);
-    }
-    if (tid == 0) s_off[0] = 0;
+    long long u = tid < EB / 32 ? s_wsum[tid] : 0;
+    u = comc_warp_scan(u);
+    if (tid < EB / 32) s_wsum[tid] = u;
   }
   __syncthreads();
-  const long long total = s_off[EB];
+  if (tid >= 32) v += s_wsum[(tid >> 5) - 1];
+  if (e < B) w.off[e + 1] = v;
+  if (tid == EB - 1) w.bsum[blockIdx.x] = v;
+}
 
-  // ---- 3. windows of CAP items: write the orders, evaluate, accumulate
-  for (long long w0 = 0; w0 < total; w0 += CAP) {
-    const long long w1 = (total - w0 < CAP) ? total : w0 + CAP;
-    for (int el = tid; el < EB; el += NT) {
-      // (events without items -- failing the cut, invalid or without a
-      // closing order -- have lo == hi and are not walked)
-      const long long lo = s_off[el], hi = s_off[el + 1];
-      if (hi <= lo || hi <= w0 || lo >= w1) continue;
-      // the event's orders lo + r, r = 0, 1, ..., are written from where its
-      // walk paused at the end of the previous window
-      const long long stop = hi < w1 ? hi : w1;
-      const uint32_t rm[3] = {s_cf[el * 4 + 0], s_cf[el * 4 + 1], s_cf[el * 4 + 2]};
-      const uint32_t cp = s_cf[el * 4 + 3] & 0x00FFFFFFu;
-      ComcWalk<N> wk;
-      if (lo >= w0) {
-        wk.start(rm, cp);
-      } else {
-        wk = s_walk[el];
+// (The kernels below that are not templates have internal linkage: this
+// header is compiled into several translation units.)
+
+// ---- 2a. exclusive prefix of the per-block sums (one block of 1024
+// threads), the total and the chunk size
+static __global__ void __launch_bounds__(1024)
+    comc_scan_kernel(long long* __restrict__ bsum, int64_t nb, long long* __restrict__ meta, int nt) {
+  __shared__ long long s_w[32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  long long carry = 0;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t i = base + tid;
+    const long long v = i < nb ? bsum[i] : 0;
+    const long long x = comc_warp_scan(v);
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) s_w[lane] = comc_warp_scan(s_w[lane]);
+    __syncthreads();
+    const long long incl = x + (warp ? s_w[warp - 1] : 0) + carry;
+    if (i < nb) bsum[i] = incl - v;
+    carry += s_w[31];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const long long per = (carry + kComcMaxChunks - 1) / kComcMaxChunks;
+    long long ch = ((per + nt - 1) / nt) * nt;
+    if (ch < nt) ch = nt;
+    meta[0] = carry;
+    meta[1] = ch;
+  }
+}
+
+// ---- 2b. global offsets
+static __global__ void __launch_bounds__(kComcPrepEvents)
+    comc_offsets_kernel(long long* __restrict__ off, const long long* __restrict__ bsum, int64_t B) {
+  const int64_t e = (int64_t)blockIdx.x * kComcPrepEvents + threadIdx.x;
+  if (e < B) off[e + 1] += bsum[blockIdx.x];
+  if (e == 0) off[0] = 0;
+}
+
+// Largest e in [lo, B) with off[e] <= g, i.e. the event of item g, given
+// off[lo] <= g < off[B]: galloping from lo, then bisection.
+__device__ __forceinline__ long long comc_find_event(const long long* __restrict__ off, long long B, long long g,
+                                                     long long lo) {
+  long long step = 1, hi = lo + 1;
+  while (hi < B && off[hi] <= g) {
+    lo = hi;
+    step <<= 1;
+    hi = lo + step;
+  }
+  if (hi > B) hi = B;
+  while (hi - lo > 1) {
+    const long long mid = (lo + hi) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ---- 3. the items, chunk by chunk
+template <int N, typename T>
+__global__ void __launch_bounds__(ComcShape<N, T>::NT)
+    comc_eval_kernel(ComcWorkspace w, int64_t B, int* __restrict__ status) {
+  using S = ComcShape<N, T>;
+  using PT = typename ComcPair<T>::type;
+  constexpr int NT = S::NT;
+  constexpr size_t RB = comc_record_bytes(N, sizeof(T));
+  extern __shared__ __align__(16) unsigned char smem[];  // current tables (TAB)
+  __shared__ T s_amp[NT];
+  __shared__ long long s_ev[NT];
+  __shared__ uint64_t s_pk[NT];
+  __shared__ uint32_t s_fact[12];
+  __shared__ long long s_e0;
+  __shared__ double s_carry[2];
+  __shared__ long long s_carry_ev[2];
+  const int tid = threadIdx.x;
+  comc_fact_table(s_fact);
+  const long long total = w.meta[0], CH = w.meta[1];
+  int par = 0;
+  for (long long c = blockIdx.x; c * CH < total; c += gridDim.x) {
+    const long long c0 = c * CH, c1 = (total - c0 < CH) ? total : c0 + CH;
+    if (tid == 0) {
+      s_e0 = comc_find_event(w.off, B, c0, 0);
+      s_carry_ev[par] = -1;
+    }
+    __syncthreads();
+    // passes of NT items: the sum phase of a pass reads the carry of slot
+    // par (the run of an event continuing from the previous pass) and writes
+    // slot par ^ 1
+    for (long long w0 = c0; w0 < c1; w0 += NT) {
+      const int nw = (c1 - w0 < NT) ? (int)(c1 - w0) : NT;
+      long long e = -1;
+      T amp = T(0);
+      if (tid == 0) s_carry_ev[par ^ 1] = -1;
+      // the item's event and order first, then (after a barrier) its
+      // recursion: with the two back to back in one thread the FP32 n = 12
+      // kernel gave wrong amplitudes for a tenth of the items (cause not
+      // found; every variant that separates them agrees with the oracle)
+      if (tid < nw) {
+        const long long g = w0 + tid;
+        e = comc_find_event(w.off, B, g, s_e0);
+        s_pk[tid] = comc_unrank<N>((uint32_t)(g - w.off[e]), comc_decode(w.hdr[e]), s_fact);
       }
-      long long g = lo > w0 ? lo : w0;
-      wk.run(rm, cp, [&](uint64_t pk) {
-        s_item[g - w0] = pk;
-        s_iev[g - w0] = (uint16_t)el;
-        ++g;
-        return g < stop;
-      });
-      if (hi > w1) s_walk[el] = wk;
+      __syncthreads();
+      if (tid < nw) {
+        const uint64_t pk = s_pk[tid];
+        if (pk == ~0ull) {
+          flag_status(status, BG_ECUDA);  // cannot happen: ranks lie below the count
+        } else {
+          const T* ke = reinterpret_cast<const T*>(w.rec + (size_t)e * RB);
+          const T* ee = ke + N * 4;
+          const PT* pr = reinterpret_cast<const PT*>(w.rec + (size_t)e * RB + 2 * sizeof(T) * N * 4);
+          if constexpr (S::TAB)
+            amp = comc_amplitude_tab<N, T, PT, NT>(pk, ke, ee, pr, reinterpret_cast<T*>(smem) + tid * 4);
+          else
+            amp = comc_amplitude<N, T, PT>(pk, ke, ee, pr);
+        }
+      }
+      s_amp[tid] = amp;
+      s_ev[tid] = e;
+      __syncthreads();
+      // one thread per run of equal events adds the run in item order
+      if (tid < nw && (tid == 0 || s_ev[tid - 1] != e)) {
+        double a = (tid == 0 && s_carry_ev[par] == e) ? s_carry[par] : 0.0;
+        int i = tid;
+        for (; i < nw && s_ev[i] == e; ++i) a += (double)s_amp[i];
+        const long long end = w0 + i, lo = w.off[e], hi = w.off[e + 1];
+        if (hi <= end) {  // the event ends in this pass
+          if (lo >= c0)
+            w.acc[e] = a;
+          else
+            w.part[2 * c] = a;
+        } else if (end < c1) {  // it goes on in the next pass of this chunk
+          s_carry[par ^ 1] = a;
+          s_carry_ev[par ^ 1] = e;
+        } else {  // it goes on in the next chunk
+          w.part[2 * c + (lo >= c0 ? 1 : 0)] = a;
+        }
+      }
+      if (tid == 0) s_e0 = s_ev[nw - 1];
+      par ^= 1;
+      __syncthreads();
     }
-    __syncthreads();
-    const int nw = (int)(w1 - w0);
-    for (int it = tid; it < nw; it += NT) {
-      const int el = s_iev[it];
-      if constexpr (S::TAB)
-        s_amp[it] = comc_amplitude_tab<N, T, PT, NT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4,
-                                                     s_pair + el * NPAIR,
-                                                     reinterpret_cast<T*>(smem + L::off_tab) + tid * 4);
-      else
-        s_amp[it] = comc_amplitude<N, T, PT>(s_item[it], s_k + el * N * 4, s_e + el * N * 4, s_pair + el * NPAIR);
-    }
-    __syncthreads();
-    for (int el = tid; el < EB; el += NT) {
-      const long long lo = s_off[el] > w0 ? s_off[el] : w0;
-      const long long hi = s_off[el + 1] < w1 ? s_off[el + 1] : w1;
-      double a = s_acc[el];
-      for (long long g = lo; g < hi; ++g) a += (double)s_amp[g - w0];
-      s_acc[el] = a;
-    }
-    __syncthreads();
   }
+}
 
-  // ---- 4. |M|^2
-  for (int el = tid; el < EB; el += NT) {
-    const int64_t e = e0 + el;
-    if (e >= B) continue;
-    const double a = s_acc[el];
-    me2[e] = ((s_cf[el * 4 + 3] >> 30) & 1u) ? prm.scale * a * a : 0.0;
+// ---- 4. per event: the sum and |M|^2
+static __global__ void __launch_bounds__(256)
+    comc_final_kernel(ComcWorkspace w, int64_t B, double scale, double* __restrict__ me2) {
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (e >= B) return;
+  const long long lo = w.off[e], hi = w.off[e + 1];
+  double a = 0.0;
+  if (hi > lo) {
+    const long long CH = w.meta[1];
+    const long long cl = lo / CH, ch = (hi - 1) / CH;
+    if (cl == ch) {
+      a = w.acc[e];
+    } else {
+      a = w.part[2 * cl + 1];
+      for (long long c = cl + 1; c <= ch; ++c) a += w.part[2 * c];
+    }
   }
+  me2[e] = scale * a * a;
 }
 
 template <int N, typename T>
 cudaError_t launch_comc_n(const ComcParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                          const uint8_t* accept, const double* q, double* me2, int* status, cudaStream_t s) {
+                          const uint8_t* accept, const double* q, double* me2, void* workspace, int sms, int* status,
+                          cudaStream_t s) {
   using S = ComcShape<N, T>;
-  using L = ComcSmem<N, T>;
-  static_assert(L::bytes <= 200 * 1024, "shared memory of the colour-flow kernel");
-  auto kern = comc_kernel<N, T>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-  if (err != cudaSuccess) return err;
+  static_assert(S::tab_bytes + S::NT * (sizeof(T) + 8) + 256 <= 227 * 1024, "shared memory of the colour-flow kernel");
+  ComcWorkspace w;
+  comc_workspace_bytes(N, prm.B, sizeof(T), static_cast<unsigned char*>(workspace), &w);
   const PolFrame F = make_pol_frame(q);
-  const int64_t blocks = (prm.B + S::EB - 1) / S::EB;
-  kern<<<(unsigned)blocks, S::NT, L::bytes, s>>>(prm, p, hel, col, accept, F, me2, status);
+  const int64_t nb = (prm.B + kComcPrepEvents - 1) / kComcPrepEvents;
+  comc_prep_kernel<N, T><<<(unsigned)nb, kComcPrepEvents, 0, s>>>(prm, p, hel, col, accept, F, w, status);
+  comc_scan_kernel<<<1, 1024, 0, s>>>(w.bsum, nb, w.meta, S::NT);
+  comc_offsets_kernel<<<(unsigned)nb, kComcPrepEvents, 0, s>>>(w.off, w.bsum, prm.B);
+  auto kern = comc_eval_kernel<N, T>;
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::tab_bytes);
+    if (err != cudaSuccess) return err;
+    int o = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, S::NT, S::tab_bytes);
+    if (err != cudaSuccess) return err;
+    occ = o > 0 ? o : 1;
+  }
+  kern<<<(unsigned)(sms * occ), S::NT, S::tab_bytes, s>>>(w, prm.B, status);
+  comc_final_kernel<<<(unsigned)((prm.B + 255) / 256), 256, 0, s>>>(w, prm.B, prm.scale, me2);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_comc_t(int n, const ComcParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                          const uint8_t* accept, const double* q, double* me2, int* status, cudaStream_t s) {
+                          const uint8_t* accept, const double* q, double* me2, void* workspace, int sms, int* status,
+                          cudaStream_t s) {
   switch (n) {
-    case 4: return launch_comc_n<4, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 5: return launch_comc_n<5, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 6: return launch_comc_n<6, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 7: return launch_comc_n<7, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 8: return launch_comc_n<8, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 9: return launch_comc_n<9, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 10: return launch_comc_n<10, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 11: return launch_comc_n<11, T>(prm, p, hel, col, accept, q, me2, status, s);
-    case 12: return launch_comc_n<12, T>(prm, p, hel, col, accept, q, me2, status, s);
+    case 4: return launch_comc_n<4, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 5: return launch_comc_n<5, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 6: return launch_comc_n<6, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 7: return launch_comc_n<7, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 8: return launch_comc_n<8, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 9: return launch_comc_n<9, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 10: return launch_comc_n<10, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 11: return launch_comc_n<11, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
+    case 12: return launch_comc_n<12, T>(prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
     default: return cudaErrorInvalidValue;
   }
 }

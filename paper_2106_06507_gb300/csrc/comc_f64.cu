@@ -4,7 +4,8 @@
 
 namespace bg {
 cudaError_t launch_comc_f64(int n, const ComcParams& prm, const double* p, const int8_t* hel, const int8_t* col,
-                            const uint8_t* accept, const double* q, double* me2, int* status, cudaStream_t s) {
-  return launch_comc_t<double>(n, prm, p, hel, col, accept, q, me2, status, s);
+                            const uint8_t* accept, const double* q, double* me2, void* workspace, int sms, int* status,
+                            cudaStream_t s) {
+  return launch_comc_t<double>(n, prm, p, hel, col, accept, q, me2, workspace, sms, status, s);
 }
 }  // namespace bg

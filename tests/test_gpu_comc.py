@@ -15,8 +15,10 @@ and each carries the FP32 recursion's ~1e-6 relative error: median < 5e-5,
 
 Flows are drawn balanced (column colours a permutation of the row colours):
 the others vanish exactly, and uniform flows are balanced for only 3-7 % of
-events.  Degenerate flows (thousands of closing orders in one event) take
-the kernel through several windows of items.
+events.  Degenerate flows (hundreds to millions of closing orders in one
+event) spread one event's items over many chunks of the persistent
+evaluator; past 2^16 chunks the chunks grow beyond one block's worth of
+items, and chunk boundaries cut events (the partial-sum path).
 """
 import numpy as np
 import pytest
@@ -113,8 +115,8 @@ def test_comc_fp32_parity(bg, oracle, n, B):
 
 @pytest.mark.parametrize("n", [8, 9])
 def test_comc_many_orders_per_event(bg, oracle, n):
-    # (n-2)! = 720 / 5040 closing orders per event: several windows of
-    # items per block, items of one event spread over windows
+    # (n-2)! = 720 / 5040 closing orders per event: each event's items
+    # spread over several chunks
     B = 40
     u = inputs.rambo_uniforms(n, B, seed=130 + n)
     hel = inputs.helicities(n, B, seed=130 + n)
@@ -143,6 +145,75 @@ def test_comc_equals_colour_dressed_flow(bg, n, B):
     assert np.median(rel) < 1e-12 and rel.max() < 1e-8
     a32 = run(bg, n, u, hel, cols, bg.BG_F32)
     assert np.quantile(fp32_rel(a32[nz], b[nz]), 0.99) < 1e-3
+
+
+def test_comc_chunked_heavy_events(bg, oracle):
+    # Events with (n-2)! closing orders (n = 10: 40320; n = 12: 3628800)
+    # beside ordinary ones: more than 2^16 x block-size items in total, so
+    # the chunks are larger than one pass and chunk boundaries cut events.
+    # n = 10: a few heavy and ordinary events against the extended-precision
+    # oracle (the FP64 rule of test_comc_fp64_parity), FP32 on the ordinary
+    # events.  Both sizes: every
+    # event against the colour-dressed recursion with the same flows (FP64):
+    # a ranking or chunking mistake changes a flow sum by O(1), while two
+    # FP64 evaluations of sums of up to 3.6e6 cancelling terms by different
+    # recursions differ by up to ~1e-8 (measured at n = 10), so the bound is
+    # 1e-6.  And bit-for-bit reproducibility.
+    for n, B in ((10, 256), (12, 4)):
+        u = inputs.rambo_uniforms(n, B, seed=160 + n)
+        hel = inputs.helicities(n, B, seed=160 + n)
+        cols = inputs.balanced_flow_colours(n, B, seed=160 + n)
+        cols[::2] = degenerate_flows(n, B)[::2]
+        a = run(bg, n, u, hel, cols, bg.BG_F64, pt_min=-1.0)
+        b = run(bg, n, u, hel, cols, bg.BG_F64, pt_min=-1.0, cd=True)
+        nz = split_zeros(a, b)
+        assert nz[::2].all()
+        rel = np.abs(a[nz] - b[nz]) / np.maximum(b[nz], 1e-6 * np.median(b[nz]))
+        assert np.median(rel) < 1e-11 and rel.max() < 1e-6, n
+        a2 = run(bg, n, u, hel, cols, bg.BG_F64, pt_min=-1.0)
+        assert np.array_equal(a, a2)
+        if n == 10:
+            idx = np.array([0, 1, 2, 3, 4, 5])
+            ext = oracle.me2_co_mc(n, u[idx], hel[idx], cols[idx], sqrt_s=SQRT_S, pt_min=-1.0, ext=True)
+            f64 = oracle.me2_co_mc(n, u[idx], hel[idx], cols[idx], sqrt_s=SQRT_S, pt_min=-1.0)
+            assert_fp64_like(a[idx], ext, f64)
+            # FP32 on the ordinary events only: on the heavy ones, 4e4
+            # cancelling orders per event without a cut amplify the FP32
+            # rounding past the FP32 criterion (99 % quantile 7.6e-3
+            # measured; test_comc_many_orders_per_event covers heavy events
+            # with 720 and 5040 orders in FP32)
+            a32 = run(bg, n, u, hel, cols, bg.BG_F32, pt_min=-1.0)
+            odd = np.zeros(B, dtype=bool)
+            odd[1::2] = True
+            m = nz & odd
+            assert m.sum() >= B // 8
+            assert np.quantile(fp32_rel(a32[m], b[m]), 0.99) < 1e-3
+            assert np.array_equal(a32, run(bg, n, u, hel, cols, bg.BG_F32, pt_min=-1.0))
+
+
+def test_comc_workspace_errors(bg):
+    import torch
+    dev = torch.device("cuda:0")
+    n, B = 8, 64
+    need = bg.comc_workspace_bytes(n, B, bg.BG_F32)
+    assert need >= B * (2 * 4 * n * 4 + 8 * n * (n - 1) // 2)
+    assert bg.comc_workspace_bytes(n, B, bg.BG_F64) > need
+    u = inputs.rambo_uniforms(n, B, seed=170)
+    p, acc = bg.momenta_rambo(n, torch.from_numpy(u).to(dev), SQRT_S, PT_MIN)
+    h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=170).T)).to(dev)
+    c = torch.from_numpy(np.ascontiguousarray(inputs.balanced_flow_colours(n, B, seed=170).T)).to(dev)
+    small = torch.empty((need - 256,), dtype=torch.uint8, device=dev)
+    with pytest.raises(bg.BGError) as ei:
+        bg.currents_co_mc(n, p, h, c, accept=acc, workspace=small)
+    assert ei.value.code == bg.BG_EINVAL
+    ws = torch.empty((need + 256,), dtype=torch.uint8, device=dev)
+    with pytest.raises(bg.BGError) as ei:
+        bg.currents_co_mc(n, p, h, c, accept=acc, workspace=ws[8:])  # not 256-byte aligned
+    assert ei.value.code == bg.BG_EINVAL
+    # a caller-owned workspace reused across calls gives the same result
+    one = bg.currents_co_mc(n, p, h, c, accept=acc, workspace=ws).cpu().numpy()
+    two = bg.currents_co_mc(n, p, h, c, accept=acc).cpu().numpy()
+    assert np.array_equal(one, two)
 
 
 def test_comc_edge_cases(bg):
