@@ -76,8 +76,13 @@ struct ComcShape {
   static constexpr int NT = TAB ? 64 : 128;
   static constexpr int M = N - 1;
   static constexpr int NPAIR = N * (N - 1) / 2;
-  static constexpr int NSEG = M * (M + 1) / 2;  // segments (i..j), i <= j, of the off-shell current
-  static constexpr int NSLOT = NSEG + N;         // + prefix sums S_0..S_M of the ordered momenta
+  // LEAF: the one-gluon currents are read from the event's record rather
+  // than kept in the table (FP32 n = 10: a smaller table, one more resident
+  // block per SM, 11 % faster; at n = 11, 12 the extra block's local-memory
+  // stack outgrows L1 and it is slower)
+  static constexpr bool LEAF = TAB && sizeof(T) == 4 && N == 10;
+  static constexpr int NSEGT = LEAF ? M * (M - 1) / 2 : M * (M + 1) / 2;  // segments (i..j) in the table
+  static constexpr int NSLOT = NSEGT + N;  // + prefix sums S_0..S_M of the ordered momenta
   static constexpr size_t tab_bytes = TAB ? sizeof(T) * NSLOT * NT * 4 : 0;
 };
 
@@ -166,13 +171,19 @@ __device__ __forceinline__ float p2_value(float2 a) { return __fadd_rn(a.x, a.y)
 __device__ __forceinline__ double p2_value(double a) { return a; }
 
 
-// Current table in shared memory: segment (i..j), i <= j, of thread t at
+// Current table in shared memory: segment (i..j) of thread t at
 // tab[(seg(i, j) * NT + t) * 4], four consecutive values (one 16-byte load in
-// FP32), consecutive threads in consecutive slots; the prefix sums S_p of the
-// ordered momenta in slots NSEG + p.
-template <int N>
+// FP32), consecutive threads in consecutive slots, segments i <= j (or, with
+// LEAF, i < j: the one-gluon currents J(p..p) are the polarisation vectors
+// and are read from the event's record); the prefix sums S_p of the ordered
+// momenta follow the segments (slot comc_nseg + p).
+template <int N, bool LEAF>
 __host__ __device__ constexpr int comc_seg(int i, int j) {
-  return i * (N - 1) - i * (i - 1) / 2 + (j - i);
+  return LEAF ? i * (N - 2) - i * (i - 1) / 2 + (j - i - 1) : i * (N - 1) - i * (i - 1) / 2 + (j - i);
+}
+template <int N, bool LEAF>
+__host__ __device__ constexpr int comc_nseg() {
+  return LEAF ? (N - 1) * (N - 2) / 2 : (N - 1) * N / 2;
 }
 // The loads are volatile asm statements so that the compiler keeps them in
 // program order instead of hoisting the whole unrolled recursion's loads
@@ -208,6 +219,36 @@ __device__ __forceinline__ void tab_st(double* __restrict__ tab, int seg, const 
   asm volatile("st.volatile.shared.v2.f64 [%0], {%1, %2};" ::"r"(a + 16), "d"(v[2]), "d"(v[3]));
 }
 
+// J(a..b): with LEAF and a == b the polarisation vector of the gluon at
+// position a from the record (ee, 16-byte aligned rows), else the table.
+template <int N, int NT, bool LEAF>
+__device__ __forceinline__ void comc_ldJ(const float* __restrict__ tab, const float* __restrict__ ee,
+                                         const int (&gl)[N], int a, int b, float (&v)[4]) {
+  if (LEAF && a == b) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(ee) + gl[a]);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+    tab_ld<NT>(tab, comc_seg<N, LEAF>(a, b), v);
+  }
+}
+template <int N, int NT, bool LEAF>
+__device__ __forceinline__ void comc_ldJ(const double* __restrict__ tab, const double* __restrict__ ee,
+                                         const int (&gl)[N], int a, int b, double (&v)[4]) {
+  if (LEAF && a == b) {
+    const double2 q0 = __ldg(reinterpret_cast<const double2*>(ee) + 2 * gl[a]);
+    const double2 q1 = __ldg(reinterpret_cast<const double2*>(ee) + 2 * gl[a] + 1);
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    v[3] = q1.y;
+  } else {
+    tab_ld<NT>(tab, comc_seg<N, LEAF>(a, b), v);
+  }
+}
+
 // Bracket of segment (i..j) (the V3 and V4 sums before the propagator, unit
 // vertex factors) from the shared-memory table: the same terms as the
 // register form of the colour-ordered kernels, with the loop over the second
@@ -215,15 +256,16 @@ __device__ __forceinline__ void tab_st(double* __restrict__ tab, int seg, const 
 // J(t+1..j) is loaded once per t, the interior J(s+1..t) as it is used, and
 // the coefficient of J(t+1..j) is complete (and applied) at the end of
 // iteration t.
-template <int N, typename T, int NT>
-__device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, const int i, const int j, T (&br)[4]) {
-  constexpr int M = N - 1, NSEG = M * (M + 1) / 2;
+template <int N, typename T, int NT, bool LEAF>
+__device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, const T* __restrict__ ee,
+                                                 const int (&gl)[N], const int i, const int j, T (&br)[4]) {
+  constexpr int M = N - 1, SP0 = comc_nseg<N, LEAF>();
   T X[M][4];
 #pragma unroll
-  for (int s = i; s < j; ++s) tab_ld<NT>(tab, comc_seg<N>(i, s), X[s]);
+  for (int s = i; s < j; ++s) comc_ldJ<N, NT, LEAF>(tab, ee, gl, i, s, X[s]);
   T Si[4], Sj[4], P2[4];
-  tab_ld<NT>(tab, NSEG + i, Si);
-  tab_ld<NT>(tab, NSEG + j + 1, Sj);
+  tab_ld<NT>(tab, SP0 + i, Si);
+  tab_ld<NT>(tab, SP0 + j + 1, Sj);
   sub4(Sj, Si, P2);
   scale4(T(2), P2, P2);
   T by[4], W[4];
@@ -235,16 +277,16 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
   // during iteration t, J(s+2..t) during iteration s), so that the shared-
   // memory latency overlaps arithmetic; the arithmetic order is unchanged
   T Z[4], St[4];
-  tab_ld<NT>(tab, comc_seg<N>(i + 1, j), Z);
-  tab_ld<NT>(tab, NSEG + i + 1, St);
+  comc_ldJ<N, NT, LEAF>(tab, ee, gl, i + 1, j, Z);
+  tab_ld<NT>(tab, SP0 + i + 1, St);
 #pragma unroll
   for (int t = i; t < j; ++t) {
     T Zn[4], Stn[4], Y[4];
     if (t + 1 < j) {
-      tab_ld<NT>(tab, comc_seg<N>(t + 2, j), Zn);
-      tab_ld<NT>(tab, NSEG + t + 2, Stn);
+      comc_ldJ<N, NT, LEAF>(tab, ee, gl, t + 2, j, Zn);
+      tab_ld<NT>(tab, SP0 + t + 2, Stn);
     }
-    if (i < t) tab_ld<NT>(tab, comc_seg<N>(i + 1, t), Y);
+    if (i < t) comc_ldJ<N, NT, LEAF>(tab, ee, gl, i + 1, t, Y);
     // three-vertex term of the split at t
     const T xy0 = mdot(X[t], Z);
     sxy += xy0;
@@ -255,7 +297,7 @@ __device__ __forceinline__ void comc_bracket_tab(const T* __restrict__ tab, cons
 #pragma unroll
     for (int s = i; s < t; ++s) {
       T Yn[4];
-      if (s + 1 < t) tab_ld<NT>(tab, comc_seg<N>(s + 2, t), Yn);
+      if (s + 1 < t) comc_ldJ<N, NT, LEAF>(tab, ee, gl, s + 2, t, Yn);
       const T xz = mdot(X[s], Z);
       const T xy = mdot(X[s], Y);
       const T yz = mdot(Y, Z);
@@ -345,28 +387,29 @@ __device__ __forceinline__ T comc_amplitude(uint64_t packed, const T* __restrict
 
 // The same with the current table in shared memory (tab: this thread's
 // slice, see tab_ld).
-template <int N, typename T, typename PT, int NT>
+template <int N, typename T, typename PT, int NT, bool LEAF>
 __device__ __forceinline__ T comc_amplitude_tab(uint64_t packed, const T* __restrict__ ke, const T* __restrict__ ee,
                                                 const PT* __restrict__ pr, T* __restrict__ tab) {
-  constexpr int M = N - 1, NSEG = M * (M + 1) / 2;
+  constexpr int M = N - 1, SP0 = comc_nseg<N, LEAF>();
   int gl[N];
   gl[0] = 0;
 #pragma unroll
   for (int pos = 1; pos < N; ++pos) gl[pos] = (int)((packed >> (4 * (pos - 1))) & 15u);
   {
     T S[4] = {T(0), T(0), T(0), T(0)};
-    tab_st<NT>(tab, NSEG, S);
+    tab_st<NT>(tab, SP0, S);
 #pragma unroll
     for (int pos = 0; pos < M; ++pos) {
       const int g = gl[pos];
-      T v[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        v[m] = ee[g * 4 + m];
-        S[m] += ke[g * 4 + m];
+      for (int m = 0; m < 4; ++m) S[m] += ke[g * 4 + m];
+      if (!LEAF) {
+        T v[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) v[m] = ee[g * 4 + m];
+        tab_st<NT>(tab, comc_seg<N, LEAF>(pos, pos), v);
       }
-      tab_st<NT>(tab, comc_seg<N>(pos, pos), v);
-      tab_st<NT>(tab, NSEG + pos + 1, S);
+      tab_st<NT>(tab, SP0 + pos + 1, S);
     }
   }
   PT p2[M];
@@ -380,7 +423,7 @@ __device__ __forceinline__ T comc_amplitude_tab(uint64_t packed, const T* __rest
 #pragma unroll
     for (int i = j - 1; i >= 0; --i) {
       T br[4];
-      comc_bracket_tab<N, T, NT>(tab, i, j, br);
+      comc_bracket_tab<N, T, NT, LEAF>(tab, ee, gl, i, j, br);
       if (i == 0 && j == M - 1) {
         T en[4];
 #pragma unroll
@@ -393,7 +436,7 @@ __device__ __forceinline__ T comc_amplitude_tab(uint64_t packed, const T* __rest
         const T ip = T(1) / T(p2_value(p2[i]));
         T J[4];
         scale4(ip, br, J);
-        tab_st<NT>(tab, comc_seg<N>(i, j), J);
+        tab_st<NT>(tab, comc_seg<N, LEAF>(i, j), J);
       }
       // table values are reloaded by each segment rather than kept live in
       // registers across segments (which would spill)
@@ -660,7 +703,7 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
           const T* ee = ke + N * 4;
           const PT* pr = reinterpret_cast<const PT*>(w.rec + (size_t)e * RB + 2 * sizeof(T) * N * 4);
           if constexpr (S::TAB)
-            amp = comc_amplitude_tab<N, T, PT, NT>(pk, ke, ee, pr, reinterpret_cast<T*>(smem) + tid * 4);
+            amp = comc_amplitude_tab<N, T, PT, NT, S::LEAF>(pk, ke, ee, pr, reinterpret_cast<T*>(smem) + tid * 4);
           else
             amp = comc_amplitude<N, T, PT>(pk, ke, ee, pr);
         }

@@ -37,9 +37,11 @@
 #if defined(__CUDACC__)
 #define COMC_HD __host__ __device__ __forceinline__
 #define COMC_UNROLL _Pragma("unroll")
+#define COMC_ROLLED _Pragma("unroll 1")
 #else
 #define COMC_HD inline
 #define COMC_UNROLL
+#define COMC_ROLLED
 #endif
 
 namespace bg {
@@ -132,7 +134,9 @@ COMC_HD uint64_t comc_unrank(uint32_t rank, const ComcFlow& f, const uint32_t* f
   uint64_t m = comc_types(f), packed = 0;
   uint32_t avail = ((1u << N) - 1u) & ~1u;
   int x = f.c0;
-COMC_UNROLL
+  // not unrolled: the unrolled form adds enough code to the colour-flow
+  // evaluator to thrash its instruction cache (2-3x slower at n = 10..12)
+COMC_ROLLED
   for (int pos = 1; pos < N; ++pos) {
     const uint32_t rowx = x == 0 ? f.rm0 : (x == 1 ? f.rm1 : f.rm2);
     const uint32_t t0 = comc_field(m, 3 * x + 0) ? comc_trails(m - comc_unit(x, 0), 0, f.r0, fact) : 0u;
