@@ -1483,7 +1483,8 @@ def run_forms(args) -> None:
 def run_profile_case(args) -> None:
     """A small case of one multiplicity for ncu captures: `warmup` steps, then
     one step (Rambo, recursion, colour sum; with --workload cd or comc: Rambo
-    once, then the colour-dressed or colour-flow recursion), on cuda:0."""
+    once, then the colour-dressed or colour-flow recursion; with --workload
+    grad: the plan's gradient call), on cuda:0."""
     import numpy as np
     import torch
 
@@ -1512,6 +1513,17 @@ def run_profile_case(args) -> None:
         torch.cuda.synchronize(dev)
         print(json.dumps({"profile_case": {"workload": "comc", "n": n, "batch": B,
                                            "sum_me2": float(me2.sum().item())}}), flush=True)
+        return
+    if args.workload == "grad":
+        u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
+        h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
+        plan = bg.Plan(n, B, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_F32, hel_sampled=True, grad=True)
+        for _ in range(args.warmup + 1):
+            g = plan.grad(u, h)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_case": {"workload": "grad", "n": n, "batch": B,
+                                           "sum_abs_grad": float(g.abs().sum().item())}}), flush=True)
+        plan.close()
         return
     u = torch.from_numpy(inputs.rambo_uniforms(n, B, seed=SEED)).to(dev)
     h = torch.from_numpy(np.ascontiguousarray(inputs.helicities(n, B, seed=SEED).T)).to(dev)
