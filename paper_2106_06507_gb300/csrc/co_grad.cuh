@@ -103,6 +103,9 @@ __device__ __forceinline__ void grad_forward(T (&J)[N - 1][N - 1][4], const T (&
   constexpr int M = N - 1;
 #pragma unroll
   for (int len = 2; len <= M; ++len) {
+    // keeps the block's warps on the same stretch of this long unrolled code,
+    // so that one warp's instruction-cache miss serves the others
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i + len - 1 < M; ++i) {
       const int j = i + len - 1;
@@ -144,6 +147,7 @@ __device__ __forceinline__ void grad_reverse(const T (&J)[N - 1][N - 1][4], cons
 
 #pragma unroll
   for (int len = M; len >= 2; --len) {
+    __syncthreads();  // as in the forward sweep
 #pragma unroll
     for (int i = 0; i + len - 1 < M; ++i) {
       const int j = i + len - 1;
@@ -341,15 +345,19 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
     const int r = t - el * KP;
     const int64_t e = e0 + el;
     const bool live = (e < B) && (r < K);
-    if (live) {
-      const int packed = s_ord[r];
+    {
+      // every thread runs the sweeps (they hold block barriers): the padding
+      // tasks on a clamped ordering and event, with a zero seed
+      const int rc = r < K ? r : K - 1;
+      const int elc = e < B ? el : 0;
+      const int packed = s_ord[rc];
       int gl[N];
       gl[0] = 0;
 #pragma unroll
       for (int pos = 1; pos < N - 1; ++pos) gl[pos] = (packed >> (4 * (pos - 1))) & 15;
       gl[N - 1] = N - 1;
-      const T* ke = s_k + el * N * 4;
-      const T* ee = s_e + el * N * 4;
+      const T* ke = s_k + elc * N * 4;
+      const T* ee = s_e + elc * N * 4;
       T J[M][M][4], Jb[M][M][4], Sp[N][4], Sb[N][4];
       int msk[N];
       msk[0] = 0;
@@ -368,9 +376,9 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
       T en[4], brtop[4], enb[4];
 #pragma unroll
       for (int m = 0; m < 4; ++m) en[m] = ee[(N - 1) * 4 + m];
-      const T* inv = s_inv + el * S::NMASK;
+      const T* inv = s_inv + elc * S::NMASK;
       grad_forward<N, T>(J, Sp, msk, inv, brtop);
-      const T abar = T(2) * vfac * Y[e * (int64_t)K + r];
+      const T abar = live ? T(2) * vfac * Y[e * (int64_t)K + rc] : T(0);
       grad_reverse<N, T>(J, Sp, msk, inv, en, brtop, abar, Jb, Sb, enb);
       // momentum adjoint of the gluon at position q: the sum of Sbar_p over
       // p > q (S_p holds the momenta of positions < p); polarisation adjoints
@@ -392,10 +400,8 @@ __global__ void __launch_bounds__(GradShape<N, T>::NT) co_grad_kernel(int64_t B,
         s_scr[((0 * N + N - 1) * 4 + m) * NT + tid] = T(0);
         s_scr[((1 * N + N - 1) * 4 + m) * NT + tid] = enb[m];
       }
-    } else {
-#pragma unroll
-      for (int v = 0; v < NVAL; ++v) s_scr[v * NT + tid] = T(0);
     }
+    // (dead tasks ran with a zero seed: their adjoints, stored above, are 0)
     // warp sums in a fixed order; a warp holds orderings of one event
     const int wglob = t >> 5;  // warp index among the block's tasks
     const int wel = wglob / S::WPE, wr = wglob % S::WPE;
