@@ -71,6 +71,10 @@ WORKLOAD = ("colour-ordered BG, n=5,6,7,8 gluons, 2^20 Rambo points per n at sqr
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "co_kernel_dfs_n8.md")
 DOMINANT_SOURCES = ("paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/co_f32.cu",
                     "paper_2106_06507_gb300/csrc/device_common.cuh")
+# the same for the gradient kernel at n = 8
+GRAD_SUMMARY = os.path.join(ROOT, "profiles", "co_grad_kernel_n8.md")
+GRAD_SOURCES = ("paper_2106_06507_gb300/csrc/co_grad.cuh", "paper_2106_06507_gb300/csrc/co_grad.cu",
+                "paper_2106_06507_gb300/csrc/co_recursion.cuh", "paper_2106_06507_gb300/csrc/device_common.cuh")
 
 
 def ncu_figures(path: str = NCU_SUMMARY) -> dict | None:
@@ -133,9 +137,9 @@ def colour_sum_flops(n: int) -> int:
     return 2 * k * k + 2 * k
 
 
-def sources_sha1() -> str:
+def sources_sha1(files=DOMINANT_SOURCES) -> str:
     h = hashlib.sha1()
-    for rel in DOMINANT_SOURCES:
+    for rel in files:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -683,7 +687,8 @@ def side_grad(bg, inputs, dev, stream, rank):
     return {"workload": ("|M|^2 and d|M|^2/du (4(n-2) Rambo uniforms), colour-ordered FP32 with full colour sum, "
                          "n=6,8, 2^18 events per n, pT>20 GeV, sampled helicities"),
             "value": value, "unit": "events/s", "per_n": per_n, "batch_per_n": B, "steps": SIDE_STEPS,
-            "warmup": SIDE_WARMUP, "l2": "flushed before each timed step"}, launches
+            "warmup": SIDE_WARMUP, "l2": "flushed before each timed step",
+            "roofline": grad_roofline(per_n, dev)}, launches
 
 
 def side_mixed(bg, inputs, dev, stream, rank):
@@ -1266,6 +1271,23 @@ GRAD_NS = (6, 8)
 GRAD_BATCH = 1 << 18
 
 
+def grad_roofline(per_n: dict, dev) -> dict | None:
+    """Roofline of the gradient kernel at n = 8: executed FP32 FLOPs per event
+    (ncu counters, valid while the kernel sources are those of the capture) x
+    the n = 8 events/s of the whole gradient call (Rambo, recursion, colour
+    sum, adjoint, Rambo adjoint: a conservative span for the kernel)."""
+    fig = ncu_figures(GRAD_SUMMARY)
+    if not fig or fig.get("sources_sha1") != sources_sha1(GRAD_SOURCES) or "8" not in per_n:
+        return None
+    sms = device_sms(dev)
+    achieved = fig["executed_flops_per_event"] * per_n["8"] / 1e12
+    return roofline("co_grad_kernel<8,float> (reverse-mode gradient)", "alu", achieved, fp32_peak_tflops(sms),
+                    "TFLOP/s", fp32_peak_source(sms), flops_model="executed FP32 operations per event (ncu)",
+                    executed_flops_per_event=fig["executed_flops_per_event"],
+                    ncu_summary=os.path.relpath(GRAD_SUMMARY, ROOT),
+                    timed_span="the whole n = 8 gradient call: Rambo, recursion, colour sum, adjoint, Rambo adjoint")
+
+
 def run_grad(args) -> None:
     import numpy as np
     import torch
@@ -1326,7 +1348,7 @@ def run_grad(args) -> None:
             "config": {"workload": ("|M|^2 and d|M|^2/du (4(n-2) Rambo uniforms), colour-ordered FP32 with full "
                                     "colour sum, n=6,8, 2^18 events per n, pT>20 GeV, sampled helicities"),
                        "n": list(GRAD_NS), "batch_per_n": GRAD_BATCH, "parallelism": f"replicas x{world}"},
-            "per_n": per_n, "roofline": None,
+            "per_n": per_n, "roofline": grad_roofline(per_n, dev),
             "e2e": {"value": world * len(GRAD_NS) * GRAD_BATCH * args.steps / e2e_s, "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 5 * len(GRAD_NS) * args.steps, "clocks": clk}), flush=True)

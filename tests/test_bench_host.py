@@ -125,3 +125,31 @@ def test_reference_arm_json_contract(monkeypatch, capsys):
     # the same workload keys as the GPU arm's line
     for k, v in bench.ref_arm_config().items():
         assert line["config"][k] == v
+
+
+def test_gradient_roofline_uses_the_committed_figures_only_for_their_sources():
+    # the executed-FLOP figures the bench reads apply only while the kernel
+    # sources are those of the capture: with matching sources the roofline is
+    # figures x events/s, with other sources (or no n = 8 rate) there is none
+    sys.path.insert(0, ROOT)
+    import bench
+    for summary in (bench.NCU_SUMMARY, bench.GRAD_SUMMARY):
+        fig = bench.ncu_figures(summary)
+        assert fig and fig["executed_flops_per_event"] > 0 and len(fig["sources_sha1"]) == 40
+
+    class Dev:
+        pass
+
+    orig = bench.device_sms
+    bench.device_sms = lambda dev: 152
+    try:
+        r = bench.grad_roofline({"6": 1.0, "8": 1.0e6}, Dev())
+        assert bench.grad_roofline({"6": 1.0}, Dev()) is None
+    finally:
+        bench.device_sms = orig
+    fig = bench.ncu_figures(bench.GRAD_SUMMARY)
+    if fig["sources_sha1"] != bench.sources_sha1(bench.GRAD_SOURCES):
+        assert r is None
+    else:
+        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+        assert abs(r["achieved"] - fig["executed_flops_per_event"] * 1e6 / 1e12) < 1e-9
