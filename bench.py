@@ -706,14 +706,17 @@ def side_mixed(bg, inputs, dev, stream, rank):
     mx.colors.copy_(torch.from_numpy(np.ascontiguousarray(evs["colors"].T)))
     t = timed_side(lambda: mx.run(B, stream=stream), dev, stream)
     counts = mx.counts()[4:]
+    kernels = mx.kernel_nodes()
     mx.close()
+    rl = mixed_roofline(mixed_accepted(bg, evs["nev"], evs["u"], dev), B, B / t, dev)
     return {"workload": ("mixed batch: 10^6 events (the 10^7-event configuration at a tenth of its size) with n "
                          "uniform in 4..12 in one launch: colour-ordered + tensor-core colour sum for n=6..9 (FP32 "
                          "CUDA cores n=4,5), colour-dressed with sampled adjoint colours for n=10..12, FP32 currents, "
                          "FP64 Rambo and accumulation, pT>20 GeV, autotuned kernel variants"),
             "value": B / t, "unit": "events/s", "events": B, "counts_per_n": counts, "seconds_per_step": t,
             "steps": SIDE_STEPS, "warmup": SIDE_WARMUP, "l2": "flushed before each timed step",
-            "launch": "one CUDA-graph launch per step"}, 0
+            "launch": "one CUDA-graph launch per step", "kernels_per_graph": kernels,
+            "roofline": rl}, (SIDE_WARMUP + SIDE_STEPS) * kernels
 
 
 def timed_steps(step, args, dev, stream) -> tuple[float, dict]:
@@ -1360,6 +1363,39 @@ def run_grad(args) -> None:
 MIXED_EVENTS = 10_000_000
 
 
+def mixed_accepted(bg, nev, u, dev) -> dict:
+    """Events with n >= 10 of a mixed batch that pass the cut, per n: the
+    library's own Rambo and cut on their uniforms (outside any timed region)."""
+    import numpy as np
+    import torch
+    out = {}
+    for n in (10, 11, 12):
+        idx = np.nonzero(np.asarray(nev) == n)[0]
+        if idx.size == 0:
+            out[n] = 0
+            continue
+        un = torch.from_numpy(np.ascontiguousarray(np.asarray(u)[idx, :4 * (n - 2)])).to(dev)
+        _, acc = bg.momenta_rambo(n, un, SQRT_S, PT_MIN)
+        out[n] = int(acc.sum().item())
+    return out
+
+
+def mixed_roofline(accepted: dict, batch: int, events_per_s: float, dev) -> dict:
+    """Roofline of the colour-dressed kernel, which carries most of a mixed
+    batch: its dense-model FLOPs for the events with n >= 10 that pass the cut
+    (every such event is computed, whether or not its sampled colours give a
+    non-zero amplitude) x batches per second of the whole graph (a
+    conservative span: every other kernel of the batch runs in that time
+    too)."""
+    flops = sum(cd_dense_flops(n) * accepted.get(n, 0) for n in (10, 11, 12))
+    sms = device_sms(dev)
+    achieved = flops * events_per_s / batch / 1e12
+    return roofline("cd_kernel<10..12,float> in the mixed batch", "alu", achieved, fp32_peak_tflops(sms), "TFLOP/s",
+                    fp32_peak_source(sms), flops_model="dense-model FLOPs of the events with n >= 10 passing the cut",
+                    events_computed={str(n): accepted.get(n, 0) for n in (10, 11, 12)},
+                    timed_span="the whole graph launch (every multiplicity's kernels)")
+
+
 def run_mixed(args) -> None:
     import numpy as np
     import torch
@@ -1398,6 +1434,8 @@ def run_mixed(args) -> None:
         raise RuntimeError("e2e mixed |M|^2 differs from the device-resident run")
     h2d = sum(h.numel() * h.element_size() for h in host)
     tuned = {str(n): bg.tune_get(bg.BG_ALGO_CO if n <= 9 else bg.BG_ALGO_CD, n, bg.BG_F32) for n in range(6, 13)}
+    kernels = mx.kernel_nodes()
+    rl = mixed_roofline(mixed_accepted(bg, ev["nev"], ev["u"], dev), B, value / world, dev)
     if rank == 0:
         print(json.dumps({
             "metric": "events/s", "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -1410,10 +1448,11 @@ def run_mixed(args) -> None:
                        "events": B, "counts_per_n": counts[4:], "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2", "tuned_variants": tuned,
                        "workspace_gb": mx.workspace_bytes / 1e9},
-            "roofline": None,
+            "roofline": rl,
             "e2e": {"value": world * B * args.steps / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": B * 8},
-            "gpu_launches": None, "graph_launches": args.steps, "clocks": clk}), flush=True)
+            "gpu_launches": kernels * args.steps, "graph_launches": args.steps, "kernels_per_graph": kernels,
+            "clocks": clk}), flush=True)
     mx.close()
     finish_gpu(world)
 

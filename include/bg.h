@@ -478,6 +478,10 @@ int64_t bg_mixed_workspace_bytes(const bg_mixed* plan);
 bg_status bg_mixed_run(bg_mixed* plan, int64_t B, void* stream);
 /* counts[13]: events of each n in the last run (synchronises the device). */
 bg_status bg_mixed_counts(bg_mixed* plan, int64_t* counts);
+/* *kernels: the number of kernels one bg_mixed_run launches (the kernel
+ * nodes of the plan's CUDA graph; its other nodes are memory copies and
+ * sets).  Host only, no device work.  Errors: BG_EINVAL, BG_ECUDA. */
+bg_status bg_mixed_kernel_nodes(const bg_mixed* plan, int64_t* kernels);
 
 /* ---------------------------------------------------------------------------
  * Autotuning (no counterpart in the paper).  Each recursion has kernel

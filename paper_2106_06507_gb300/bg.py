@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         L.bg_mixed_workspace_bytes.restype = c_i64
         L.bg_mixed_run.argtypes = [vp, c_i64, vp]
         L.bg_mixed_counts.argtypes = [vp, ctypes.POINTER(c_i64)]
+        L.bg_mixed_kernel_nodes.argtypes = [vp, ctypes.POINTER(c_i64)]
         L.bg_tune_num_variants.argtypes = [c_int, c_int]
         L.bg_tune_num_variants.restype = c_int
         L.bg_autotune.argtypes = [c_int, c_int, c_int, c_i64, vp, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)]
@@ -110,7 +111,7 @@ def lib() -> ctypes.CDLL:
                      "bg_currents_co", "bg_currents_co_tensor", "bg_color_sum", "bg_device_status", "bg_device_status_reset",
                      "bg_plan_create", "bg_me2_batch", "bg_me2_batch_async", "bg_cd_workspace_bytes",
                      "bg_currents_cd", "bg_currents_cd_cont", "bg_apply_cuts", "bg_comc_workspace_bytes", "bg_currents_co_mc", "bg_lc_workspace_bytes", "bg_currents_lc", "bg_me2_grad", "bg_mixed_create", "bg_mixed_buffers", "bg_mixed_run",
-                     "bg_mixed_counts", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
+                     "bg_mixed_counts", "bg_mixed_kernel_nodes", "bg_autotune", "bg_tune_set", "bg_tune_get", "bg_tune_save",
                      "bg_tune_load"):
             getattr(L, name).restype = c_int
         _lib = L
@@ -444,6 +445,12 @@ class Mixed:
         c = (ctypes.c_int64 * 13)()
         _check(lib().bg_mixed_counts(self._h, c))
         return list(c)
+
+    def kernel_nodes(self) -> int:
+        """Kernels one run launches (the kernel nodes of the plan's graph)."""
+        k = ctypes.c_int64()
+        _check(lib().bg_mixed_kernel_nodes(self._h, ctypes.byref(k)))
+        return k.value
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -417,6 +417,28 @@ bg_status bg_mixed_run(bg_mixed* P, int64_t B, void* stream) {
   return cuda_check(cudaGraphLaunch(P->exec, s), "bg_mixed_run: graph launch");
 }
 
+bg_status bg_mixed_kernel_nodes(const bg_mixed* P, int64_t* kernels) {
+  if (!P || !kernels) return fail(BG_EINVAL, "bg_mixed_kernel_nodes: NULL argument");
+  if (!P->graph) return fail(BG_EINVAL, "bg_mixed_kernel_nodes: plan has no graph");
+  size_t num = 0;
+  bg_status st = cuda_check(cudaGraphGetNodes(P->graph, nullptr, &num), "bg_mixed_kernel_nodes");
+  if (st != BG_OK) return st;
+  std::vector<cudaGraphNode_t> nodes(num);
+  if (num) {
+    st = cuda_check(cudaGraphGetNodes(P->graph, nodes.data(), &num), "bg_mixed_kernel_nodes");
+    if (st != BG_OK) return st;
+  }
+  int64_t k = 0;
+  for (size_t i = 0; i < num; ++i) {
+    cudaGraphNodeType t;
+    st = cuda_check(cudaGraphNodeGetType(nodes[i], &t), "bg_mixed_kernel_nodes");
+    if (st != BG_OK) return st;
+    k += t == cudaGraphNodeTypeKernel ? 1 : 0;
+  }
+  *kernels = k;
+  return BG_OK;
+}
+
 bg_status bg_mixed_counts(bg_mixed* P, int64_t* counts) {
   if (!P || !counts) return fail(BG_EINVAL, "bg_mixed_counts: NULL argument");
   // the counts of the last run: wait for it on the device

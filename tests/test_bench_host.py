@@ -153,3 +153,19 @@ def test_gradient_roofline_uses_the_committed_figures_only_for_their_sources():
     else:
         assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
         assert abs(r["achieved"] - fig["executed_flops_per_event"] * 1e6 / 1e12) < 1e-9
+
+
+def test_mixed_roofline_counts_accepted_colour_dressed_events():
+    # dense-model FLOPs of the accepted events with n >= 10 only
+    sys.path.insert(0, ROOT)
+    import bench
+    orig = bench.device_sms
+    bench.device_sms = lambda dev: 152
+    try:
+        r = bench.mixed_roofline({10: 1, 11: 1, 12: 2}, batch=7, events_per_s=7.0e6, dev=None)
+    finally:
+        bench.device_sms = orig
+    flops = bench.cd_dense_flops(10) + bench.cd_dense_flops(11) + 2 * bench.cd_dense_flops(12)
+    assert abs(r["achieved"] - flops * 1.0e6 / 1e12) < 1e-9
+    assert r["bound"] == "alu" and r["frac"] == r["achieved"] / r["peak"]
+    assert r["events_computed"] == {"10": 1, "11": 1, "12": 2}

@@ -112,6 +112,9 @@ def test_mixed_replay_and_edge_cases(bg):
     mx = bg.Mixed(5, 10, B, SQRT_S, PT_MIN, prec=bg.BG_F32, cs_mode=bg.BG_CS_F32, n_co_max=8, chunk_bytes=1)
     load(mx, ev, B)
     first = mx.run(B).cpu().numpy().copy()
+    # the graph's kernels: per multiplicity at least Rambo and a recursion
+    # (n = 5..10: six), plus the binning kernels
+    assert 2 * 6 < mx.kernel_nodes() < 400
     # a shorter replay of the same graph: the first events bin differently
     # but get the same values
     mx.me2.fill_(-1.0)
