@@ -1530,6 +1530,11 @@ def run_forms(args) -> None:
                         "median_rel_amplitude_difference": diff}
     if rank == 0:
         n8 = rows["8"]["ms_per_2^20_events"]
+        sms = device_sms(dev)
+        achieved = tensor_form_flops(8) * (1 << 20) / (n8["tensor_form_one_thread_per_ordering"] * 1e-3) / 1e12
+        rl = roofline("co_kernel<8,float,tensor form>", "alu", achieved, fp32_peak_tflops(sms), "TFLOP/s",
+                      fp32_peak_source(sms), flops_model="canonical FLOPs of the tensor form (tensor_form_flops)",
+                      flops_per_event=tensor_form_flops(8))
         print(json.dumps({
             "metric": "events/s", "value": (1 << 20) / (n8["tensor_form_one_thread_per_ordering"] * 1e-3),
             "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1537,7 +1542,8 @@ def run_forms(args) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": ("colour-ordered recursion alone, four-vertex form against the tensor form, FP32, "
                                     "sampled helicities, pT>20 GeV, n=6..9; value: tensor form at n=8")},
-            "forms": rows, "e2e": None, "gpu_launches": None}), flush=True)
+            "forms": rows, "roofline": rl, "e2e": None,
+            "gpu_launches": 3 * args.steps * len(FORMS_NS)}), flush=True)
     finish_gpu(world)
 
 
