@@ -101,6 +101,18 @@ def test_argument_errors_without_gpu(libbg):
     assert libbg.bg_momenta_rambo(5, 10, 1000.0, None, None, 0.0, None, None) == 1
     row = np.zeros(10)
     assert libbg.bg_colormat_row_host(10, row.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
+    # colour-flow workspace size: argument errors, and the size grows with the batch
+    ws = ctypes.c_int64()
+    libbg.bg_comc_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+    assert libbg.bg_comc_workspace_bytes(13, 10, 1, ctypes.byref(ws)) == 1
+    assert libbg.bg_comc_workspace_bytes(8, -1, 1, ctypes.byref(ws)) == 1
+    assert libbg.bg_comc_workspace_bytes(12, 1000, 1, ctypes.byref(ws)) == 0
+    small = ws.value
+    assert libbg.bg_comc_workspace_bytes(12, 2000, 1, ctypes.byref(ws)) == 0
+    assert ws.value - small >= 1000 * (2 * 4 * 12 * 4 + 8 * 66) and ws.value % 256 == 0
+    # a mixed plan's kernel count needs a plan
+    libbg.bg_mixed_kernel_nodes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    assert libbg.bg_mixed_kernel_nodes(None, ctypes.byref(ws)) == 1
 
 
 def test_tune_variant_counts_without_gpu(libbg):
