@@ -529,8 +529,10 @@ __global__ void __launch_bounds__(ComcShape<N, T>::NT)
       if (tid == 0) s_carry_ev[par ^ 1] = -1;
       // the item's event and order first, then (after a barrier) its
       // recursion: with the two back to back in one thread the FP32 n = 12
-      // kernel gave wrong amplitudes for a tenth of the items (cause not
-      // found; every variant that separates them agrees with the oracle)
+      // kernel gave wrong amplitudes for a tenth of the items.  Only the form
+      // with the asm table loads did (plain or volatile C++ loads were right,
+      // and slower); the cause was not found, and every variant that
+      // separates the two steps agrees with the oracle.
       if (tid < nw) {
         const long long g = w0 + tid;
         e = comc_find_event(w.off, B, g, s_e0);
