@@ -101,6 +101,29 @@ __host__ __device__ constexpr int cd_default_variant(int N) { return N <= 8 ? 0 
 // (shared memory admits one), several for the small tables of n <= 9.
 __host__ __device__ constexpr int cd_min_blocks(int N, int NT) { return N >= 10 ? 1 : 0 * NT; }
 
+// For n >= 10: the number c of chunks of the npart ordered partitions of each
+// of nsub subsets (3 colour rows each) that minimises the rounds of the
+// 3 nsub c tasks on a 512-thread CTA times the partitions of a chunk (the
+// threads of the CTA wait at the level's barrier for its last round), the
+// fewest chunks on ties, at most four rounds.  The choice does not depend on
+// the variant's CTA size, so that all variants add the same partial sums
+// (bitwise identical results).  n <= 9: c0.
+__host__ __device__ constexpr int cd_round_chunks(int N, int nsub, int npart, int c0) {
+  if (N <= 9) return c0;
+  constexpr int ref = 512;
+  int best = 1;
+  long long best_cost = -1;
+  for (int c = 1; c <= npart && (c == 1 || 3LL * nsub * c <= 4LL * ref); ++c) {
+    const long long rounds = (3LL * nsub * c + ref - 1) / ref;
+    const long long cost = rounds * ((npart + c - 1) / c);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
 template <int N, typename T>
 struct CdShape {
   static constexpr int M = N - 1;
@@ -120,10 +143,13 @@ struct CdShape {
   static constexpr size_t DYN_SMEM = (size_t)NSM * REC * sizeof(T);
   // top level: chunks of the partitions of the full set, per colour row
   static constexpr int NPART_TOP = NS - 2;
-  static constexpr int NCH_TOP = (TARGET + 2) / 3 < NPART_TOP ? (TARGET + 2) / 3 : NPART_TOP;
+  static constexpr int NCH_TOP = cd_round_chunks(N, 1, NPART_TOP, (TARGET + 2) / 3 < NPART_TOP ? (TARGET + 2) / 3 : NPART_TOP);
 };
 
-// Chunks of ordered partitions per (subset, colour row) at level L.
+// Chunks of ordered partitions per (subset, colour row) at level L.  n <= 9
+// (several CTAs per SM): about TARGET tasks per level.  n >= 10 (one CTA per
+// SM, whose threads wait at the level's barrier for its last round of
+// tasks): the count cd_round_chunks picks.
 template <int N, typename T>
 __host__ __device__ constexpr int cd_chunks(int L) {
   constexpr int M = N - 1;
@@ -132,7 +158,7 @@ __host__ __device__ constexpr int cd_chunks(int L) {
   int c = (CdShape<N, T>::TARGET + tasks - 1) / tasks;
   if (c < 1) c = 1;
   if (c > npart) c = npart;
-  return c;
+  return cd_round_chunks(N, cd_binom(M, L), npart, c);
 }
 
 template <int N, typename T>
