@@ -212,6 +212,19 @@ __device__ __forceinline__ void cd_ld6<double>(const double* p, double (&x)[6]) 
   x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y, x[4] = c.x, x[5] = c.y;
 }
 
+template <typename T>
+struct CdPair;
+template <>
+struct CdPair<float> {
+  using type = float2;
+};
+template <>
+struct CdPair<double> {
+  using type = double2;
+};
+__device__ __forceinline__ float2 cd_pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 cd_pair(double a, double b) { return make_double2(a, b); }
+
 // Contribution of one ordered partition (S1 left, record A; S2 right,
 // record B) to the colour entries (r, c), c = 0..2, of row r, summed over
 // the inner colour index l.  Dense: zero entries contribute exact zeros.
@@ -487,13 +500,16 @@ __global__ void __launch_bounds__(NT, cd_min_blocks(N, NT)) cd_kernel(CdParams p
             for (int m = 0; m < 6; ++m) RS[Sh::OFF_T + 6 * (3 * r + c) + m] = tc[c][m];
           }
         } else {
-          T* q = part + (size_t)t * 30;
+          // 30 values as 15 aligned pairs (t * 30 is even, the slab
+          // 16-byte aligned)
+          using V2 = typename CdPair<T>::type;
+          V2* q = reinterpret_cast<V2*>(part + (size_t)t * 30);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) q[10 * c + m] = br[c][m];
+            for (int m = 0; m < 4; m += 2) q[(10 * c + m) / 2] = cd_pair(br[c][m], br[c][m + 1]);
 #pragma unroll
-            for (int m = 0; m < 6; ++m) q[10 * c + 4 + m] = tc[c][m];
+            for (int m = 0; m < 6; m += 2) q[(10 * c + 4 + m) / 2] = cd_pair(tc[c][m], tc[c][m + 1]);
           }
         }
       }
@@ -509,7 +525,12 @@ __global__ void __launch_bounds__(NT, cd_min_blocks(N, NT)) cd_kernel(CdParams p
           for (int ch = 0; ch < nch; ++ch) {
             const size_t t = ((size_t)si * nch + ch) * 3 + r;
 #pragma unroll
-            for (int m = 0; m < 10; ++m) acc[m] += part[t * 30 + 10 * c + m];
+            for (int m = 0; m < 10; m += 2) {
+              const typename CdPair<T>::type v =
+                  reinterpret_cast<const typename CdPair<T>::type*>(part)[(t * 30 + 10 * c + m) / 2];
+              acc[m] += v.x;
+              acc[m + 1] += v.y;
+            }
           }
           T* RS = cd_rec<N, T>(sRec, gRec, rkS);
           const T ip = RS[Sh::OFF_INV];
