@@ -9,8 +9,10 @@ list are compared with brute force over all (n-1)! orders, in lexicographic
 order of the labels: equal, element by element, for random flows at
 n = 4..8, for the degenerate flows (all gluons on one colour line: every
 order closes; two colours only; a flow whose colour lines fall apart into
-two components), and the count alone at n = 9..12 against a type-level
-enumeration.  One rank past the end must be reported as out of range."""
+two components); at n = 9..12 the full ranked list against a depth-first
+search over the colour chain (flows with up to a few thousand orders), and
+the count alone against a type-level enumeration.  One rank past the end
+must be reported as out of range."""
 import itertools
 import math
 import subprocess
@@ -138,3 +140,43 @@ def run_driver_counts(exe, flows):
     text = "".join(f"-{len(f)} " + " ".join(f"{r} {c}" for r, c in f) + "\n" for f in flows)
     out = subprocess.run([str(exe)], input=text, capture_output=True, text=True, check=True).stdout
     return [int(line.split()[1]) if line.split()[0] == "1" else None for line in out.splitlines()]
+
+
+def dfs_orders(flow):
+    """Closing orders in lexicographic label order by depth-first search over
+    the colour chain (no (n-1)! enumeration: usable at n = 9..12)."""
+    n = len(flow)
+    r0 = flow[0][0]
+    out, seq, used = [], [], [False] * n
+
+    def rec(x):
+        if len(seq) == n - 1:
+            if x == r0:
+                out.append(tuple(seq))
+            return
+        for g in range(1, n):
+            if not used[g] and flow[g][0] == x:
+                used[g] = True
+                seq.append(g)
+                rec(flow[g][1])
+                seq.pop()
+                used[g] = False
+
+    rec(flow[0][1])
+    return out
+
+
+@pytest.mark.parametrize("n", [9, 10, 11, 12])
+def test_ranked_orders_equal_dfs_at_large_n(driver, n):
+    # every order, in order, for random balanced flows with at most a few
+    # thousand closing orders each (about 2 * 10^4 orders per n in all)
+    flows, total = [], 0
+    for f in random_flows(n, 200, seed=600 + n):
+        c = type_level_count(f)
+        if c <= 5000 and total + c <= 20000:
+            flows.append(f)
+            total += c
+    assert sum(type_level_count(f) > 0 for f in flows) >= 5
+    for f, g in zip(flows, run_driver(driver, flows)):
+        ref = dfs_orders(f)
+        assert g[0] == len(ref) and g[1] == ref, f
